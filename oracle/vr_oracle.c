@@ -1,0 +1,560 @@
+/*
+ * vr_oracle.c -- plain FP64 CPU ray caster: the definition the CUDA path is
+ * checked against.
+ *
+ * TEST INFRASTRUCTURE.  Only the test suite, the smoke check and the timed CPU
+ * baseline of the benchmark may load this library.  It shares no code, header,
+ * table or constant with the CUDA library; it is deliberately slow and written
+ * for a reader to check against the paper by eye.
+ *
+ * What it computes (Hassan et al. 2012, Section 3.3 "Transfer functions",
+ * 3.3.2 "Generic transfer function volume rendering", 3.4 "The frame
+ * composition processes", and the constant-step trilinear sampling of
+ * Section 4.4 "3D spectrum tool"): one ray per output pixel is clipped to the
+ * volume box and sampled at a constant step; each sample is the trilinear
+ * interpolation of the grid, mapped through a discrete RGBA transfer function
+ * (colour plus an opacity in [0,1] per data level), and the samples are merged
+ * front to back with the "over" operator (emission-absorption model of
+ * Levoy 1988, which the paper cites).  Early ray termination is not in the
+ * paper; it is a stated extension: stop after the sample at which the
+ * accumulated opacity reaches the threshold.
+ *
+ * Readings where the paper is silent (all of them documented with the build):
+ *   - camera: f = normalize(forward), r = normalize(f x up), u = r x f; pixel
+ *     centres at +1/2; row 0 is the top (+u); aspect = W/H.  Orthographic rays
+ *     start on the image plane and are not clipped at t = 0; perspective rays
+ *     start at the eye and keep t >= 0.
+ *   - grid: voxel centres at integer indices, box = closed [0, n-1] per axis.
+ *   - samples: t_k = t_in + (k + 1/2) * step while t_k <= t_out, i.e.
+ *     n = floor((t_out - t_in)/step + 1/2); positions are o + t_k d, never
+ *     accumulated.  The step is in world units along the unit direction.
+ *   - trilinear: cell origin i0 = clamp(floor(x), 0, n-2), weight x - i0.
+ *   - transfer function: u = clamp((v - vmin)/(vmax - vmin), 0, 1) * (K-1),
+ *     i0 = min(floor(u), K-2), w = u - i0, linear blend of entries i0, i0+1;
+ *     entries are straight (not premultiplied) RGBA; no opacity correction.
+ *   - composite: C += T a c; T *= (1 - a); stop after the sample once
+ *     1 - T >= thr (thr > 1 disables); output (C + T bg.rgb, 1 - T + T bg.a).
+ *
+ * The backward pass is plain reverse-mode differentiation of that forward
+ * definition: every sample of a ray is stored, then the ray is walked back to
+ * front with suffix accumulators (no division by transmittance), followed by
+ * the chain rule through the transfer-function blend and the trilinear
+ * weights.
+ */
+#include <math.h>
+#include <pthread.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* ------------------------------------------------------------------------ */
+/* Types (this file's own; nothing is shared with the CUDA library)          */
+/* ------------------------------------------------------------------------ */
+
+typedef struct {
+    int kind;                 /* 0 orthographic, 1 perspective */
+    double eye[3];
+    double forward[3];
+    double up[3];
+    double fov_y_deg;         /* perspective: full vertical field of view */
+    double ortho_height;      /* orthographic: world height of the image */
+    int width, height;
+} orc_camera;
+
+typedef struct {
+    const void *data;         /* dense, x fastest then y then z */
+    int dtype;                /* 0 float32, 1 float64, 2 binary16 bits, 3 bfloat16 bits */
+    int64_t n[3];             /* nx, ny, nz (each >= 2) */
+    double origin[3];         /* world position of voxel (0,0,0) */
+    double spacing[3];        /* world size of one voxel step per axis */
+} orc_volume;
+
+typedef struct {
+    const double *tf;         /* K x 4 straight RGBA */
+    int K;
+    double vmin, vmax;
+    double step;              /* world units, > 0 */
+    double ert;               /* early-termination opacity; > 1 disables */
+    double bg[4];             /* background RGBA */
+} orc_params;
+
+/* ------------------------------------------------------------------------ */
+/* Voxel access (exact widening of the stored value)                         */
+/* ------------------------------------------------------------------------ */
+
+static double half_bits_to_double(uint16_t h)
+{
+    /* IEEE 754 binary16: 1 sign, 5 exponent (bias 15), 10 fraction bits. */
+    int s = (h >> 15) & 1, e = (h >> 10) & 31, m = h & 1023;
+    double mag;
+    if (e == 0)
+        mag = ldexp((double)m, -24);                  /* subnormal: m * 2^-24 */
+    else if (e == 31)
+        mag = m ? NAN : INFINITY;
+    else
+        mag = ldexp((double)(1024 + m), e - 25);      /* (1 + m/1024) * 2^(e-15) */
+    return s ? -mag : mag;
+}
+
+static double bf16_bits_to_double(uint16_t b)
+{
+    /* bfloat16 is the upper half of an IEEE binary32. */
+    uint32_t u = (uint32_t)b << 16;
+    float f;
+    memcpy(&f, &u, sizeof f);
+    return (double)f;
+}
+
+static double voxel_at(const orc_volume *v, int64_t x, int64_t y, int64_t z)
+{
+    int64_t i = (z * v->n[1] + y) * v->n[0] + x;
+    switch (v->dtype) {
+    case 0: return (double)((const float *)v->data)[i];
+    case 1: return ((const double *)v->data)[i];
+    case 2: return half_bits_to_double(((const uint16_t *)v->data)[i]);
+    default: return bf16_bits_to_double(((const uint16_t *)v->data)[i]);
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Camera (per pixel ray in world space)                                     */
+/* ------------------------------------------------------------------------ */
+
+static void cross3(const double a[3], const double b[3], double o[3])
+{
+    o[0] = a[1] * b[2] - a[2] * b[1];
+    o[1] = a[2] * b[0] - a[0] * b[2];
+    o[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+static void normalize3(double a[3])
+{
+    double l = sqrt(a[0] * a[0] + a[1] * a[1] + a[2] * a[2]);
+    a[0] /= l; a[1] /= l; a[2] /= l;
+}
+
+typedef struct { double f[3], r[3], u[3]; } basis;
+
+static basis camera_basis(const orc_camera *c)
+{
+    basis b;
+    memcpy(b.f, c->forward, sizeof b.f);
+    normalize3(b.f);
+    cross3(b.f, c->up, b.r);
+    normalize3(b.r);
+    cross3(b.r, b.f, b.u);
+    return b;
+}
+
+/* Ray through the centre of pixel (i, j): origin o and unit direction d. */
+static void pixel_ray(const orc_camera *c, const basis *b, int i, int j, double o[3], double d[3])
+{
+    double sx = ((i + 0.5) / c->width) * 2.0 - 1.0;
+    double sy = 1.0 - ((j + 0.5) / c->height) * 2.0;
+    double aspect = (double)c->width / (double)c->height;
+    if (c->kind == 0) {
+        double hh = 0.5 * c->ortho_height;
+        for (int a = 0; a < 3; ++a) {
+            o[a] = c->eye[a] + sx * hh * aspect * b->r[a] + sy * hh * b->u[a];
+            d[a] = b->f[a];
+        }
+    } else {
+        double th = tan(c->fov_y_deg * M_PI / 360.0);   /* tan(fov/2) */
+        for (int a = 0; a < 3; ++a) {
+            o[a] = c->eye[a];
+            d[a] = b->f[a] + sx * th * aspect * b->r[a] + sy * th * b->u[a];
+        }
+        normalize3(d);
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Box clipping (slab method) in voxel coordinates                           */
+/* ------------------------------------------------------------------------ */
+
+/* p_vox(t) = ov + t * dv, t in world units along the unit world direction.
+ * Returns 1 and [t_in, t_out] when the ray meets the closed box [0, n-1]^3
+ * over an interval of positive length, else 0. */
+static int clip_box(const orc_volume *v, int perspective, const double ov[3], const double dv[3],
+                    double *t_in, double *t_out)
+{
+    double tin = perspective ? 0.0 : -INFINITY, tout = INFINITY;
+    for (int a = 0; a < 3; ++a) {
+        double lo = 0.0, hi = (double)(v->n[a] - 1);
+        if (dv[a] == 0.0) {
+            if (ov[a] < lo || ov[a] > hi) return 0;   /* parallel and outside */
+            continue;                                   /* parallel and inside */
+        }
+        double t0 = (lo - ov[a]) / dv[a], t1 = (hi - ov[a]) / dv[a];
+        if (t0 > t1) { double s = t0; t0 = t1; t1 = s; }
+        if (t0 > tin) tin = t0;
+        if (t1 < tout) tout = t1;
+    }
+    *t_in = tin;
+    *t_out = tout;
+    return tin < tout;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Trilinear interpolation and transfer function                             */
+/* ------------------------------------------------------------------------ */
+
+typedef struct {
+    int64_t idx[8];           /* dense voxel indices of the 8 corners */
+    double wt[8];             /* their trilinear weights */
+} corners;
+
+static double trilinear(const orc_volume *v, const double p[3], corners *cs)
+{
+    int64_t c0[3];
+    double fr[3];
+    for (int a = 0; a < 3; ++a) {
+        double fl = floor(p[a]);
+        int64_t i0 = (int64_t)fl;
+        if (i0 < 0) i0 = 0;
+        if (i0 > v->n[a] - 2) i0 = v->n[a] - 2;
+        c0[a] = i0;
+        fr[a] = p[a] - (double)i0;
+    }
+    double val = 0.0;
+    int k = 0;
+    for (int dz = 0; dz < 2; ++dz)
+        for (int dy = 0; dy < 2; ++dy)
+            for (int dx = 0; dx < 2; ++dx, ++k) {
+                double w = (dx ? fr[0] : 1.0 - fr[0]) * (dy ? fr[1] : 1.0 - fr[1]) *
+                           (dz ? fr[2] : 1.0 - fr[2]);
+                int64_t x = c0[0] + dx, y = c0[1] + dy, z = c0[2] + dz;
+                if (cs) {
+                    cs->idx[k] = (z * v->n[1] + y) * v->n[0] + x;
+                    cs->wt[k] = w;
+                }
+                val += w * voxel_at(v, x, y, z);
+            }
+    return val;
+}
+
+typedef struct {
+    int i0;                   /* lower table entry */
+    double w;                 /* blend weight of entry i0+1 */
+    int interior;             /* vmin < v < vmax: the lookup has a slope in v */
+} tf_pos;
+
+static void tf_lookup(const orc_params *P, double v, double rgba[4], tf_pos *pos)
+{
+    double s = (v - P->vmin) / (P->vmax - P->vmin);
+    int interior = (s > 0.0 && s < 1.0);
+    if (!(s > 0.0)) s = 0.0;                 /* also maps NaN to the low end */
+    if (s > 1.0) s = 1.0;
+    double u = s * (P->K - 1);
+    int i0 = (int)floor(u);
+    if (i0 > P->K - 2) i0 = P->K - 2;
+    double w = u - i0;
+    for (int ch = 0; ch < 4; ++ch)
+        rgba[ch] = (1.0 - w) * P->tf[4 * i0 + ch] + w * P->tf[4 * (i0 + 1) + ch];
+    if (pos) { pos->i0 = i0; pos->w = w; pos->interior = interior; }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Per-ray forward                                                           */
+/* ------------------------------------------------------------------------ */
+
+typedef struct {
+    double ov[3], dv[3];      /* ray in voxel coordinates */
+    double t_in;
+    int64_t n;                /* samples on the clipped ray (before early termination) */
+    double margin_n;          /* distance of (t_out-t_in)/step + 1/2 to the nearest integer */
+} ray_setup;
+
+static void setup_ray(const orc_volume *v, const orc_camera *c, const basis *b, const orc_params *P,
+                      int i, int j, ray_setup *rs)
+{
+    double o[3], d[3];
+    pixel_ray(c, b, i, j, o, d);
+    for (int a = 0; a < 3; ++a) {
+        rs->ov[a] = (o[a] - v->origin[a]) / v->spacing[a];
+        rs->dv[a] = d[a] / v->spacing[a];
+    }
+    double tin, tout;
+    if (!clip_box(v, c->kind == 1, rs->ov, rs->dv, &tin, &tout)) {
+        rs->n = 0;
+        rs->t_in = 0.0;
+        rs->margin_n = INFINITY;
+        return;
+    }
+    double q = (tout - tin) / P->step + 0.5;
+    rs->n = (int64_t)floor(q);
+    rs->margin_n = fabs(q - floor(q + 0.5));
+    rs->t_in = tin;
+}
+
+static void sample_pos(const ray_setup *rs, const orc_params *P, int64_t k, double p[3])
+{
+    double t = rs->t_in + ((double)k + 0.5) * P->step;
+    for (int a = 0; a < 3; ++a) p[a] = rs->ov[a] + t * rs->dv[a];
+}
+
+/* Renders pixel (i, j); writes RGBA, the number of composited samples and the
+ * two decision margins (sample count, early termination). */
+static void render_pixel(const orc_volume *v, const orc_camera *c, const basis *b, const orc_params *P,
+                         int i, int j, double out[4], int32_t *n_used, double *m_n, double *m_ert)
+{
+    ray_setup rs;
+    setup_ray(v, c, b, P, i, j, &rs);
+    double C[3] = {0.0, 0.0, 0.0}, T = 1.0, mert = INFINITY;
+    int64_t used = 0;
+    for (int64_t k = 0; k < rs.n; ++k) {
+        double p[3], rgba[4];
+        sample_pos(&rs, P, k, p);
+        double val = trilinear(v, p, NULL);
+        tf_lookup(P, val, rgba, NULL);
+        double a = rgba[3];
+        for (int ch = 0; ch < 3; ++ch) C[ch] += T * a * rgba[ch];
+        T *= (1.0 - a);
+        used = k + 1;
+        double opacity = 1.0 - T;
+        if (P->ert <= 1.0) {
+            double m = fabs(opacity - P->ert);
+            if (m < mert) mert = m;
+        }
+        if (opacity >= P->ert) break;
+    }
+    for (int ch = 0; ch < 3; ++ch) out[ch] = C[ch] + T * P->bg[ch];
+    out[3] = 1.0 - T + T * P->bg[3];
+    if (n_used) *n_used = (int32_t)used;
+    if (m_n) *m_n = rs.margin_n;
+    if (m_ert) *m_ert = mert;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Threaded driver over image rows                                           */
+/* ------------------------------------------------------------------------ */
+
+typedef struct {
+    const orc_volume *v;
+    const orc_camera *c;
+    const orc_params *P;
+    basis b;
+    int row0, row1, stride, first;
+    double *rgba;             /* H*W*4 */
+    int32_t *n_used;          /* H*W or NULL */
+    double *margin_n;         /* H*W or NULL */
+    double *margin_ert;       /* H*W or NULL */
+    /* backward */
+    const double *grad_rgba;
+    double *grad_tf;          /* private K*4 */
+    double *grad_vox;         /* private nx*ny*nz or NULL */
+} job;
+
+static void *fwd_worker(void *arg)
+{
+    job *J = (job *)arg;
+    int W = J->c->width;
+    for (int j = J->row0 + J->first; j < J->row1; j += J->stride)
+        for (int i = 0; i < W; ++i) {
+            int64_t px = (int64_t)j * W + i;
+            render_pixel(J->v, J->c, &J->b, J->P, i, j, J->rgba + 4 * px,
+                         J->n_used ? J->n_used + px : NULL, J->margin_n ? J->margin_n + px : NULL,
+                         J->margin_ert ? J->margin_ert + px : NULL);
+        }
+    return NULL;
+}
+
+static int run_threads(job *jobs, int nthreads, void *(*fn)(void *))
+{
+    if (nthreads <= 1) {
+        fn(&jobs[0]);
+        return 0;
+    }
+    pthread_t *th = (pthread_t *)malloc(sizeof(pthread_t) * (size_t)nthreads);
+    if (!th) return -3;
+    int started = 0, rc = 0;
+    for (int t = 0; t < nthreads; ++t) {
+        if (pthread_create(&th[t], NULL, fn, &jobs[t]) != 0) { rc = -3; break; }
+        ++started;
+    }
+    for (int t = 0; t < started; ++t) pthread_join(th[t], NULL);
+    for (int t = started; t < nthreads && rc == 0; ++t) fn(&jobs[t]);
+    free(th);
+    return rc;
+}
+
+static int check_args(const orc_volume *v, const orc_camera *c, const orc_params *P)
+{
+    if (!v || !c || !P || !v->data || !P->tf) return -1;
+    for (int a = 0; a < 3; ++a)
+        if (v->n[a] < 2 || !(v->spacing[a] > 0.0)) return -1;
+    if (c->width <= 0 || c->height <= 0 || P->K < 2 || !(P->step > 0.0) || !(P->vmax > P->vmin)) return -1;
+    if (c->kind != 0 && c->kind != 1) return -1;
+    return 0;
+}
+
+/* Forward render of rows [row0, row1) of the image.  Outputs are indexed by
+ * the full image (row j, column i at j*W + i); rows outside the range are not
+ * touched.  Returns 0, or -1 on invalid arguments. */
+int orc_render(const orc_volume *v, const orc_camera *c, const orc_params *P, int row0, int row1,
+               double *rgba, int32_t *n_used, double *margin_n, double *margin_ert, int nthreads)
+{
+    if (check_args(v, c, P) || !rgba) return -1;
+    if (row0 < 0) row0 = 0;
+    if (row1 > c->height) row1 = c->height;
+    if (nthreads < 1) nthreads = 1;
+    job *jobs = (job *)calloc((size_t)nthreads, sizeof(job));
+    if (!jobs) return -3;
+    basis b = camera_basis(c);
+    for (int t = 0; t < nthreads; ++t) {
+        jobs[t].v = v; jobs[t].c = c; jobs[t].P = P; jobs[t].b = b;
+        jobs[t].row0 = row0; jobs[t].row1 = row1; jobs[t].stride = nthreads; jobs[t].first = t;
+        jobs[t].rgba = rgba; jobs[t].n_used = n_used;
+        jobs[t].margin_n = margin_n; jobs[t].margin_ert = margin_ert;
+    }
+    int rc = run_threads(jobs, nthreads, fwd_worker);
+    free(jobs);
+    return rc;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Backward: store-all reverse mode, back to front                            */
+/* ------------------------------------------------------------------------ */
+
+typedef struct {
+    double rgba[4];
+    double T;                 /* transmittance in front of the sample */
+    tf_pos pos;
+    corners cs;
+} stored_sample;
+
+static void backward_pixel(job *J, int i, int j, stored_sample **buf, int64_t *cap)
+{
+    const orc_volume *v = J->v;
+    const orc_params *P = J->P;
+    ray_setup rs;
+    setup_ray(v, J->c, &J->b, P, i, j, &rs);
+    if (rs.n <= 0) return;
+    if (rs.n > *cap) {
+        free(*buf);
+        *cap = rs.n;
+        *buf = (stored_sample *)malloc(sizeof(stored_sample) * (size_t)rs.n);
+    }
+    stored_sample *S = *buf;
+
+    /* Forward, storing every composited sample. */
+    double T = 1.0;
+    int64_t used = 0;
+    for (int64_t k = 0; k < rs.n; ++k) {
+        double p[3];
+        sample_pos(&rs, P, k, p);
+        double val = trilinear(v, p, &S[k].cs);
+        tf_lookup(P, val, S[k].rgba, &S[k].pos);
+        S[k].T = T;
+        T *= (1.0 - S[k].rgba[3]);
+        used = k + 1;
+        if (1.0 - T >= P->ert) break;
+    }
+
+    /* Output I = (C + T_n bg.rgb, 1 - T_n (1 - bg.a)).  With g = dL/dI.rgb and
+     * gA = dL/dI.a the loss reacts to C through g and to T_n through gT. */
+    const double *gI = J->grad_rgba + 4 * ((int64_t)j * J->c->width + i);
+    double g[3] = {gI[0], gI[1], gI[2]};
+    double gT = g[0] * P->bg[0] + g[1] * P->bg[1] + g[2] * P->bg[2] - gI[3] * (1.0 - P->bg[3]);
+
+    /* Suffix accumulators normalised to the transmittance behind sample k:
+     * Ssuf = sum_{j>k} (T_j / T_{k+1}) a_j (c_j . g),  Psuf = T_n / T_{k+1}. */
+    double Ssuf = 0.0, Psuf = 1.0;
+    double scale = (double)(P->K - 1) / (P->vmax - P->vmin);
+    for (int64_t k = used - 1; k >= 0; --k) {
+        const stored_sample *s = &S[k];
+        double a = s->rgba[3];
+        double cg = s->rgba[0] * g[0] + s->rgba[1] * g[1] + s->rgba[2] * g[2];
+        double dr[4];
+        for (int ch = 0; ch < 3; ++ch) dr[ch] = s->T * a * g[ch];     /* dL/dc_k */
+        dr[3] = s->T * (cg - Ssuf - gT * Psuf);                        /* dL/da_k */
+        Ssuf = a * cg + (1.0 - a) * Ssuf;
+        Psuf = (1.0 - a) * Psuf;
+
+        int i0 = s->pos.i0;
+        double w = s->pos.w;
+        double dv = 0.0;
+        for (int ch = 0; ch < 4; ++ch) {
+            J->grad_tf[4 * i0 + ch] += (1.0 - w) * dr[ch];
+            J->grad_tf[4 * (i0 + 1) + ch] += w * dr[ch];
+            dv += dr[ch] * (P->tf[4 * (i0 + 1) + ch] - P->tf[4 * i0 + ch]);
+        }
+        if (J->grad_vox && s->pos.interior) {
+            dv *= scale;
+            for (int q = 0; q < 8; ++q) J->grad_vox[s->cs.idx[q]] += s->cs.wt[q] * dv;
+        }
+    }
+}
+
+static void *bwd_worker(void *arg)
+{
+    job *J = (job *)arg;
+    stored_sample *buf = NULL;
+    int64_t cap = 0;
+    for (int j = J->row0 + J->first; j < J->row1; j += J->stride)
+        for (int i = 0; i < J->c->width; ++i) backward_pixel(J, i, j, &buf, &cap);
+    free(buf);
+    return NULL;
+}
+
+/* Gradients of L with respect to the K x 4 table and (optionally) the dense
+ * voxels, given dL/dI (H*W*4).  Both outputs are overwritten.  Per-thread
+ * partial sums are added in thread order, so the result is deterministic for
+ * a given thread count. */
+int orc_render_backward(const orc_volume *v, const orc_camera *c, const orc_params *P,
+                        const double *grad_rgba, double *grad_tf, double *grad_vox, int nthreads)
+{
+    if (check_args(v, c, P) || !grad_rgba || !grad_tf) return -1;
+    if (nthreads < 1) nthreads = 1;
+    int64_t nvox = v->n[0] * v->n[1] * v->n[2];
+    job *jobs = (job *)calloc((size_t)nthreads, sizeof(job));
+    if (!jobs) return -3;
+    basis b = camera_basis(c);
+    int rc = 0;
+    for (int t = 0; t < nthreads; ++t) {
+        jobs[t].v = v; jobs[t].c = c; jobs[t].P = P; jobs[t].b = b;
+        jobs[t].row0 = 0; jobs[t].row1 = c->height; jobs[t].stride = nthreads; jobs[t].first = t;
+        jobs[t].grad_rgba = grad_rgba;
+        jobs[t].grad_tf = (double *)calloc((size_t)P->K * 4, sizeof(double));
+        jobs[t].grad_vox = grad_vox ? (double *)calloc((size_t)nvox, sizeof(double)) : NULL;
+        if (!jobs[t].grad_tf || (grad_vox && !jobs[t].grad_vox)) rc = -3;
+    }
+    if (rc == 0) rc = run_threads(jobs, nthreads, bwd_worker);
+    if (rc == 0) {
+        memset(grad_tf, 0, sizeof(double) * (size_t)P->K * 4);
+        if (grad_vox) memset(grad_vox, 0, sizeof(double) * (size_t)nvox);
+        for (int t = 0; t < nthreads; ++t) {
+            for (int q = 0; q < P->K * 4; ++q) grad_tf[q] += jobs[t].grad_tf[q];
+            if (grad_vox)
+                for (int64_t q = 0; q < nvox; ++q) grad_vox[q] += jobs[t].grad_vox[q];
+        }
+    }
+    for (int t = 0; t < nthreads; ++t) { free(jobs[t].grad_tf); free(jobs[t].grad_vox); }
+    free(jobs);
+    return rc;
+}
+
+/* Single-sample probes used by the tests: the trilinear value at a voxel
+ * position, and the table lookup of a value. */
+double orc_trilinear(const orc_volume *v, const double p[3])
+{
+    return trilinear(v, p, NULL);
+}
+
+void orc_tf_lookup(const orc_params *P, double val, double rgba[4])
+{
+    tf_lookup(P, val, rgba, NULL);
+}
+
+/* Ray setup probe: voxel-space origin/direction, t_in and the sample count of
+ * pixel (i, j).  Returns the sample count (0 on a miss). */
+int64_t orc_ray(const orc_volume *v, const orc_camera *c, const orc_params *P, int i, int j,
+                double ov[3], double dv[3], double *t_in)
+{
+    basis b = camera_basis(c);
+    ray_setup rs;
+    setup_ray(v, c, &b, P, i, j, &rs);
+    for (int a = 0; a < 3; ++a) { ov[a] = rs.ov[a]; dv[a] = rs.dv[a]; }
+    *t_in = rs.t_in;
+    return rs.n;
+}
