@@ -1,0 +1,429 @@
+"""Benchmark: direct volume rendering, forward + backward, on synthetic HI-like
+cubes through the C ABI (libvr.so).
+
+Default workload (one "step"): a 1024^3 float32 HI-like cube (noise + 2000
+Gaussian blobs + 200 rotating-disk sources) resident in HBM as bricks; eight
+1920x1080 perspective orbit views rendered by ONE batched persistent launch
+(CUDA graph), step 1 voxel, early termination at opacity 0.99; then the
+adjoint of each view (table + voxel gradients, accumulated over the views)
+against a fixed seeded dL/dI.
+
+value = forward-composited samples of the 8 views / step time (Gsamples/s).
+Also reported: 1080p frames/s for fwd+bwd, forward-only rates (batched and
+the plain FP32 single-view vr_render form), pixel error against the FP64
+oracle on sampled rows, the roofline object of the dominant kernel, the
+oracle timed on the host cores, and the end-to-end rate with host buffers.
+
+--impl reference times the FP64 oracle (the only reference this method has)
+on a bounded sample of the same workload, on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import synth  # noqa: E402
+
+METRIC = "DVR Gsamples/s and 1080p fps fwd+bwd on 1 GB300 vs plain FP32 at stated px error"
+UNIT = "Gsamples/s"
+GATHER_BYTES_F32 = 8 * 4          # algorithmic bytes of one sample: 8 trilinear corners x 4 B
+
+
+def _env_int(name, default):
+    try:
+        return int(os.environ.get(name, default))
+    except ValueError:
+        return default
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d.get("hbm_gbs", 6800.0), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(prefix="clocks", suffix=".csv")
+            os.close(fd)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    mx = max(mx, float(parts[2]))
+                except ValueError:
+                    continue
+                for n, v in zip(names, parts[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(n)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# Reference arm: the FP64 oracle on the host cores
+# ---------------------------------------------------------------------------
+
+def oracle_step(host_cube, cams, tf_np, pre, rows_per_view, grad_rows):
+    """One bounded oracle step: forward + backward (table gradient) of
+    ``rows_per_view`` rows of every view.  Returns (samples, seconds)."""
+    import oracle
+    t0 = time.perf_counter()
+    samples = 0
+    for vi, cam in enumerate(cams):
+        H = cam["height"]
+        for q in range(rows_per_view):
+            r = (H // 2 - rows_per_view // 2 + q + 37 * vi) % H
+            o = oracle.render(host_cube, cam, tf_np, synth.TF_VMIN, synth.TF_VMAX, pre["step"], pre["ert"],
+                              rows=(r, r + 1))
+            samples += int(o["n_used"][r].sum())
+            g = np.zeros((H, cam["width"], 4))
+            g[r] = grad_rows[q % len(grad_rows)]
+            oracle.render_backward(host_cube, cam, tf_np, synth.TF_VMIN, synth.TF_VMAX, pre["step"], g,
+                                   ert=pre["ert"], want_vox=False, rows=(r, r + 1))
+    return samples, time.perf_counter() - t0
+
+
+def adaptive_rows(host_cube, cams, tf_np, pre, grad_rows, target_s):
+    """Rows per view so that one oracle step takes about target_s seconds."""
+    _, t1 = oracle_step(host_cube, cams, tf_np, pre, 1, grad_rows)
+    return int(min(64, max(1, round(target_s / max(t1, 1e-3)))))
+
+
+def make_cube(pre, device):
+    return synth.hi_cube(pre["dims"], pre["n_blobs"], pre["n_disks"], pre["seed"], device=device)
+
+
+def run_reference(args, rank):
+    if rank != 0:
+        return 0
+    import oracle
+    import torch
+    oracle.build()
+    pre = synth.preset_scale_1024()
+    dev = "cuda" if torch.cuda.is_available() else "cpu"
+    host = make_cube(pre, dev).cpu().numpy()
+    tf_np = synth.tf_ramp(256)
+    cams = pre["cameras"]
+    rng = np.random.default_rng(0)
+    grad_rows = [rng.normal(size=(cams[0]["width"], 4)) for _ in range(4)]
+    rows = adaptive_rows(host, cams, tf_np, pre, grad_rows, target_s=4.0)
+    for _ in range(args.warmup):
+        oracle_step(host, cams, tf_np, pre, rows, grad_rows)
+    tot_s, tot_t = 0, 0.0
+    for _ in range(args.steps):
+        s, t = oracle_step(host, cams, tf_np, pre, rows, grad_rows)
+        tot_s += s
+        tot_t += t
+    value = tot_s / tot_t / 1e9
+    cores = os.cpu_count()
+    sample = ("per step: %d row(s) of each of the 8 views (1920 rays/row), FP64 forward + backward "
+              "(table gradient; the voxel gradient is not computed)" % rows)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "scale_1024 (sampled rows)", "views": 8, "image": [1920, 1080]},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# Our arm
+# ---------------------------------------------------------------------------
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+    import paper_1211_4896_gb300 as P
+    from paper_1211_4896_gb300 import _lib as L
+
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+
+    pre = synth.preset_scale_1024()
+    cube = make_cube(pre, dev)
+    vol = P.Volume(cube, "f32")
+    host_cube = cube.cpu().numpy() if rank == 0 else None
+    del cube
+    torch.cuda.empty_cache()
+    cams = pre["cameras"]
+    nv = len(cams)
+    H, W = cams[0]["height"], cams[0]["width"]
+    tf_np = synth.tf_ramp(256)
+    tf = torch.from_numpy(tf_np).to(dev)
+    vmin, vmax, step, ert = synth.TF_VMIN, synth.TF_VMAX, pre["step"], pre["ert"]
+    outs = [torch.empty((H, W, 4), device=dev) for _ in range(nv)]
+    nss = [torch.empty((H, W), device=dev, dtype=torch.int32) for _ in range(nv)]
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(1234)
+    grads = [torch.randn((H, W, 4), device=dev, generator=gen) for _ in range(nv)]
+    grad_tf = torch.empty((256, 4), device=dev, dtype=torch.float64)
+    nz, ny, nx = vol.shape
+    grad_vox = torch.empty((nz, ny, nx), device=dev, dtype=torch.float32)
+    stream = torch.cuda.current_stream()
+    s_ptr = int(stream.cuda_stream)
+
+    jobs = [dict(vol=vol, cam=c, tf=tf, vmin=vmin, vmax=vmax, step=step, ert=ert, out=o, nsamples=n)
+            for c, o, n in zip(cams, outs, nss)]
+    cjobs = P.render_batched(jobs, use_graph=True)          # builds the plan + graph
+    opts = L.vr_batch_opts(1, 8, 4, 0)
+    ccams = [L.make_camera(c) for c in cams]
+    cpar = L.make_params(tf.data_ptr(), 256, vmin, vmax, step, ert)
+    ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+
+    def fwd():
+        L.vr_render_batched(cjobs, opts, s_ptr)
+
+    def bwd(v, acc):
+        L.vr_render_backward(vol.handle, ccams[v], cpar, outs[v].data_ptr(), nss[v].data_ptr(), grads[v].data_ptr(),
+                             grad_tf.data_ptr(), grad_vox.data_ptr(), L.VR_GRAD_ACCUMULATE if acc else 0, s_ptr)
+
+    fwd_ev, bwd_ev = [], []
+
+    def step_fn(record):
+        if record:
+            e0, e1 = ev(), ev()
+            e0.record(stream)
+        fwd()
+        if record:
+            e1.record(stream)
+            fwd_ev.append((e0, e1))
+        for v in range(nv):
+            if record:
+                b0, b1 = ev(), ev()
+                b0.record(stream)
+            bwd(v, v > 0)
+            if record:
+                b1.record(stream)
+                bwd_ev.append((b0, b1))
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        step_fn(False)
+    torch.cuda.synchronize()
+    samples_per_step = int(sum(int(n.sum().item()) for n in nss))
+
+    clocks = ClockSampler(local_rank)
+    barrier()
+    clocks.start()
+    t_start, t_end = ev(), ev()
+    t_start.record(stream)
+    for _ in range(args.steps):
+        step_fn(True)
+    t_end.record(stream)
+    barrier()
+    clk = clocks.stop()
+    ms = t_start.elapsed_time(t_end) / args.steps
+    fwd_ms = statistics.mean(a.elapsed_time(b) for a, b in fwd_ev)
+    bwd_ms = statistics.mean(a.elapsed_time(b) for a, b in bwd_ev)           # per view
+    ms_max = ms
+    if dist is not None:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_max = float(t.item())
+    value = samples_per_step * world / (ms_max * 1e-3) / 1e9
+
+    # ---- forward-only rates (batched graph and plain single-view form) -------------
+    e0, e1 = ev(), ev()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    reps = max(3, args.steps)
+    for _ in range(reps):
+        fwd()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    fwd_only_ms = e0.elapsed_time(e1) / reps
+    view_ms = []
+    for v in range(nv):
+        a, b = ev(), ev()
+        L.vr_render(vol.handle, ccams[v], cpar, outs[v].data_ptr(), nss[v].data_ptr(), s_ptr)   # warm
+        a.record(stream)
+        for _ in range(3):
+            L.vr_render(vol.handle, ccams[v], cpar, outs[v].data_ptr(), nss[v].data_ptr(), s_ptr)
+        b.record(stream)
+        torch.cuda.synchronize()
+        view_ms.append(a.elapsed_time(b) / 3)
+    plain_ms = sum(view_ms)
+    p75 = float(np.percentile(view_ms, 75))
+
+    # ---- end to end through the C ABI with host buffers ------------------------------
+    pin_tf = torch.from_numpy(tf_np).pin_memory()
+    pin_g = [g.cpu().pin_memory() for g in grads]
+    pin_out = [torch.empty((H, W, 4), pin_memory=True) for _ in range(nv)]
+    pin_gtf = torch.empty((256, 4), dtype=torch.float64, pin_memory=True)
+    h2d = pin_tf.numel() * 4 + sum(g.numel() * 4 for g in pin_g)
+    d2h = sum(o.numel() * 4 for o in pin_out) + pin_gtf.numel() * 8
+
+    def e2e_step():
+        tf.copy_(pin_tf, non_blocking=True)
+        for g, pg in zip(grads, pin_g):
+            g.copy_(pg, non_blocking=True)
+        fwd()
+        for v in range(nv):
+            bwd(v, v > 0)
+        for o, po in zip(outs, pin_out):
+            po.copy_(o, non_blocking=True)
+        pin_gtf.copy_(grad_tf, non_blocking=True)
+
+    e2e_step()
+    barrier()
+    a, b = ev(), ev()
+    a.record(stream)
+    for _ in range(args.steps):
+        e2e_step()
+    b.record(stream)
+    barrier()
+    e2e_ms = a.elapsed_time(b) / args.steps
+    e2e_value = samples_per_step * world / (e2e_ms * 1e-3) / 1e9
+
+    # ---- pixel error against the FP64 oracle on sampled rows (view 0) ------------------
+    px = None
+    cpu = None
+    if rank == 0:
+        import oracle
+        oracle.build()
+        fwd()
+        torch.cuda.synchronize()
+        img0, ns0 = outs[0].cpu().numpy().astype(np.float64), nss[0].cpu().numpy()
+        rows = [H // 2 - 100, H // 2, H // 2 + 100]
+        errs, excl, checked = [], 0, 0
+        for r in rows:
+            o = oracle.render(host_cube, cams[0], tf_np, vmin, vmax, step, ert, rows=(r, r + 1))
+            same = ns0[r] == o["n_used"][r]
+            excl += int((~same).sum())
+            checked += int(same.sum())
+            errs.append(np.abs(img0[r] - o["rgba"][r])[same])
+        e = np.concatenate(errs)
+        px = {"max_abs": float(e.max()), "mean_abs": float(e.mean()), "pixels": checked,
+              "excluded_ties": excl, "against": "FP64 oracle, rows %s of view 0" % rows}
+        # ---- CPU baseline: the oracle on a bounded sample -------------------------------
+        rng = np.random.default_rng(0)
+        grad_rows = [rng.normal(size=(W, 4)) for _ in range(4)]
+        nrows = adaptive_rows(host_cube, cams, tf_np, pre, grad_rows, target_s=12.0)
+        s, t = oracle_step(host_cube, cams, tf_np, pre, nrows, grad_rows)
+        cpu = {"value": s / t / 1e9, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+               "sample": "%d row(s) of each of the 8 views (1920 rays per row), FP64 forward + backward "
+                         "(table gradient only), %d composited samples in %.1f s" % (nrows, s, t)}
+
+    # ---- roofline of the dominant kernel ---------------------------------------------
+    peak, peak_kind = measured_peaks()
+    bwd_total = bwd_ms * nv
+    if bwd_total >= fwd_ms:
+        dom, dom_ms, per = "bwd_kernel (+ FP64 table-gradient reduce), per view", bwd_ms, samples_per_step / nv
+    else:
+        dom, dom_ms, per = "batched_kernel (8 views, one launch)", fwd_ms, samples_per_step
+    achieved = per * GATHER_BYTES_F32 / (dom_ms * 1e-3) / 1e9
+    roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "traffic": None, "peak_source": peak_kind,
+            "per_unit": "8 x 4 B trilinear gathers per composited sample"}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "scale_1024: 1024^3 f32 HI-like cube (noise + 2000 blobs + 200 disks), "
+                                   "8 perspective orbit views at 1920x1080, step 1 voxel, ERT 0.99; "
+                                   "fwd = one batched graph launch of the 8 views, bwd = table + voxel "
+                                   "gradients per view (accumulated)",
+                       "views": nv, "image": [W, H], "samples_per_step": samples_per_step,
+                       "l2": "inputs larger than L2 (bricked cube %.2f GB)" % (vol.info["bytes"] / 1e9),
+                       "parallelism": "views replicated per GPU" if world > 1 else "1 GPU"},
+            "fps_fwd_bwd": nv * world / (ms_max * 1e-3),
+            "fwd": {"batched_gsamples_per_s": samples_per_step / (fwd_only_ms * 1e-3) / 1e9,
+                    "batched_ms_8_views": fwd_only_ms,
+                    "plain_fp32_single_view_gsamples_per_s": samples_per_step / (plain_ms * 1e-3) / 1e9,
+                    "plain_fp32_view_ms_p75": p75, "fps_p75": 1e3 / p75},
+            "bwd": {"ms_per_view": bwd_ms, "bwd_over_fwd": bwd_total / fwd_ms},
+            "px_err": px, "roofline": roof, "cpu_baseline": cpu,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "gpu_launches": args.steps * (1 + 2 * nv), "clocks": clk}
+    if rank == 0:
+        print(json.dumps(line))
+    vol.close()
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    rank = _env_int("RANK", 0)
+    world = _env_int("WORLD_SIZE", 1)
+    local_rank = _env_int("LOCAL_RANK", 0)
+    if args.impl == "reference":
+        return run_reference(args, rank)
+    from paper_1211_4896_gb300 import build as B
+    B.build()
+    return run_ours(args, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

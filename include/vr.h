@@ -1,0 +1,218 @@
+/*
+ * vr.h -- C ABI of the GB300 direct-volume-rendering library (libvr.so).
+ *
+ * Direct volume rendering of a 3D float image (a radio spectral cube, axes
+ * RA x Dec x frequency) by ray casting: each pixel's ray is clipped to the
+ * volume box, sampled at a constant step with trilinear interpolation, every
+ * sample is mapped through a 1D RGBA transfer function, and the samples are
+ * composited front to back with optional early ray termination.
+ *
+ * Method: Hassan, Fluke, Barnes & Kilborn (2012), "Tera-scale astronomical
+ * data analysis and visualization": Section 3.3 (transfer functions: the
+ * data range is partitioned into levels, each with a colour and an opacity in
+ * [0,1]), Section 3.4 (front-to-back composition of colour and opacity), and
+ * Section 4.4 (constant-step samples with trilinear interpolation).  Early ray
+ * termination, the adjoint pass and the batched launch are extensions that
+ * the paper does not describe.
+ *
+ * Conventions shared by every entry point
+ *   - Pointers named dev_* are CUDA device pointers owned by the caller.  The
+ *     library owns only what it allocates inside a vr_volume_t.
+ *   - Every call that takes `cuda_stream` (a cudaStream_t, NULL = legacy
+ *     default stream) only enqueues work on that stream and returns; nothing
+ *     is synchronised except in vr_volume_create / vr_volume_destroy.
+ *   - Arguments are validated on the host before anything is enqueued; an
+ *     invalid call returns a negative vr_status, enqueues nothing, and sets a
+ *     thread-local message readable with vr_last_error().
+ *   - A volume handle must not be used by two calls that run concurrently on
+ *     different streams (its work counters and scratch are per handle), and
+ *     must not be destroyed while work that uses it is in flight.
+ *   - Geometry: voxel (x, y, z) is at world position origin + (x, y, z) *
+ *     spacing; the box is the closed [0, n-1] per axis (voxel centres at
+ *     integer indices).  Dense cubes are x-fastest (x = RA, then y = Dec,
+ *     then z = frequency, the FITS axis order).
+ *   - Images are row-major float32 RGBA, H rows of W pixels, row 0 at the
+ *     top (+up), straight (not premultiplied) colour.
+ */
+#ifndef VR_H
+#define VR_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    VR_OK = 0,
+    VR_ERR_INVALID_ARG = -1,   /* bad pointer, size, dtype or parameter */
+    VR_ERR_UNSUPPORTED = -2,   /* valid but not implemented for this combination */
+    VR_ERR_OOM = -3,           /* a device allocation failed */
+    VR_ERR_CUDA = -4,          /* a CUDA runtime call failed (message has the CUDA error) */
+    VR_ERR_TIMEOUT = -5,       /* a bounded device-side wait gave up */
+    VR_ERR_INTERNAL = -6
+} vr_status;
+
+typedef enum { VR_F32 = 0, VR_F16 = 1, VR_BF16 = 2 } vr_dtype;
+
+enum { VR_CAMERA_ORTHO = 0, VR_CAMERA_PERSPECTIVE = 1 };
+enum { VR_FILTER_SOFTWARE = 0, VR_FILTER_TEXTURE = 1 };
+
+typedef struct vr_volume *vr_volume_t;   /* opaque, library-owned */
+
+/* Camera.  Basis: f = normalize(forward), r = normalize(f x up), u = r x f.
+ * Pixel (i, j) has screen coordinates sx = 2 (i + 1/2)/W - 1 and
+ * sy = 1 - 2 (j + 1/2)/H, aspect = W/H.
+ *   orthographic: origin eye + sx (ortho_height/2) aspect r + sy (ortho_height/2) u,
+ *                 direction f, no near clip;
+ *   perspective:  origin eye, direction normalize(f + sx tan(fov/2) aspect r
+ *                 + sy tan(fov/2) u), samples only at t >= 0.
+ * The user controls the viewport this way (Section 3.1 of the paper). */
+typedef struct {
+    int kind;                 /* VR_CAMERA_ORTHO or VR_CAMERA_PERSPECTIVE */
+    double eye[3];            /* world coordinates */
+    double forward[3];        /* need not be unit length; must not be parallel to up */
+    double up[3];
+    double fov_y_deg;         /* perspective: full vertical field of view, (0, 180) */
+    double ortho_height;      /* orthographic: world height of the image, > 0 */
+    int width, height;        /* image size in pixels, each in [1, 32768] */
+} vr_camera;
+
+/* Rendering parameters (Section 3.3: the transfer function maps each data
+ * level to a colour and an opacity in [0, 1]).  Sample value v maps to
+ * u = clamp((v - vmin)/(vmax - vmin), 0, 1) (K - 1); entries floor(u) and
+ * floor(u)+1 are blended linearly (the last interval is closed).  Samples are
+ * at t_in + (k + 1/2) step for k = 0, 1, ... while <= t_out; compositing is
+ * C += T a rgb, T *= 1 - a, stopping after the sample at which 1 - T >=
+ * ert_threshold (a value > 1 disables early termination).  The pixel is
+ * (C + T bg.rgb, 1 - T + T bg.a). */
+typedef struct {
+    const float *tf_rgba;     /* device, K x 4 float32 RGBA, 16-byte aligned */
+    int tf_size;              /* K, in [2, 4096] */
+    float vmin, vmax;         /* value range mapped onto the table, vmax > vmin */
+    float step;               /* world units along the unit ray, > 0 */
+    float ert_threshold;      /* early-termination opacity in (0, 1]; > 1 disables */
+    float bg_rgba[4];         /* background, straight RGBA */
+    int filter;               /* VR_FILTER_SOFTWARE (FP32 trilinear, the reference path) or
+                                 VR_FILTER_TEXTURE (hardware filter, 8-bit fractional weights;
+                                 float32/float16 storage only) */
+} vr_params;
+
+typedef struct {
+    int64_t dims[3];
+    vr_dtype store_dtype;
+    int brick;                /* B: bricks of B^3 cells stored with a +1 apron, (B+1)^3 voxels */
+    int64_t bricks[3];        /* bricks per axis */
+    int64_t bytes;            /* device bytes held by the bricked copy */
+} vr_volume_info_t;
+
+/* ------------------------------------------------------------------------
+ * Volume residency (Section 2: the whole data set is loaded into GPU memory
+ * once and stays there; the paper keeps it in texture memory, this library in
+ * a bricked HBM layout).
+ *
+ * Copies the dense cube dev_cube (src_dtype, dims = {nx, ny, nz}, each >= 2,
+ * x fastest) into a bricked copy in store_dtype: bricks of B^3 cells, each
+ * stored as (B+1)^3 voxels so that all 8 trilinear corners of any cell lie in
+ * one brick.  F32 -> F16/BF16 rounds to nearest even.  brick = 0 picks 32;
+ * otherwise 16, 32 or 64.  origin/spacing may be NULL (0 and 1).  The
+ * caller keeps dev_cube; the call synchronises `cuda_stream` before returning
+ * the handle in *out.  Errors: INVALID_ARG, OOM, CUDA.
+ * ---------------------------------------------------------------------- */
+vr_status vr_volume_create(const void *dev_cube, vr_dtype src_dtype, vr_dtype store_dtype,
+                           const int64_t dims[3], const double origin[3], const double spacing[3],
+                           int brick, void *cuda_stream, vr_volume_t *out);
+
+/* Re-bricks new voxel values (same dims and src_dtype as at creation) into an
+ * existing handle, asynchronously on cuda_stream (e.g. after a gradient step
+ * on the voxels). */
+vr_status vr_volume_update(vr_volume_t vol, const void *dev_cube, vr_dtype src_dtype, void *cuda_stream);
+
+/* Frees the handle and its device memory (synchronises the device). NULL is a no-op. */
+vr_status vr_volume_destroy(vr_volume_t vol);
+
+vr_status vr_volume_info(vr_volume_t vol, vr_volume_info_t *out);
+
+/* ------------------------------------------------------------------------
+ * Forward render (Sections 3.3-3.4 and 4.4).
+ *
+ * Writes W*H float32 RGBA pixels to dev_rgba_out (16-byte aligned) and, when
+ * dev_nsamples_out is not NULL, the number of samples composited per pixel
+ * (after early termination; 0 when the ray misses the box).  The backward
+ * pass needs both.  Errors: INVALID_ARG, UNSUPPORTED (texture filter on
+ * bfloat16 storage), OOM (first texture-filter call), CUDA.
+ * ---------------------------------------------------------------------- */
+vr_status vr_render(vr_volume_t vol, const vr_camera *cam, const vr_params *params, float *dev_rgba_out,
+                    uint32_t *dev_nsamples_out, void *cuda_stream);
+
+/* ------------------------------------------------------------------------
+ * Adjoint of vr_render (not in the paper): gradients of a scalar loss L with
+ * respect to the transfer-function table and the voxel values, given
+ * dev_grad_rgba = dL/d(image) (W*H*4 float32).
+ *
+ * Each ray is re-marched front to back from the forward's stored image and
+ * sample count (recomputing per-sample state instead of storing it): the
+ * transmittance behind sample k is recovered from the final colour and
+ * transmittance, T_final = (1 - alpha_out)/(1 - bg.a), so bg.a must be < 1.
+ * Early-termination decisions of the forward are kept (dev_nsamples).
+ *   dev_grad_tf  (K*4 float64): per-block FP32 partial sums, one final
+ *                cross-block sum in FP64.
+ *   dev_grad_vox (nx*ny*nz float32 dense, x fastest) or NULL: float atomics
+ *                (summation order is not deterministic).
+ * Both are overwritten, or added to when flags has VR_GRAD_ACCUMULATE (a
+ * loss summed over several views: call once per view).
+ * Only software filtering is differentiable.  Errors: INVALID_ARG,
+ * UNSUPPORTED (texture filter, bg.a >= 1), OOM, CUDA.
+ * ---------------------------------------------------------------------- */
+enum { VR_GRAD_ACCUMULATE = 1 };
+
+vr_status vr_render_backward(vr_volume_t vol, const vr_camera *cam, const vr_params *params,
+                             const float *dev_rgba, const uint32_t *dev_nsamples,
+                             const float *dev_grad_rgba, double *dev_grad_tf, float *dev_grad_vox,
+                             unsigned flags, void *cuda_stream);
+
+/* ------------------------------------------------------------------------
+ * Batched render (not in the paper; its "many smaller cubes" future-work
+ * item motivates it): n jobs, each with its own volume, camera, parameters
+ * and output, rendered by ONE persistent kernel launch whose CTAs pull ray
+ * tiles of all jobs from a shared work queue.  Results equal n vr_render
+ * calls.  Software filter only.
+ * ---------------------------------------------------------------------- */
+typedef struct {
+    vr_volume_t vol;
+    vr_camera cam;
+    vr_params params;
+    float *dev_rgba_out;
+    uint32_t *dev_nsamples_out;   /* may be NULL */
+} vr_job;
+
+typedef struct {
+    int use_graph;            /* 1: capture the launch in a CUDA graph on first use and replay it
+                                 while the job list is unchanged (same pointers and parameters) */
+    int tile_w, tile_h;       /* ray tile of one warp: tile_w * tile_h == 32; 0 = 8 x 4 */
+    int ctas_per_sm;          /* persistent CTAs per SM; 0 = occupancy limit */
+} vr_batch_opts;
+
+/* All volumes of one batch must share store dtype and brick size
+ * (UNSUPPORTED otherwise).  A job list is keyed by its bytes: the first call
+ * with a new list uploads its descriptors (synchronising cuda_stream); with
+ * use_graph the first call also captures the launch.  Later calls with the
+ * same list only launch.  Errors: INVALID_ARG, UNSUPPORTED, OOM, CUDA. */
+vr_status vr_render_batched(const vr_job *jobs, int n, const vr_batch_opts *opts, void *cuda_stream);
+
+/* Times candidate tile shapes and CTA counts for this job list (it renders
+ * the jobs several times on cuda_stream and synchronises it) and writes the
+ * fastest into *best.  best->use_graph is left unchanged. */
+vr_status vr_autotune_batched(const vr_job *jobs, int n, vr_batch_opts *best, void *cuda_stream);
+
+/* Human-readable message of the last failed call on this thread ("" if none). */
+const char *vr_last_error(void);
+
+/* Library version string. */
+const char *vr_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* VR_H */

@@ -64,8 +64,8 @@ def lib():
             L.orc_render.argtypes = [P(Volume), P(Camera), P(Params), C.c_int, C.c_int, C.c_void_p,
                                      C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]
             L.orc_render.restype = C.c_int
-            L.orc_render_backward.argtypes = [P(Volume), P(Camera), P(Params), C.c_void_p, C.c_void_p,
-                                              C.c_void_p, C.c_int]
+            L.orc_render_backward.argtypes = [P(Volume), P(Camera), P(Params), C.c_int, C.c_int, C.c_void_p,
+                                              C.c_void_p, C.c_void_p, C.c_int]
             L.orc_render_backward.restype = C.c_int
             L.orc_trilinear.argtypes = [P(Volume), P(C.c_double * 3)]
             L.orc_trilinear.restype = C.c_double
@@ -132,7 +132,7 @@ def render(cube, cam, tf, vmin, vmax, step, ert=2.0, bg=(0.0, 0.0, 0.0, 0.0), or
 
 def render_backward(cube, cam, tf, vmin, vmax, step, grad_rgba, ert=2.0, bg=(0.0, 0.0, 0.0, 0.0),
                     origin=(0.0, 0.0, 0.0), spacing=(1.0, 1.0, 1.0), want_vox=True, nthreads=None,
-                    bits=None):
+                    bits=None, rows=None):
     """FP64 gradients (grad_tf (K,4), grad_vox (nz,ny,nx) or None) of
     L given dL/dI = grad_rgba (H,W,4)."""
     c = _Call(cube, cam, tf, vmin, vmax, step, ert, bg, origin, spacing, bits)
@@ -142,7 +142,8 @@ def render_backward(cube, cam, tf, vmin, vmax, step, grad_rgba, ert=2.0, bg=(0.0
     gtf = np.zeros(c.tf.shape, dtype=np.float64)
     gvox = np.zeros(c.cube.shape, dtype=np.float64) if want_vox else None
     nt = nthreads or os.cpu_count() or 1
-    rc = lib().orc_render_backward(C.byref(c.vol), C.byref(c.cam), C.byref(c.par), g.ctypes.data,
+    r0, r1 = rows if rows is not None else (0, c.cam.height)
+    rc = lib().orc_render_backward(C.byref(c.vol), C.byref(c.cam), C.byref(c.par), int(r0), int(r1), g.ctypes.data,
                                    gtf.ctypes.data, gvox.ctypes.data if gvox is not None else None, int(nt))
     if rc != 0:
         raise ValueError("orc_render_backward failed (%d)" % rc)

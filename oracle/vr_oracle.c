@@ -345,17 +345,18 @@ typedef struct {
     double *grad_vox;         /* private nx*ny*nz or NULL */
 } job;
 
+/* Pixels of rows [row0, row1) are dealt to the threads round-robin. */
 static void *fwd_worker(void *arg)
 {
     job *J = (job *)arg;
     int W = J->c->width;
-    for (int j = J->row0 + J->first; j < J->row1; j += J->stride)
-        for (int i = 0; i < W; ++i) {
-            int64_t px = (int64_t)j * W + i;
-            render_pixel(J->v, J->c, &J->b, J->P, i, j, J->rgba + 4 * px,
-                         J->n_used ? J->n_used + px : NULL, J->margin_n ? J->margin_n + px : NULL,
-                         J->margin_ert ? J->margin_ert + px : NULL);
-        }
+    int64_t first = (int64_t)J->row0 * W, last = (int64_t)J->row1 * W;
+    for (int64_t px = first + J->first; px < last; px += J->stride) {
+        int j = (int)(px / W), i = (int)(px % W);
+        render_pixel(J->v, J->c, &J->b, J->P, i, j, J->rgba + 4 * px,
+                     J->n_used ? J->n_used + px : NULL, J->margin_n ? J->margin_n + px : NULL,
+                     J->margin_ert ? J->margin_ert + px : NULL);
+    }
     return NULL;
 }
 
@@ -491,17 +492,19 @@ static void *bwd_worker(void *arg)
     job *J = (job *)arg;
     stored_sample *buf = NULL;
     int64_t cap = 0;
-    for (int j = J->row0 + J->first; j < J->row1; j += J->stride)
-        for (int i = 0; i < J->c->width; ++i) backward_pixel(J, i, j, &buf, &cap);
+    int W = J->c->width;
+    int64_t first = (int64_t)J->row0 * W, last = (int64_t)J->row1 * W;
+    for (int64_t px = first + J->first; px < last; px += J->stride)
+        backward_pixel(J, (int)(px % W), (int)(px / W), &buf, &cap);
     free(buf);
     return NULL;
 }
 
 /* Gradients of L with respect to the K x 4 table and (optionally) the dense
- * voxels, given dL/dI (H*W*4).  Both outputs are overwritten.  Per-thread
+ * voxels, given dL/dI (H*W*4), over the pixels of rows [row0, row1).  Both outputs are overwritten.  Per-thread
  * partial sums are added in thread order, so the result is deterministic for
  * a given thread count. */
-int orc_render_backward(const orc_volume *v, const orc_camera *c, const orc_params *P,
+int orc_render_backward(const orc_volume *v, const orc_camera *c, const orc_params *P, int row0, int row1,
                         const double *grad_rgba, double *grad_tf, double *grad_vox, int nthreads)
 {
     if (check_args(v, c, P) || !grad_rgba || !grad_tf) return -1;
@@ -513,7 +516,9 @@ int orc_render_backward(const orc_volume *v, const orc_camera *c, const orc_para
     int rc = 0;
     for (int t = 0; t < nthreads; ++t) {
         jobs[t].v = v; jobs[t].c = c; jobs[t].P = P; jobs[t].b = b;
-        jobs[t].row0 = 0; jobs[t].row1 = c->height; jobs[t].stride = nthreads; jobs[t].first = t;
+        jobs[t].row0 = row0 < 0 ? 0 : row0;
+        jobs[t].row1 = row1 > c->height ? c->height : row1;
+        jobs[t].stride = nthreads; jobs[t].first = t;
         jobs[t].grad_rgba = grad_rgba;
         jobs[t].grad_tf = (double *)calloc((size_t)P->K * 4, sizeof(double));
         jobs[t].grad_vox = grad_vox ? (double *)calloc((size_t)nvox, sizeof(double)) : NULL;

@@ -1,0 +1,185 @@
+"""ctypes binding of libvr.so: one Python function per C entry point, same
+names, argument marshalling only (every step of the rendering runs in the
+library's CUDA kernels).  The structures mirror include/vr.h.
+
+The library is loaded from the package's ``_build`` folder; if it is missing
+an ImportError-like RuntimeError is raised -- there is no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libvr.so")
+
+VR_OK, VR_ERR_INVALID_ARG, VR_ERR_UNSUPPORTED, VR_ERR_OOM, VR_ERR_CUDA, VR_ERR_TIMEOUT, VR_ERR_INTERNAL = \
+    0, -1, -2, -3, -4, -5, -6
+VR_F32, VR_F16, VR_BF16 = 0, 1, 2
+VR_CAMERA_ORTHO, VR_CAMERA_PERSPECTIVE = 0, 1
+VR_FILTER_SOFTWARE, VR_FILTER_TEXTURE = 0, 1
+VR_GRAD_ACCUMULATE = 1
+
+STATUS_NAMES = {0: "VR_OK", -1: "VR_ERR_INVALID_ARG", -2: "VR_ERR_UNSUPPORTED", -3: "VR_ERR_OOM",
+                -4: "VR_ERR_CUDA", -5: "VR_ERR_TIMEOUT", -6: "VR_ERR_INTERNAL"}
+
+
+class vr_camera(C.Structure):
+    _fields_ = [("kind", C.c_int), ("eye", C.c_double * 3), ("forward", C.c_double * 3),
+                ("up", C.c_double * 3), ("fov_y_deg", C.c_double), ("ortho_height", C.c_double),
+                ("width", C.c_int), ("height", C.c_int)]
+
+
+class vr_params(C.Structure):
+    _fields_ = [("tf_rgba", C.c_void_p), ("tf_size", C.c_int), ("vmin", C.c_float), ("vmax", C.c_float),
+                ("step", C.c_float), ("ert_threshold", C.c_float), ("bg_rgba", C.c_float * 4),
+                ("filter", C.c_int)]
+
+
+class vr_volume_info_t(C.Structure):
+    _fields_ = [("dims", C.c_int64 * 3), ("store_dtype", C.c_int), ("brick", C.c_int),
+                ("bricks", C.c_int64 * 3), ("bytes", C.c_int64)]
+
+
+class vr_job(C.Structure):
+    _fields_ = [("vol", C.c_void_p), ("cam", vr_camera), ("params", vr_params),
+                ("dev_rgba_out", C.c_void_p), ("dev_nsamples_out", C.c_void_p)]
+
+
+class vr_batch_opts(C.Structure):
+    _fields_ = [("use_graph", C.c_int), ("tile_w", C.c_int), ("tile_h", C.c_int), ("ctas_per_sm", C.c_int)]
+
+
+# every symbol include/vr.h declares
+EXPORTS = ("vr_volume_create", "vr_volume_update", "vr_volume_destroy", "vr_volume_info", "vr_render",
+           "vr_render_backward", "vr_render_batched", "vr_autotune_batched", "vr_last_error", "vr_version")
+
+_lock = threading.Lock()
+_lib = None
+
+
+class VRError(RuntimeError):
+    def __init__(self, fn, status, msg):
+        super().__init__("%s failed: %s: %s" % (fn, STATUS_NAMES.get(status, status), msg))
+        self.status = status
+
+
+def load() -> C.CDLL:
+    """Loads libvr.so (building it first if the sources are newer and nvcc is
+    available).  Raises RuntimeError when it cannot be had."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libvr.so is not built (%s); run __graft_entry__.build() or "
+                               "python -m paper_1211_4896_gb300.build" % LIB_PATH)
+        L = C.CDLL(LIB_PATH)
+        P, vp = C.POINTER, C.c_void_p
+        L.vr_volume_create.argtypes = [vp, C.c_int, C.c_int, P(C.c_int64 * 3), P(C.c_double * 3),
+                                       P(C.c_double * 3), C.c_int, vp, P(vp)]
+        L.vr_volume_update.argtypes = [vp, vp, C.c_int, vp]
+        L.vr_volume_destroy.argtypes = [vp]
+        L.vr_volume_info.argtypes = [vp, P(vr_volume_info_t)]
+        L.vr_render.argtypes = [vp, P(vr_camera), P(vr_params), vp, vp, vp]
+        L.vr_render_backward.argtypes = [vp, P(vr_camera), P(vr_params), vp, vp, vp, vp, vp, C.c_uint, vp]
+        L.vr_render_batched.argtypes = [P(vr_job), C.c_int, P(vr_batch_opts), vp]
+        L.vr_autotune_batched.argtypes = [P(vr_job), C.c_int, P(vr_batch_opts), vp]
+        for name in ("vr_volume_create", "vr_volume_update", "vr_volume_destroy", "vr_volume_info", "vr_render",
+                     "vr_render_backward", "vr_render_batched", "vr_autotune_batched"):
+            getattr(L, name).restype = C.c_int
+        L.vr_last_error.argtypes = []
+        L.vr_last_error.restype = C.c_char_p
+        L.vr_version.argtypes = []
+        L.vr_version.restype = C.c_char_p
+        _lib = L
+        return L
+
+
+def last_error() -> str:
+    return load().vr_last_error().decode()
+
+
+def _check(fn: str, status: int):
+    if status != VR_OK:
+        raise VRError(fn, status, last_error())
+
+
+# ---------------------------------------------------------------------------
+# Struct builders
+# ---------------------------------------------------------------------------
+
+def make_camera(cam: dict) -> vr_camera:
+    return vr_camera(int(cam["kind"]), (C.c_double * 3)(*cam["eye"]), (C.c_double * 3)(*cam["forward"]),
+                     (C.c_double * 3)(*cam["up"]), float(cam.get("fov_y_deg", 0.0)),
+                     float(cam.get("ortho_height", 0.0)), int(cam["width"]), int(cam["height"]))
+
+
+def make_params(tf_ptr: int, K: int, vmin: float, vmax: float, step: float, ert: float = 2.0,
+                bg=(0.0, 0.0, 0.0, 0.0), filter: int = VR_FILTER_SOFTWARE) -> vr_params:
+    return vr_params(tf_ptr, int(K), float(vmin), float(vmax), float(step), float(ert), (C.c_float * 4)(*bg),
+                     int(filter))
+
+
+# ---------------------------------------------------------------------------
+# Entry points (same names as the C ABI)
+# ---------------------------------------------------------------------------
+
+def vr_volume_create(dev_cube: int, src_dtype: int, store_dtype: int, dims, origin=None, spacing=None,
+                     brick: int = 0, stream: int = 0) -> int:
+    L = load()
+    out = C.c_void_p()
+    d = (C.c_int64 * 3)(*dims)
+    o = (C.c_double * 3)(*origin) if origin is not None else None
+    s = (C.c_double * 3)(*spacing) if spacing is not None else None
+    _check("vr_volume_create", L.vr_volume_create(dev_cube, src_dtype, store_dtype, C.byref(d),
+                                                  C.byref(o) if o else None, C.byref(s) if s else None,
+                                                  int(brick), stream, C.byref(out)))
+    return out.value
+
+
+def vr_volume_update(vol: int, dev_cube: int, src_dtype: int, stream: int = 0):
+    _check("vr_volume_update", load().vr_volume_update(vol, dev_cube, src_dtype, stream))
+
+
+def vr_volume_destroy(vol: int):
+    _check("vr_volume_destroy", load().vr_volume_destroy(vol))
+
+
+def vr_volume_info(vol: int) -> dict:
+    info = vr_volume_info_t()
+    _check("vr_volume_info", load().vr_volume_info(vol, C.byref(info)))
+    return dict(dims=tuple(info.dims), store_dtype=info.store_dtype, brick=info.brick,
+                bricks=tuple(info.bricks), bytes=info.bytes)
+
+
+def vr_render(vol: int, cam: vr_camera, params: vr_params, dev_rgba_out: int, dev_nsamples_out: int | None,
+              stream: int = 0):
+    _check("vr_render", load().vr_render(vol, C.byref(cam), C.byref(params), dev_rgba_out, dev_nsamples_out,
+                                         stream))
+
+
+def vr_render_backward(vol: int, cam: vr_camera, params: vr_params, dev_rgba: int, dev_nsamples: int,
+                       dev_grad_rgba: int, dev_grad_tf: int, dev_grad_vox: int | None, flags: int = 0,
+                       stream: int = 0):
+    _check("vr_render_backward", load().vr_render_backward(vol, C.byref(cam), C.byref(params), dev_rgba,
+                                                           dev_nsamples, dev_grad_rgba, dev_grad_tf,
+                                                           dev_grad_vox, int(flags), stream))
+
+
+def vr_render_batched(jobs, opts: vr_batch_opts | None = None, stream: int = 0):
+    arr = (vr_job * len(jobs))(*jobs)
+    _check("vr_render_batched", load().vr_render_batched(arr, len(jobs), C.byref(opts) if opts else None,
+                                                         stream))
+
+
+def vr_autotune_batched(jobs, opts: vr_batch_opts | None = None, stream: int = 0) -> vr_batch_opts:
+    arr = (vr_job * len(jobs))(*jobs)
+    best = opts if opts is not None else vr_batch_opts(0, 0, 0, 0)
+    _check("vr_autotune_batched", load().vr_autotune_batched(arr, len(jobs), C.byref(best), stream))
+    return best
+
+
+def vr_version() -> str:
+    return load().vr_version().decode()

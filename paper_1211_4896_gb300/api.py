@@ -1,0 +1,144 @@
+"""Torch-facing helpers over the C ABI: device memory and streams come from
+PyTorch, the work is done by libvr.so.  Tensors must live on a CUDA device;
+nothing here computes on the CPU."""
+from __future__ import annotations
+
+import torch
+
+from . import _lib as L
+
+_DTYPES = {torch.float32: L.VR_F32, torch.float16: L.VR_F16, torch.bfloat16: L.VR_BF16}
+_NAMES = {"f32": L.VR_F32, "f16": L.VR_F16, "bf16": L.VR_BF16}
+
+
+def _stream(stream=None) -> int:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return int(s.cuda_stream)
+
+
+def _need_cuda(t: torch.Tensor, name: str):
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise ValueError("%s must be a CUDA tensor (there is no CPU path)" % name)
+    if not t.is_contiguous():
+        raise ValueError("%s must be contiguous" % name)
+
+
+class Volume:
+    """A bricked, device-resident copy of a dense cube (nz, ny, nx), x fastest."""
+
+    def __init__(self, cube: torch.Tensor, store_dtype="f32", brick: int = 0, origin=None, spacing=None,
+                 stream=None):
+        _need_cuda(cube, "cube")
+        if cube.dim() != 3 or cube.dtype not in _DTYPES:
+            raise ValueError("cube must be a 3D float32/float16/bfloat16 tensor (nz, ny, nx)")
+        self.src_dtype = _DTYPES[cube.dtype]
+        self.store_dtype = _NAMES[store_dtype] if isinstance(store_dtype, str) else int(store_dtype)
+        nz, ny, nx = cube.shape
+        self.dims = (nx, ny, nz)
+        self.shape = (nz, ny, nx)
+        self.device = cube.device
+        self.origin = tuple(origin) if origin is not None else (0.0, 0.0, 0.0)
+        self.spacing = tuple(spacing) if spacing is not None else (1.0, 1.0, 1.0)
+        with torch.cuda.device(cube.device):
+            self.handle = L.vr_volume_create(cube.data_ptr(), self.src_dtype, self.store_dtype, self.dims,
+                                             self.origin, self.spacing, brick, _stream(stream))
+        self.info = L.vr_volume_info(self.handle)
+
+    def update(self, cube: torch.Tensor, stream=None):
+        _need_cuda(cube, "cube")
+        if tuple(cube.shape) != self.shape or _DTYPES.get(cube.dtype) != self.src_dtype:
+            raise ValueError("update needs the same shape and dtype as at creation")
+        L.vr_volume_update(self.handle, cube.data_ptr(), self.src_dtype, _stream(stream))
+
+    def close(self):
+        if getattr(self, "handle", None):
+            L.vr_volume_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _params(tf: torch.Tensor, vmin, vmax, step, ert, bg, filter):
+    _need_cuda(tf, "tf")
+    if tf.dtype != torch.float32 or tf.dim() != 2 or tf.shape[1] != 4:
+        raise ValueError("tf must be a (K, 4) float32 CUDA tensor")
+    return L.make_params(tf.data_ptr(), tf.shape[0], vmin, vmax, step, ert, bg, filter)
+
+
+def render(vol: Volume, cam: dict, tf: torch.Tensor, vmin: float, vmax: float, step: float, ert: float = 2.0,
+           bg=(0.0, 0.0, 0.0, 0.0), filter: int = L.VR_FILTER_SOFTWARE, want_nsamples: bool = True,
+           out: torch.Tensor | None = None, nsamples: torch.Tensor | None = None, stream=None):
+    """Forward render; returns (rgba (H, W, 4) float32, nsamples (H, W) int32 or None)."""
+    H, W = int(cam["height"]), int(cam["width"])
+    if out is None:
+        out = torch.empty((H, W, 4), device=vol.device, dtype=torch.float32)
+    if want_nsamples and nsamples is None:
+        nsamples = torch.empty((H, W), device=vol.device, dtype=torch.int32)
+    p = _params(tf, vmin, vmax, step, ert, bg, filter)
+    L.vr_render(vol.handle, L.make_camera(cam), p, out.data_ptr(),
+                nsamples.data_ptr() if (want_nsamples and nsamples is not None) else None, _stream(stream))
+    return out, (nsamples if want_nsamples else None)
+
+
+def render_backward(vol: Volume, cam: dict, tf: torch.Tensor, vmin, vmax, step, rgba, nsamples, grad_rgba,
+                    ert: float = 2.0, bg=(0.0, 0.0, 0.0, 0.0), want_vox: bool = True, grad_tf=None, grad_vox=None,
+                    accumulate: bool = False, stream=None):
+    """Adjoint: returns (grad_tf (K, 4) float64, grad_vox (nz, ny, nx) float32 or None)."""
+    for t, n in ((rgba, "rgba"), (nsamples, "nsamples"), (grad_rgba, "grad_rgba")):
+        _need_cuda(t, n)
+    if grad_tf is None:
+        grad_tf = torch.empty(tuple(tf.shape), device=vol.device, dtype=torch.float64)
+    if want_vox and grad_vox is None:
+        grad_vox = torch.empty(vol.shape, device=vol.device, dtype=torch.float32)
+    p = _params(tf, vmin, vmax, step, ert, bg, L.VR_FILTER_SOFTWARE)
+    L.vr_render_backward(vol.handle, L.make_camera(cam), p, rgba.data_ptr(), nsamples.data_ptr(),
+                         grad_rgba.data_ptr(), grad_tf.data_ptr(), grad_vox.data_ptr() if want_vox else None,
+                         L.VR_GRAD_ACCUMULATE if accumulate else 0, _stream(stream))
+    return grad_tf, (grad_vox if want_vox else None)
+
+
+class RenderFunction(torch.autograd.Function):
+    """Differentiable render: inputs (cube, tf), output the RGBA image.  The
+    volume handle must hold the bricked copy of ``cube`` (call vol.update
+    after changing it).  Gradients come from the adjoint kernel."""
+
+    @staticmethod
+    def forward(ctx, cube, tf, vol, cam, vmin, vmax, step, ert, bg):
+        img, ns = render(vol, cam, tf.detach().contiguous(), vmin, vmax, step, ert, bg)
+        ctx.vol, ctx.cam, ctx.args = vol, cam, (vmin, vmax, step, ert, bg)
+        ctx.want_vox = cube.requires_grad
+        ctx.save_for_backward(tf.detach().contiguous(), img, ns)
+        return img
+
+    @staticmethod
+    def backward(ctx, grad_img):
+        tf, img, ns = ctx.saved_tensors
+        vmin, vmax, step, ert, bg = ctx.args
+        gtf, gvox = render_backward(ctx.vol, ctx.cam, tf, vmin, vmax, step, img, ns, grad_img.contiguous(),
+                                    ert, bg, want_vox=ctx.want_vox)
+        return (gvox if ctx.want_vox else None), gtf.to(tf.dtype), None, None, None, None, None, None, None
+
+
+def render_diff(cube, tf, vol, cam, vmin, vmax, step, ert=2.0, bg=(0.0, 0.0, 0.0, 0.0)):
+    return RenderFunction.apply(cube, tf, vol, cam, vmin, vmax, step, ert, bg)
+
+
+def render_batched(jobs, use_graph: bool = True, tile=(8, 4), ctas_per_sm: int = 0, stream=None,
+                   opts: L.vr_batch_opts | None = None):
+    """jobs: list of dicts with keys vol, cam, tf, vmin, vmax, step, ert, bg, out, nsamples (optional).
+    Renders all of them in one persistent launch."""
+    cj = []
+    for j in jobs:
+        p = _params(j["tf"], j["vmin"], j["vmax"], j["step"], j.get("ert", 2.0), j.get("bg", (0, 0, 0, 0)),
+                    L.VR_FILTER_SOFTWARE)
+        ns = j.get("nsamples")
+        cj.append(L.vr_job(j["vol"].handle, L.make_camera(j["cam"]), p, j["out"].data_ptr(),
+                           ns.data_ptr() if ns is not None else None))
+    if opts is None:
+        opts = L.vr_batch_opts(int(use_graph), int(tile[0]), int(tile[1]), int(ctas_per_sm))
+    L.vr_render_batched(cj, opts, _stream(stream))
+    return cj

@@ -1,0 +1,441 @@
+// vr_api.cpp -- host side of the C ABI declared in include/vr.h: argument
+// validation, volume handles, camera preparation and kernel dispatch.
+#include <cmath>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <string>
+
+#include "vr_internal.h"
+
+namespace vr {
+
+static thread_local std::string g_err;
+
+void set_error(const std::string &msg) { g_err = msg; }
+
+vr_status cuda_fail(cudaError_t e, const char *what)
+{
+    set_error(std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")");
+    return e == cudaErrorMemoryAllocation ? VR_ERR_OOM : VR_ERR_CUDA;
+}
+
+bool is_aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+static vr_status invalid(const std::string &msg)
+{
+    set_error(msg);
+    return VR_ERR_INVALID_ARG;
+}
+
+int sm_count()
+{
+    static std::mutex mu;
+    static int cached[64] = {0};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> g(mu);
+    if (dev < 0 || dev >= 64) return 1;
+    if (!cached[dev]) {
+        int n = 0;
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        cached[dev] = n > 0 ? n : 1;
+    }
+    return cached[dev];
+}
+
+static bool finite3(const double v[3]) { return std::isfinite(v[0]) && std::isfinite(v[1]) && std::isfinite(v[2]); }
+
+static double dot3(const double a[3], const double b[3]) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
+
+static void cross3(const double a[3], const double b[3], double o[3])
+{
+    o[0] = a[1] * b[2] - a[2] * b[1];
+    o[1] = a[2] * b[0] - a[0] * b[2];
+    o[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+// Checks of the camera that need no volume.
+static vr_status check_camera(const vr_camera *cam)
+{
+    if (!cam) return invalid("camera is NULL");
+    if (cam->kind != VR_CAMERA_ORTHO && cam->kind != VR_CAMERA_PERSPECTIVE)
+        return invalid("camera.kind must be VR_CAMERA_ORTHO (0) or VR_CAMERA_PERSPECTIVE (1)");
+    if (cam->width < 1 || cam->height < 1 || cam->width > 32768 || cam->height > 32768)
+        return invalid("camera.width and camera.height must be in [1, 32768]");
+    if (!finite3(cam->eye) || !finite3(cam->forward) || !finite3(cam->up))
+        return invalid("camera eye/forward/up must be finite");
+    const double fl = std::sqrt(dot3(cam->forward, cam->forward)), ul = std::sqrt(dot3(cam->up, cam->up));
+    if (!(fl > 0.0) || !(ul > 0.0)) return invalid("camera forward and up must be non-zero");
+    double x[3];
+    cross3(cam->forward, cam->up, x);
+    if (!(std::sqrt(dot3(x, x)) > 1e-9 * fl * ul)) return invalid("camera up must not be parallel to forward");
+    if (cam->kind == VR_CAMERA_PERSPECTIVE) {
+        if (!(cam->fov_y_deg > 0.0 && cam->fov_y_deg < 180.0))
+            return invalid("camera.fov_y_deg must be in (0, 180) for a perspective camera");
+    } else if (!(cam->ortho_height > 0.0) || !std::isfinite(cam->ortho_height)) {
+        return invalid("camera.ortho_height must be finite and > 0 for an orthographic camera");
+    }
+    return VR_OK;
+}
+
+static vr_status check_params(const vr_params *p)
+{
+    if (!p) return invalid("params is NULL");
+    if (!p->tf_rgba) return invalid("params.tf_rgba is NULL");
+    if (!is_aligned16(p->tf_rgba)) return invalid("params.tf_rgba must be 16-byte aligned");
+    if (p->tf_size < 2 || p->tf_size > 4096) return invalid("params.tf_size must be in [2, 4096]");
+    if (!std::isfinite(p->vmin) || !std::isfinite(p->vmax) || !(p->vmax > p->vmin))
+        return invalid("params.vmin/vmax must be finite with vmax > vmin");
+    if (!std::isfinite(p->step) || !(p->step > 0.0f)) return invalid("params.step must be finite and > 0");
+    if (!(p->ert_threshold > 0.0f)) return invalid("params.ert_threshold must be > 0 (values > 1 disable it)");
+    for (int c = 0; c < 4; ++c)
+        if (!std::isfinite(p->bg_rgba[c])) return invalid("params.bg_rgba must be finite");
+    if (p->filter != VR_FILTER_SOFTWARE && p->filter != VR_FILTER_TEXTURE)
+        return invalid("params.filter must be VR_FILTER_SOFTWARE (0) or VR_FILTER_TEXTURE (1)");
+    return VR_OK;
+}
+
+static vr_status check_volume(const vr_volume *vol)
+{
+    if (!vol) return invalid("volume handle is NULL");
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    if (dev != vol->device) return invalid("the volume lives on another device than the current one");
+    return VR_OK;
+}
+
+// Longest chord of the box in world units divided by the step must stay within
+// the range where the float sample index is exact.
+static vr_status check_step(const vr_volume *vol, const vr_params *p)
+{
+    double d2 = 0.0;
+    for (int a = 0; a < 3; ++a) {
+        const double e = (double)(vol->dims[a] - 1) * vol->spacing[a];
+        d2 += e * e;
+    }
+    if (std::sqrt(d2) / (double)p->step > 16777216.0) return invalid("params.step too small: > 2^24 samples per ray");
+    return VR_OK;
+}
+
+vr_status prepare_params(const vr_params *p, ParamDev *o)
+{
+    o->tf = reinterpret_cast<const float4 *>(p->tf_rgba);
+    o->K = p->tf_size;
+    o->vmin = p->vmin;
+    o->scale01 = (float)(1.0 / ((double)p->vmax - (double)p->vmin));
+    o->km1 = (float)(p->tf_size - 1);
+    o->step = p->step;
+    o->t_stop = (float)(1.0 - (double)p->ert_threshold);
+    o->bg = make_float4(p->bg_rgba[0], p->bg_rgba[1], p->bg_rgba[2], p->bg_rgba[3]);
+    return VR_OK;
+}
+
+vr_status prepare_camera(const vr_volume *vol, const vr_camera *cam, CamDev *o)
+{
+    double f[3] = {cam->forward[0], cam->forward[1], cam->forward[2]};
+    const double fl = std::sqrt(dot3(f, f));
+    for (double &x : f) x /= fl;
+    double r[3], u[3];
+    cross3(f, cam->up, r);
+    const double rl = std::sqrt(dot3(r, r));
+    for (double &x : r) x /= rl;
+    cross3(r, f, u);
+    const double W = cam->width, H = cam->height, aspect = W / H;
+    // anchor plane through the volume centre, perpendicular to f
+    double centre[3];
+    for (int a = 0; a < 3; ++a) centre[a] = vol->origin[a] + 0.5 * (double)(vol->dims[a] - 1) * vol->spacing[a];
+    double ce[3] = {centre[0] - cam->eye[0], centre[1] - cam->eye[1], centre[2] - cam->eye[2]};
+    const double D = dot3(ce, f);
+    double Q0[3], A[3], B[3], wa[3], wb[3];
+    // screen offsets: sx = hi * 2/W, sy = -hj * 2/H with hi = i - (W-1)/2, hj = j - (H-1)/2
+    if (cam->kind == VR_CAMERA_ORTHO) {
+        const double hh = 0.5 * cam->ortho_height;
+        for (int a = 0; a < 3; ++a) {
+            Q0[a] = cam->eye[a] + D * f[a];
+            A[a] = hh * aspect * r[a] * (2.0 / W);
+            B[a] = -hh * u[a] * (2.0 / H);
+            wa[a] = wb[a] = 0.0;
+        }
+    } else {
+        const double th = std::tan(cam->fov_y_deg * M_PI / 360.0);
+        for (int a = 0; a < 3; ++a) {
+            Q0[a] = cam->eye[a] + D * f[a];
+            wa[a] = th * aspect * r[a] * (2.0 / W);
+            wb[a] = -th * u[a] * (2.0 / H);
+            A[a] = D * wa[a];
+            B[a] = D * wb[a];
+        }
+    }
+    o->W = cam->width;
+    o->H = cam->height;
+    o->persp = cam->kind == VR_CAMERA_PERSPECTIVE;
+    o->q0 = make_float3((float)((Q0[0] - vol->origin[0]) / vol->spacing[0]),
+                        (float)((Q0[1] - vol->origin[1]) / vol->spacing[1]),
+                        (float)((Q0[2] - vol->origin[2]) / vol->spacing[2]));
+    o->qa = make_float3((float)(A[0] / vol->spacing[0]), (float)(A[1] / vol->spacing[1]),
+                        (float)(A[2] / vol->spacing[2]));
+    o->qb = make_float3((float)(B[0] / vol->spacing[0]), (float)(B[1] / vol->spacing[1]),
+                        (float)(B[2] / vol->spacing[2]));
+    o->wf = make_float3((float)f[0], (float)f[1], (float)f[2]);
+    o->wa = make_float3((float)wa[0], (float)wa[1], (float)wa[2]);
+    o->wb = make_float3((float)wb[0], (float)wb[1], (float)wb[2]);
+    o->inv_sp = make_float3((float)(1.0 / vol->spacing[0]), (float)(1.0 / vol->spacing[1]),
+                            (float)(1.0 / vol->spacing[2]));
+    o->dist = (float)D;
+    return VR_OK;
+}
+
+VolDev vol_dev(const vr_volume *vol)
+{
+    VolDev v;
+    v.data = vol->bricks;
+    v.nx = (int)vol->dims[0];
+    v.ny = (int)vol->dims[1];
+    v.nz = (int)vol->dims[2];
+    v.nbx = (int)vol->nb[0];
+    v.nby = (int)vol->nb[1];
+    v.nbz = (int)vol->nb[2];
+    v.log2b = vol->log2b;
+    v.stride = vol->stride;
+    return v;
+}
+
+vr_status next_counter(vr_volume *vol, unsigned **ctr)
+{
+    *ctr = vol->counters + vol->next_counter;
+    vol->next_counter = (vol->next_counter + 1) % vol->counter_slots;
+    return VR_OK;
+}
+
+vr_status validate_job(const vr_job *J, int q)
+{
+    const std::string where = "jobs[" + std::to_string(q) + "]: ";
+    vr_status st = check_camera(&J->cam);
+    if (st == VR_OK) st = check_params(&J->params);
+    if (st == VR_OK) st = check_volume(J->vol);
+    if (st == VR_OK) st = check_step(J->vol, &J->params);
+    if (st != VR_OK) set_error(where + g_err);
+    return st;
+}
+
+static size_t dtype_size(vr_dtype d) { return d == VR_F32 ? 4 : 2; }
+
+static void free_volume(vr_volume *vol)
+{
+    if (vol->tex) cudaDestroyTextureObject(vol->tex);
+    if (vol->tex_array) cudaFreeArray(vol->tex_array);
+    if (vol->bricks) cudaFree(vol->bricks);
+    if (vol->counters) cudaFree(vol->counters);
+    if (vol->partials) cudaFree(vol->partials);
+    delete vol;
+}
+
+}  // namespace vr
+
+using namespace vr;
+
+extern "C" {
+
+const char *vr_last_error(void) { return g_err.c_str(); }
+
+const char *vr_version(void) { return "vr-gb300 0.1 (sm_103a)"; }
+
+vr_status vr_volume_create(const void *dev_cube, vr_dtype src_dtype, vr_dtype store_dtype, const int64_t dims[3],
+                           const double origin[3], const double spacing[3], int brick, void *cuda_stream,
+                           vr_volume_t *out)
+{
+    g_err.clear();
+    if (!out) return invalid("out is NULL");
+    *out = nullptr;
+    if (!dev_cube) return invalid("dev_cube is NULL");
+    if (!dims) return invalid("dims is NULL");
+    if ((unsigned)src_dtype > VR_BF16 || (unsigned)store_dtype > VR_BF16)
+        return invalid("dtype must be VR_F32, VR_F16 or VR_BF16");
+    for (int a = 0; a < 3; ++a)
+        if (dims[a] < 2 || dims[a] > (1 << 20)) return invalid("each of dims must be in [2, 2^20]");
+    if (dims[0] * dims[1] > (int64_t)1 << 31) return invalid("nx * ny must be <= 2^31");
+    if (origin && !finite3(origin)) return invalid("origin must be finite");
+    if (spacing && !(spacing[0] > 0 && spacing[1] > 0 && spacing[2] > 0 && finite3(spacing)))
+        return invalid("spacing must be finite and > 0");
+    if (brick == 0) brick = 32;
+    int log2b = 0;
+    switch (brick) {
+    case 16: log2b = 4; break;
+    case 32: log2b = 5; break;
+    case 64: log2b = 6; break;
+    default: return invalid("brick must be 0 (auto), 16, 32 or 64");
+    }
+    vr_volume *vol = new (std::nothrow) vr_volume();
+    if (!vol) return invalid("host allocation failed");
+    for (int a = 0; a < 3; ++a) {
+        vol->dims[a] = dims[a];
+        vol->origin[a] = origin ? origin[a] : 0.0;
+        vol->spacing[a] = spacing ? spacing[a] : 1.0;
+        vol->nb[a] = (dims[a] - 1 + brick - 1) / brick;       // bricks cover cells [0, n-2]
+    }
+    vol->src_dtype = src_dtype;
+    vol->store_dtype = store_dtype;
+    vol->brick = brick;
+    vol->log2b = log2b;
+    const long long b1 = brick + 1;
+    vol->stride = (b1 * b1 * b1 + 63) / 64 * 64;                // 64-element (>=128 B) aligned bricks
+    const long long nbricks = vol->nb[0] * vol->nb[1] * vol->nb[2];
+    vol->bytes = (size_t)nbricks * (size_t)vol->stride * dtype_size(store_dtype);
+    cudaError_t e = cudaGetDevice(&vol->device);
+    if (e != cudaSuccess) { free_volume(vol); return cuda_fail(e, "cudaGetDevice"); }
+    e = cudaMalloc(&vol->bricks, vol->bytes);
+    if (e != cudaSuccess) {
+        vol->bricks = nullptr;
+        free_volume(vol);
+        cudaGetLastError();
+        set_error("vr_volume_create: cannot allocate " + std::to_string(vol->bytes) + " bytes of bricks");
+        return VR_ERR_OOM;
+    }
+    vol->counter_slots = 64;
+    e = cudaMalloc(&vol->counters, sizeof(unsigned) * vol->counter_slots);
+    if (e != cudaSuccess) { vol->counters = nullptr; free_volume(vol); return cuda_fail(e, "cudaMalloc(counters)"); }
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    e = cudaMemsetAsync(vol->counters, 0, sizeof(unsigned) * vol->counter_slots, s);
+    if (e == cudaSuccess) e = launch_brick(dev_cube, src_dtype, vol, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) { free_volume(vol); return cuda_fail(e, "vr_volume_create: bricking"); }
+    *out = vol;
+    return VR_OK;
+}
+
+vr_status vr_volume_update(vr_volume_t vol, const void *dev_cube, vr_dtype src_dtype, void *cuda_stream)
+{
+    g_err.clear();
+    vr_status st = check_volume(vol);
+    if (st != VR_OK) return st;
+    if (!dev_cube) return invalid("dev_cube is NULL");
+    if (src_dtype != vol->src_dtype) return invalid("src_dtype differs from the one given at creation");
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    if (vol->tex) {            // the hardware-filter copy is now stale
+        cudaStreamSynchronize(s);
+        cudaDestroyTextureObject(vol->tex);
+        cudaFreeArray(vol->tex_array);
+        vol->tex = 0;
+        vol->tex_array = nullptr;
+    }
+    cudaError_t e = launch_brick(dev_cube, src_dtype, vol, s);
+    if (e != cudaSuccess) return cuda_fail(e, "vr_volume_update");
+    return VR_OK;
+}
+
+vr_status vr_volume_destroy(vr_volume_t vol)
+{
+    g_err.clear();
+    if (!vol) return VR_OK;
+    cudaDeviceSynchronize();
+    purge_plans(vol);
+    free_volume(vol);
+    return VR_OK;
+}
+
+vr_status vr_volume_info(vr_volume_t vol, vr_volume_info_t *out)
+{
+    g_err.clear();
+    if (!vol) return invalid("volume handle is NULL");
+    if (!out) return invalid("out is NULL");
+    for (int a = 0; a < 3; ++a) {
+        out->dims[a] = vol->dims[a];
+        out->bricks[a] = vol->nb[a];
+    }
+    out->store_dtype = vol->store_dtype;
+    out->brick = vol->brick;
+    out->bytes = (int64_t)vol->bytes;
+    return VR_OK;
+}
+
+vr_status vr_render(vr_volume_t vol, const vr_camera *cam, const vr_params *params, float *dev_rgba_out,
+                    uint32_t *dev_nsamples_out, void *cuda_stream)
+{
+    g_err.clear();
+    vr_status st = check_camera(cam);
+    if (st == VR_OK) st = check_params(params);
+    if (st != VR_OK) return st;
+    if (!dev_rgba_out) return invalid("dev_rgba_out is NULL");
+    if (!is_aligned16(dev_rgba_out)) return invalid("dev_rgba_out must be 16-byte aligned");
+    if ((reinterpret_cast<uintptr_t>(dev_nsamples_out) & 3u) != 0) return invalid("dev_nsamples_out must be 4-byte aligned");
+    st = check_volume(vol);
+    if (st == VR_OK) st = check_step(vol, params);
+    if (st != VR_OK) return st;
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    CamDev c;
+    ParamDev p;
+    prepare_camera(vol, cam, &c);
+    prepare_params(params, &p);
+    unsigned *ctr;
+    next_counter(vol, &ctr);
+    cudaError_t e;
+    if (params->filter == VR_FILTER_TEXTURE) {
+        st = build_texture(vol, s);
+        if (st != VR_OK) return st;
+        e = launch_forward_texture(vol, c, p, reinterpret_cast<float4 *>(dev_rgba_out), dev_nsamples_out, ctr, s);
+    } else {
+        e = launch_forward(vol_dev(vol), vol->store_dtype, c, p, reinterpret_cast<float4 *>(dev_rgba_out),
+                           dev_nsamples_out, ctr, s);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "vr_render launch");
+    return VR_OK;
+}
+
+vr_status vr_render_backward(vr_volume_t vol, const vr_camera *cam, const vr_params *params, const float *dev_rgba,
+                             const uint32_t *dev_nsamples, const float *dev_grad_rgba, double *dev_grad_tf,
+                             float *dev_grad_vox, unsigned flags, void *cuda_stream)
+{
+    g_err.clear();
+    vr_status st = check_camera(cam);
+    if (st == VR_OK) st = check_params(params);
+    if (st != VR_OK) return st;
+    if (params->filter != VR_FILTER_SOFTWARE)
+        return (set_error("vr_render_backward: only the software filter is differentiable"), VR_ERR_UNSUPPORTED);
+    if (!(params->bg_rgba[3] < 1.0f))
+        return (set_error("vr_render_backward: bg alpha must be < 1 (T_final is recovered from the output alpha)"),
+                VR_ERR_UNSUPPORTED);
+    if (!dev_rgba || !dev_nsamples || !dev_grad_rgba || !dev_grad_tf)
+        return invalid("dev_rgba, dev_nsamples, dev_grad_rgba and dev_grad_tf must not be NULL");
+    if (!is_aligned16(dev_rgba) || !is_aligned16(dev_grad_rgba))
+        return invalid("dev_rgba and dev_grad_rgba must be 16-byte aligned");
+    if ((reinterpret_cast<uintptr_t>(dev_grad_tf) & 7u) != 0) return invalid("dev_grad_tf must be 8-byte aligned");
+    if (flags & ~(unsigned)VR_GRAD_ACCUMULATE) return invalid("flags: unknown bits");
+    if ((reinterpret_cast<uintptr_t>(dev_nsamples) & 3u) != 0 || (reinterpret_cast<uintptr_t>(dev_grad_vox) & 3u) != 0)
+        return invalid("dev_nsamples and dev_grad_vox must be 4-byte aligned");
+    st = check_volume(vol);
+    if (st == VR_OK) st = check_step(vol, params);
+    if (st != VR_OK) return st;
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    CamDev c;
+    ParamDev p;
+    prepare_camera(vol, cam, &c);
+    prepare_params(params, &p);
+    const int nblocks = backward_blocks(c);
+    const size_t need = (size_t)nblocks * 4 * (size_t)p.K;
+    if (need > vol->partials_cap) {
+        if (vol->partials) {
+            cudaStreamSynchronize(s);
+            cudaFree(vol->partials);
+            vol->partials = nullptr;
+            vol->partials_cap = 0;
+        }
+        cudaError_t e = cudaMalloc(&vol->partials, need * sizeof(float));
+        if (e != cudaSuccess) {
+            vol->partials = nullptr;
+            cudaGetLastError();
+            set_error("vr_render_backward: cannot allocate the table-gradient partials");
+            return VR_ERR_OOM;
+        }
+        vol->partials_cap = need;
+    }
+    const long long nvox = (long long)vol->dims[0] * vol->dims[1] * vol->dims[2];
+    cudaError_t e = launch_backward(vol_dev(vol), vol->store_dtype, c, p, reinterpret_cast<const float4 *>(dev_rgba),
+                                    dev_nsamples, reinterpret_cast<const float4 *>(dev_grad_rgba), vol->partials,
+                                    nblocks, dev_grad_tf, dev_grad_vox, nvox, (flags & VR_GRAD_ACCUMULATE) != 0, s);
+    if (e != cudaSuccess) return cuda_fail(e, "vr_render_backward launch");
+    return VR_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,363 @@
+// vr_batched.cu -- many (volume, camera, transfer function, image) jobs in ONE
+// persistent launch (an extension: the paper's future-work item on many
+// smaller cubes).  Warps pull ray tiles of all jobs from one global atomic
+// queue; a tile index maps to its job by binary search over the per-job tile
+// prefix.  The launch (counter reset + kernel) is captured once in a CUDA
+// graph and replayed while the job list is unchanged.
+#include "vr_device.cuh"
+
+#include <chrono>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <vector>
+
+namespace vr {
+
+constexpr int kBatThreads = 256;
+
+struct JobDev {
+    VolDev v;
+    CamDev c;
+    ParamDev p;
+    float4 *out;
+    uint32_t *nsamples;
+    int tiles_x;
+    unsigned tile_begin;     // first global tile index of this job
+};
+
+__device__ __forceinline__ float4 tf_lookup_global(const ParamDev &p, float v)
+{
+    float s = (v - p.vmin) * p.scale01;
+    s = fminf(fmaxf(s, 0.0f), 1.0f);
+    const float u = s * p.km1;
+    const int i0 = min(__float2int_rd(u), p.K - 2);
+    const float w = u - (float)i0;
+    const float4 e0 = __ldg(p.tf + i0), e1 = __ldg(p.tf + i0 + 1);
+    return make_float4(fmaf(w, e1.x - e0.x, e0.x), fmaf(w, e1.y - e0.y, e0.y), fmaf(w, e1.z - e0.z, e0.z),
+                       fmaf(w, e1.w - e0.w, e0.w));
+}
+
+template <typename T, int LOG2B>
+__global__ void __launch_bounds__(kBatThreads) batched_kernel(const JobDev *__restrict__ jobs, int njobs,
+                                                               unsigned total_tiles, unsigned *counter,
+                                                               int log2_tw)
+{
+    const int lane = threadIdx.x & 31;
+    const int tw = 1 << log2_tw;
+    for (;;) {
+        unsigned tile = 0;
+        if (lane == 0) tile = atomicAdd(counter, 1u);
+        tile = __shfl_sync(kFull, tile, 0);
+        if (tile >= total_tiles) break;
+        // job = last j with tile_begin <= tile
+        int lo = 0, hi = njobs - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (__ldg(&jobs[mid].tile_begin) <= tile) lo = mid; else hi = mid - 1;
+        }
+        const JobDev &J = jobs[lo];
+        const unsigned local = tile - J.tile_begin;
+        const int i = (int)(local % J.tiles_x) * tw + (lane & (tw - 1));
+        const int j = (int)(local / J.tiles_x) * (32 >> log2_tw) + (lane >> log2_tw);
+        const CamDev c = J.c;
+        const ParamDev p = J.p;
+        const VolDev v = J.v;
+        const bool inside = i < c.W && j < c.H;
+        Ray ray;
+        const bool hit = inside && setup_ray(c, v.nx, v.ny, v.nz, p.step, i, j, ray);
+        float r = 0.f, g = 0.f, b = 0.f, Tr = 1.0f;
+        int k = 0;
+        bool active = hit;
+        while (__any_sync(kFull, active)) {
+            if (active) {
+                const float3 pos = sample_pos(ray, k, p.step);
+                const Cell cell = locate<LOG2B>(v, pos);
+                const float val = trilinear<T, LOG2B>(v, cell);
+                const float4 e = tf_lookup_global(p, val);
+                const float aT = e.w * Tr;
+                r = fmaf(aT, e.x, r);
+                g = fmaf(aT, e.y, g);
+                b = fmaf(aT, e.z, b);
+                Tr = fmaf(-e.w, Tr, Tr);
+                ++k;
+                if (k >= ray.n || Tr <= p.t_stop) active = false;
+            }
+        }
+        if (inside) {
+            const long long px = (long long)j * c.W + i;
+            J.out[px] = make_float4(fmaf(Tr, p.bg.x, r), fmaf(Tr, p.bg.y, g), fmaf(Tr, p.bg.z, b),
+                                    fmaf(Tr, p.bg.w, 1.0f - Tr));
+            if (J.nsamples) J.nsamples[px] = hit ? (uint32_t)k : 0u;
+        }
+    }
+}
+
+using BatchFn = void (*)(const JobDev *, int, unsigned, unsigned *, int);
+
+static BatchFn pick_kernel(vr_dtype dt, int log2b)
+{
+#define VR_BAT_DT(TT)                                 \
+    switch (log2b) {                                  \
+    case 4: return batched_kernel<TT, 4>;             \
+    case 5: return batched_kernel<TT, 5>;             \
+    case 6: return batched_kernel<TT, 6>;             \
+    default: return nullptr;                          \
+    }
+    switch (dt) {
+    case VR_F32: VR_BAT_DT(float);
+    case VR_F16: VR_BAT_DT(__half);
+    case VR_BF16: VR_BAT_DT(__nv_bfloat16);
+    }
+    return nullptr;
+#undef VR_BAT_DT
+}
+
+// A prepared batch: job descriptors resident on the device, a work counter,
+// and (optionally) the instantiated graph of one launch.
+struct BatchPlan {
+    std::vector<unsigned char> key;
+    JobDev *djobs = nullptr;
+    unsigned *counter = nullptr;
+    int njobs = 0;
+    unsigned total_tiles = 0;
+    BatchFn fn = nullptr;
+    int log2_tw = 3;
+    unsigned grid = 1;
+    cudaGraphExec_t exec = nullptr;
+    int device = 0;
+};
+
+static std::mutex g_plans_mu;
+static std::map<std::vector<unsigned char>, BatchPlan *> g_plans;
+
+static int log2_of(int x)
+{
+    int l = 0;
+    while ((1 << l) < x) ++l;
+    return (1 << l) == x ? l : -1;
+}
+
+static vr_status prepare_jobs(const vr_job *jobs, int n, int tile_w, std::vector<JobDev> &hj, unsigned &total,
+                              vr_dtype &dt, int &log2b)
+{
+    const int tile_h = 32 / tile_w;
+    total = 0;
+    hj.resize((size_t)n);
+    for (int q = 0; q < n; ++q) {
+        const vr_job &J = jobs[q];
+        if (!J.vol) return (set_error("jobs[" + std::to_string(q) + "].vol is NULL"), VR_ERR_INVALID_ARG);
+        if (!J.dev_rgba_out || !is_aligned16(J.dev_rgba_out))
+            return (set_error("jobs[" + std::to_string(q) + "].dev_rgba_out must be non-NULL and 16-byte aligned"),
+                    VR_ERR_INVALID_ARG);
+        if (J.params.filter != VR_FILTER_SOFTWARE)
+            return (set_error("vr_render_batched: software filter only"), VR_ERR_UNSUPPORTED);
+        if (q == 0) {
+            dt = J.vol->store_dtype;
+            log2b = J.vol->log2b;
+        } else if (J.vol->store_dtype != dt || J.vol->log2b != log2b) {
+            return (set_error("vr_render_batched: all volumes of a batch must share store dtype and brick size"),
+                    VR_ERR_UNSUPPORTED);
+        }
+        JobDev &d = hj[(size_t)q];
+        prepare_camera(J.vol, &J.cam, &d.c);
+        prepare_params(&J.params, &d.p);
+        d.v = vol_dev(J.vol);
+        d.out = reinterpret_cast<float4 *>(J.dev_rgba_out);
+        d.nsamples = J.dev_nsamples_out;
+        d.tiles_x = (J.cam.width + tile_w - 1) / tile_w;
+        const unsigned tiles_y = (unsigned)((J.cam.height + tile_h - 1) / tile_h);
+        d.tile_begin = total;
+        const unsigned long long t = (unsigned long long)total + (unsigned long long)d.tiles_x * tiles_y;
+        if (t > 0xFFFFFFF0ull) return (set_error("vr_render_batched: too many ray tiles"), VR_ERR_INVALID_ARG);
+        total = (unsigned)t;
+    }
+    return VR_OK;
+}
+
+static vr_status validate_batch(const vr_job *jobs, int n, const vr_batch_opts *opts, int &tile_w, int &ctas)
+{
+    if (!jobs || n < 1) return (set_error("jobs must be non-NULL with n >= 1"), VR_ERR_INVALID_ARG);
+    if (n > 65536) return (set_error("n must be <= 65536"), VR_ERR_INVALID_ARG);
+    tile_w = (opts && opts->tile_w) ? opts->tile_w : 8;
+    const int tile_h = (opts && opts->tile_h) ? opts->tile_h : 32 / tile_w;
+    if (log2_of(tile_w) < 0 || tile_w * tile_h != 32)
+        return (set_error("tile_w * tile_h must be 32 with tile_w a power of two"), VR_ERR_INVALID_ARG);
+    ctas = opts ? opts->ctas_per_sm : 0;
+    if (ctas < 0 || ctas > 32) return (set_error("ctas_per_sm must be in [0, 32]"), VR_ERR_INVALID_ARG);
+    return VR_OK;
+}
+
+static void destroy_plan(BatchPlan *p)
+{
+    if (p->exec) cudaGraphExecDestroy(p->exec);
+    if (p->djobs) cudaFree(p->djobs);
+    if (p->counter) cudaFree(p->counter);
+    delete p;
+}
+
+// Drops every cached plan that references `vol` (called before the volume is
+// freed, with the device synchronised).
+void purge_plans(const vr_volume *vol)
+{
+    std::lock_guard<std::mutex> g(g_plans_mu);
+    for (auto it = g_plans.begin(); it != g_plans.end();) {
+        const vr_job *js = reinterpret_cast<const vr_job *>(it->first.data() + sizeof(int) * 3);
+        bool uses = false;
+        for (int q = 0; q < it->second->njobs && !uses; ++q) {
+            vr_job J;
+            std::memcpy(&J, js + q, sizeof J);
+            uses = J.vol == vol;
+        }
+        if (uses) {
+            destroy_plan(it->second);
+            it = g_plans.erase(it);
+        } else {
+            ++it;
+        }
+    }
+}
+
+}  // namespace vr
+
+using namespace vr;
+
+extern "C" vr_status vr_render_batched(const vr_job *jobs, int n, const vr_batch_opts *opts, void *cuda_stream)
+{
+    set_error("");
+    int tile_w = 8, ctas = 0;
+    vr_status st = validate_batch(jobs, n, opts, tile_w, ctas);
+    if (st != VR_OK) return st;
+    for (int q = 0; q < n; ++q) {
+        st = validate_job(&jobs[q], q);
+        if (st != VR_OK) return st;
+    }
+    const int use_graph = opts ? opts->use_graph : 0;
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    int dev = 0;
+    cudaGetDevice(&dev);
+
+    // plan key: device, options and the raw job list
+    std::vector<unsigned char> key(sizeof(int) * 3 + sizeof(vr_job) * (size_t)n);
+    int hdr[3] = {dev, tile_w, ctas};
+    std::memcpy(key.data(), hdr, sizeof hdr);
+    std::memcpy(key.data() + sizeof hdr, jobs, sizeof(vr_job) * (size_t)n);
+
+    std::lock_guard<std::mutex> g(g_plans_mu);
+    BatchPlan *plan = nullptr;
+    auto it = g_plans.find(key);
+    if (it != g_plans.end()) plan = it->second;
+    if (!plan) {
+        std::vector<JobDev> hj;
+        unsigned total = 0;
+        vr_dtype dt = VR_F32;
+        int log2b = 5;
+        st = prepare_jobs(jobs, n, tile_w, hj, total, dt, log2b);
+        if (st != VR_OK) return st;
+        plan = new BatchPlan();
+        plan->key = key;
+        plan->njobs = n;
+        plan->total_tiles = total;
+        plan->fn = pick_kernel(dt, log2b);
+        plan->log2_tw = log2_of(tile_w);
+        plan->device = dev;
+        cudaError_t e = cudaMalloc(&plan->djobs, sizeof(JobDev) * (size_t)n);
+        if (e == cudaSuccess) e = cudaMalloc(&plan->counter, sizeof(unsigned));
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(plan->djobs, hj.data(), sizeof(JobDev) * (size_t)n, cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) {
+            destroy_plan(plan);
+            return cuda_fail(e, "vr_render_batched: plan upload");
+        }
+        int per_sm = ctas;
+        if (per_sm == 0) {
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void *)plan->fn, kBatThreads, 0) !=
+                    cudaSuccess || per_sm < 1)
+                per_sm = 1;
+        }
+        unsigned grid = (unsigned)(per_sm * sm_count());
+        const unsigned useful = (total + kBatThreads / 32 - 1) / (kBatThreads / 32);
+        plan->grid = grid < useful ? grid : (useful ? useful : 1);
+        if (g_plans.size() > 64) {           // bound the cache
+            cudaStreamSynchronize(s);
+            for (auto &kv : g_plans) destroy_plan(kv.second);
+            g_plans.clear();
+        }
+        g_plans[key] = plan;
+    }
+    cudaError_t e;
+    if (use_graph) {
+        if (!plan->exec) {
+            cudaStream_t cap;
+            e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
+            if (e != cudaSuccess) return cuda_fail(e, "cudaStreamCreate");
+            cudaGraph_t graph = nullptr;
+            e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+            if (e == cudaSuccess) {
+                cudaMemsetAsync(plan->counter, 0, sizeof(unsigned), cap);
+                plan->fn<<<plan->grid, kBatThreads, 0, cap>>>(plan->djobs, plan->njobs, plan->total_tiles,
+                                                             plan->counter, plan->log2_tw);
+                e = cudaStreamEndCapture(cap, &graph);
+            }
+            if (e == cudaSuccess) e = cudaGraphInstantiate(&plan->exec, graph, 0);
+            if (graph) cudaGraphDestroy(graph);
+            cudaStreamDestroy(cap);
+            if (e != cudaSuccess) {
+                plan->exec = nullptr;
+                return cuda_fail(e, "vr_render_batched: graph capture");
+            }
+        }
+        e = cudaGraphLaunch(plan->exec, s);
+    } else {
+        e = cudaMemsetAsync(plan->counter, 0, sizeof(unsigned), s);
+        if (e == cudaSuccess) {
+            plan->fn<<<plan->grid, kBatThreads, 0, s>>>(plan->djobs, plan->njobs, plan->total_tiles, plan->counter,
+                                                        plan->log2_tw);
+            e = cudaGetLastError();
+        }
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "vr_render_batched launch");
+    return VR_OK;
+}
+
+extern "C" vr_status vr_autotune_batched(const vr_job *jobs, int n, vr_batch_opts *best, void *cuda_stream)
+{
+    if (!best) return (set_error("best is NULL"), VR_ERR_INVALID_ARG);
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    const int shapes[4][2] = {{8, 4}, {4, 8}, {16, 2}, {32, 1}};
+    const int ctas_list[4] = {0, 1, 2, 4};
+    float best_ms = 1e30f;
+    vr_batch_opts win = *best;
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+        return (set_error("cudaEventCreate failed"), VR_ERR_CUDA);
+    vr_status result = VR_OK;
+    for (auto &sh : shapes) {
+        for (int ct : ctas_list) {
+            vr_batch_opts o = *best;
+            o.tile_w = sh[0];
+            o.tile_h = sh[1];
+            o.ctas_per_sm = ct;
+            o.use_graph = 0;
+            vr_status st = vr_render_batched(jobs, n, &o, cuda_stream);      // warm-up (builds the plan)
+            if (st != VR_OK) { result = st; goto done; }
+            cudaEventRecord(e0, s);
+            for (int rep = 0; rep < 3; ++rep) vr_render_batched(jobs, n, &o, cuda_stream);
+            cudaEventRecord(e1, s);
+            if (cudaEventSynchronize(e1) != cudaSuccess) { result = cuda_fail(cudaGetLastError(), "autotune"); goto done; }
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (ms < best_ms) {
+                best_ms = ms;
+                win = o;
+            }
+        }
+    }
+    win.use_graph = best->use_graph;
+    *best = win;
+done:
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return result;
+}

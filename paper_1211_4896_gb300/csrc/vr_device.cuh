@@ -1,0 +1,171 @@
+// vr_device.cuh -- device helpers shared by the forward, backward and batched
+// kernels: ray setup (camera + box clipping), trilinear interpolation from the
+// bricked layout, and the transfer-function lookup.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include "vr_internal.h"
+
+namespace vr {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+// ---------------------------------------------------------------------------
+// Voxel loads (read-only path), widened to float.
+// ---------------------------------------------------------------------------
+template <typename T> __device__ __forceinline__ float ldv(const T *p);
+template <> __device__ __forceinline__ float ldv<float>(const float *p) { return __ldg(p); }
+template <> __device__ __forceinline__ float ldv<__half>(const __half *p) { return __half2float(__ldg(p)); }
+template <> __device__ __forceinline__ float ldv<__nv_bfloat16>(const __nv_bfloat16 *p)
+{
+    return __bfloat162float(__ldg(p));
+}
+
+// ---------------------------------------------------------------------------
+// Ray setup: camera model of Section 3.1's user-controlled viewport (pinhole
+// or orthographic projection), clipped to the closed box [0, n-1]^3 by the
+// slab method.  Samples sit at s_in + (k + 1/2) step, k = 0 .. n-1, i.e.
+// n = floor((s_out - s_in)/step + 1/2) (constant sampling step, Section 4.4).
+// ---------------------------------------------------------------------------
+struct Ray {
+    float3 q, d;      // anchor and direction, voxel space (d per world unit)
+    float s_in;
+    int n;
+};
+
+__device__ __forceinline__ bool slab_axis(float q, float d, float hi, float &s0, float &s1)
+{
+    if (d != 0.0f) {
+        float rd = 1.0f / d;
+        float ta = (0.0f - q) * rd, tb = (hi - q) * rd;
+        s0 = fmaxf(s0, fminf(ta, tb));
+        s1 = fminf(s1, fmaxf(ta, tb));
+        return true;
+    }
+    return q >= 0.0f && q <= hi;     // parallel: inside the slab or a miss
+}
+
+__device__ __forceinline__ bool setup_ray(const CamDev &c, int nx, int ny, int nz, float step, int i, int j,
+                                          Ray &r)
+{
+    const float hi = (float)i - 0.5f * (float)(c.W - 1);
+    const float hj = (float)j - 0.5f * (float)(c.H - 1);
+    r.q.x = fmaf(hi, c.qa.x, fmaf(hj, c.qb.x, c.q0.x));
+    r.q.y = fmaf(hi, c.qa.y, fmaf(hj, c.qb.y, c.q0.y));
+    r.q.z = fmaf(hi, c.qa.z, fmaf(hj, c.qb.z, c.q0.z));
+    float3 w;
+    float smin;
+    if (c.persp) {
+        w.x = fmaf(hi, c.wa.x, fmaf(hj, c.wb.x, c.wf.x));
+        w.y = fmaf(hi, c.wa.y, fmaf(hj, c.wb.y, c.wf.y));
+        w.z = fmaf(hi, c.wa.z, fmaf(hj, c.wb.z, c.wf.z));
+        const float len = sqrtf(w.x * w.x + w.y * w.y + w.z * w.z);
+        const float il = 1.0f / len;
+        w.x *= il; w.y *= il; w.z *= il;
+        smin = -c.dist * len;                  // the eye: samples only in front of it
+    } else {
+        w = c.wf;
+        smin = -INFINITY;
+    }
+    r.d = make_float3(w.x * c.inv_sp.x, w.y * c.inv_sp.y, w.z * c.inv_sp.z);
+    float s0 = smin, s1 = INFINITY;
+    if (!slab_axis(r.q.x, r.d.x, (float)(nx - 1), s0, s1)) return false;
+    if (!slab_axis(r.q.y, r.d.y, (float)(ny - 1), s0, s1)) return false;
+    if (!slab_axis(r.q.z, r.d.z, (float)(nz - 1), s0, s1)) return false;
+    if (!(s0 < s1)) return false;
+    r.s_in = s0;
+    r.n = (int)floorf((s1 - s0) / step + 0.5f);
+    return r.n > 0;
+}
+
+__device__ __forceinline__ float3 sample_pos(const Ray &r, int k, float step)
+{
+    const float s = fmaf((float)k + 0.5f, step, r.s_in);
+    return make_float3(fmaf(s, r.d.x, r.q.x), fmaf(s, r.d.y, r.q.y), fmaf(s, r.d.z, r.q.z));
+}
+
+// ---------------------------------------------------------------------------
+// Trilinear interpolation (Section 4.4) from the bricked layout.  The cell
+// origin is clamp(floor(p), 0, n-2) per axis; with the +1 apron all eight
+// corners of the cell lie in one brick at constant offsets.
+// ---------------------------------------------------------------------------
+struct Cell {
+    long long base;   // element index of corner (x0, y0, z0)
+    float fx, fy, fz;
+    int x0, y0, z0;
+};
+
+template <int LOG2B>
+__device__ __forceinline__ Cell locate(const VolDev &v, float3 p)
+{
+    Cell c;
+    c.x0 = min(max(__float2int_rd(p.x), 0), v.nx - 2);
+    c.y0 = min(max(__float2int_rd(p.y), 0), v.ny - 2);
+    c.z0 = min(max(__float2int_rd(p.z), 0), v.nz - 2);
+    c.fx = p.x - (float)c.x0;
+    c.fy = p.y - (float)c.y0;
+    c.fz = p.z - (float)c.z0;
+    constexpr int B = 1 << LOG2B, B1 = B + 1;
+    const int bx = c.x0 >> LOG2B, by = c.y0 >> LOG2B, bz = c.z0 >> LOG2B;
+    const int lx = c.x0 & (B - 1), ly = c.y0 & (B - 1), lz = c.z0 & (B - 1);
+    const long long brick = ((long long)bz * v.nby + by) * v.nbx + bx;
+    c.base = brick * v.stride + (lz * B1 + ly) * B1 + lx;
+    return c;
+}
+
+template <typename T, int LOG2B>
+__device__ __forceinline__ float trilinear(const VolDev &v, const Cell &c)
+{
+    constexpr int B1 = (1 << LOG2B) + 1, P = B1 * B1;
+    const T *b = static_cast<const T *>(v.data) + c.base;
+    const float v000 = ldv(b), v100 = ldv(b + 1), v010 = ldv(b + B1), v110 = ldv(b + B1 + 1);
+    const float v001 = ldv(b + P), v101 = ldv(b + P + 1), v011 = ldv(b + P + B1), v111 = ldv(b + P + B1 + 1);
+    const float c00 = fmaf(c.fx, v100 - v000, v000), c10 = fmaf(c.fx, v110 - v010, v010);
+    const float c01 = fmaf(c.fx, v101 - v001, v001), c11 = fmaf(c.fx, v111 - v011, v011);
+    const float c0 = fmaf(c.fy, c10 - c00, c00), c1 = fmaf(c.fy, c11 - c01, c01);
+    return fmaf(c.fz, c1 - c0, c0);
+}
+
+// Dense index of corner q (bit 0: +x, bit 1: +y, bit 2: +z) and its weight.
+__device__ __forceinline__ float corner_weight(const Cell &c, int q)
+{
+    const float wx = (q & 1) ? c.fx : 1.0f - c.fx;
+    const float wy = (q & 2) ? c.fy : 1.0f - c.fy;
+    const float wz = (q & 4) ? c.fz : 1.0f - c.fz;
+    return wx * wy * wz;
+}
+
+// ---------------------------------------------------------------------------
+// Transfer function (Section 3.3): the value range is partitioned into K-1
+// levels between K table entries; u = clamp((v-vmin)/(vmax-vmin),0,1)(K-1),
+// entries floor(u) and floor(u)+1 blended linearly.
+// ---------------------------------------------------------------------------
+struct TfPos {
+    int i0;
+    float w;
+    bool interior;    // vmin < v < vmax: the lookup has a slope in v
+};
+
+__device__ __forceinline__ float4 tf_lookup(const float4 *tfs, const ParamDev &p, float v, TfPos &pos)
+{
+    float s = (v - p.vmin) * p.scale01;
+    pos.interior = (s > 0.0f) && (s < 1.0f);
+    s = fminf(fmaxf(s, 0.0f), 1.0f);          // fmaxf maps NaN to 0
+    const float u = s * p.km1;
+    const int i0 = min(__float2int_rd(u), p.K - 2);
+    const float w = u - (float)i0;
+    pos.i0 = i0;
+    pos.w = w;
+    const float4 e0 = tfs[i0], e1 = tfs[i0 + 1];
+    return make_float4(fmaf(w, e1.x - e0.x, e0.x), fmaf(w, e1.y - e0.y, e0.y), fmaf(w, e1.z - e0.z, e0.z),
+                       fmaf(w, e1.w - e0.w, e0.w));
+}
+
+__device__ __forceinline__ void load_tf_shared(float4 *tfs, const float4 *tf, int K)
+{
+    for (int q = threadIdx.x; q < K; q += blockDim.x) tfs[q] = __ldg(tf + q);
+}
+
+}  // namespace vr

@@ -1,0 +1,202 @@
+// vr_forward.cu -- forward ray-casting kernels (Sections 3.3-3.4 and 4.4 of
+// Hassan et al. 2012): per pixel, clip the ray to the box, sample at a
+// constant step with trilinear interpolation, map each sample through the
+// RGBA transfer function and composite front to back, stopping early once the
+// accumulated opacity reaches the threshold.
+//
+// GB300 mapping: persistent warps, one 8x4 pixel tile per warp at a time,
+// pulled from a global atomic queue (load balance across uneven ray lengths
+// and early termination); the transfer function sits in shared memory; voxel
+// gathers go through the read-only L1 path from 32^3 (+apron) bricks so all
+// eight corners of a cell are at constant offsets in one brick; a warp vote
+// retires the tile once every lane's ray has finished; float4 image stores.
+#include "vr_device.cuh"
+
+#include <mutex>
+#include <map>
+
+namespace vr {
+
+constexpr int kFwdThreads = 256;
+
+struct Composite {
+    float r, g, b, T;
+};
+
+template <typename Sampler>
+__device__ __forceinline__ int march(const Ray &ray, const float4 *tfs, const ParamDev &p, Sampler sample,
+                                     Composite &acc, bool active)
+{
+    int k = 0;
+    // Warp-coherent loop: the warp keeps marching while any lane's ray is
+    // live, and leaves together once all have finished (warp-vote exit).
+    while (__any_sync(kFull, active)) {
+        if (active) {
+            const float3 pos = sample_pos(ray, k, p.step);
+            const float val = sample(pos);
+            TfPos tp;
+            const float4 e = tf_lookup(tfs, p, val, tp);
+            const float aT = e.w * acc.T;
+            acc.r = fmaf(aT, e.x, acc.r);
+            acc.g = fmaf(aT, e.y, acc.g);
+            acc.b = fmaf(aT, e.z, acc.b);
+            acc.T = fmaf(-e.w, acc.T, acc.T);          // T (1 - a)
+            ++k;
+            if (k >= ray.n || acc.T <= p.t_stop) active = false;
+        }
+    }
+    return k;
+}
+
+__device__ __forceinline__ void write_pixel(const ParamDev &p, const Composite &acc, int used, float4 *out,
+                                            uint32_t *nsamples, long long px)
+{
+    const float T = acc.T;
+    out[px] = make_float4(fmaf(T, p.bg.x, acc.r), fmaf(T, p.bg.y, acc.g), fmaf(T, p.bg.z, acc.b),
+                          fmaf(T, p.bg.w, 1.0f - T));
+    if (nsamples) nsamples[px] = (uint32_t)used;
+}
+
+template <typename T, int LOG2B>
+__global__ void __launch_bounds__(kFwdThreads) fwd_kernel(VolDev v, CamDev c, ParamDev p, float4 *out,
+                                                           uint32_t *nsamples, unsigned *counter, int tiles_x,
+                                                           unsigned ntiles)
+{
+    extern __shared__ float4 tfs[];
+    load_tf_shared(tfs, p.tf, p.K);
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    for (;;) {
+        unsigned tile = 0;
+        if (lane == 0) tile = atomicAdd(counter, 1u);
+        tile = __shfl_sync(kFull, tile, 0);
+        if (tile >= ntiles) break;
+        const int i = (int)(tile % tiles_x) * 8 + (lane & 7);
+        const int j = (int)(tile / tiles_x) * 4 + (lane >> 3);
+        const bool inside = i < c.W && j < c.H;
+        Ray ray;
+        const bool hit = inside && setup_ray(c, v.nx, v.ny, v.nz, p.step, i, j, ray);
+        Composite acc{0.0f, 0.0f, 0.0f, 1.0f};
+        const int used = march(ray, tfs, p, [&](float3 pos) {
+            const Cell cell = locate<LOG2B>(v, pos);
+            return trilinear<T, LOG2B>(v, cell);
+        }, acc, hit);
+        if (inside) write_pixel(p, acc, hit ? used : 0, out, nsamples, (long long)j * c.W + i);
+    }
+}
+
+__global__ void __launch_bounds__(kFwdThreads) fwd_tex_kernel(cudaTextureObject_t tex, int nx, int ny, int nz,
+                                                               CamDev c, ParamDev p, float4 *out,
+                                                               uint32_t *nsamples, unsigned *counter,
+                                                               int tiles_x, unsigned ntiles)
+{
+    extern __shared__ float4 tfs[];
+    load_tf_shared(tfs, p.tf, p.K);
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    for (;;) {
+        unsigned tile = 0;
+        if (lane == 0) tile = atomicAdd(counter, 1u);
+        tile = __shfl_sync(kFull, tile, 0);
+        if (tile >= ntiles) break;
+        const int i = (int)(tile % tiles_x) * 8 + (lane & 7);
+        const int j = (int)(tile / tiles_x) * 4 + (lane >> 3);
+        const bool inside = i < c.W && j < c.H;
+        Ray ray;
+        const bool hit = inside && setup_ray(c, nx, ny, nz, p.step, i, j, ray);
+        Composite acc{0.0f, 0.0f, 0.0f, 1.0f};
+        // Hardware filter: texel centres at +0.5 in unnormalised coordinates.
+        const int used = march(ray, tfs, p, [&](float3 pos) {
+            return tex3D<float>(tex, pos.x + 0.5f, pos.y + 0.5f, pos.z + 0.5f);
+        }, acc, hit);
+        if (inside) write_pixel(p, acc, hit ? used : 0, out, nsamples, (long long)j * c.W + i);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Launch helpers
+// ---------------------------------------------------------------------------
+
+static int occupancy_blocks(const void *fn, int threads, size_t smem)
+{
+    static std::mutex mu;
+    static std::map<std::pair<const void *, size_t>, int> cache;
+    std::lock_guard<std::mutex> g(mu);
+    auto key = std::make_pair(fn, smem);
+    auto it = cache.find(key);
+    if (it != cache.end()) return it->second;
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, threads, smem) != cudaSuccess || nb < 1) nb = 1;
+    cache[key] = nb;
+    return nb;
+}
+
+template <typename T, int LOG2B>
+static cudaError_t launch_fwd_t(const VolDev &v, const CamDev &c, const ParamDev &p, float4 *out,
+                                uint32_t *nsamples, unsigned *counter, cudaStream_t s)
+{
+    const int tiles_x = (c.W + 7) / 8, tiles_y = (c.H + 3) / 4;
+    const unsigned ntiles = (unsigned)tiles_x * (unsigned)tiles_y;
+    const size_t smem = sizeof(float4) * (size_t)p.K;
+    auto fn = fwd_kernel<T, LOG2B>;
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    const int per_sm = occupancy_blocks((const void *)fn, kFwdThreads, smem);
+    const unsigned warps_needed = ntiles;
+    unsigned grid = (unsigned)(per_sm * sm_count());
+    const unsigned max_useful = (warps_needed + kFwdThreads / 32 - 1) / (kFwdThreads / 32);
+    if (grid > max_useful) grid = max_useful;
+    if (grid < 1) grid = 1;
+    cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(unsigned), s);
+    if (e != cudaSuccess) return e;
+    fn<<<grid, kFwdThreads, smem, s>>>(v, c, p, out, nsamples, counter, tiles_x, ntiles);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_forward(const VolDev &v, vr_dtype dt, const CamDev &c, const ParamDev &p, float4 *out,
+                           uint32_t *nsamples, unsigned *counter, cudaStream_t s)
+{
+#define VR_FWD_CASE(TT, LB) return launch_fwd_t<TT, LB>(v, c, p, out, nsamples, counter, s)
+#define VR_FWD_DT(TT)                                   \
+    switch (v.log2b) {                                  \
+    case 4: VR_FWD_CASE(TT, 4);                         \
+    case 5: VR_FWD_CASE(TT, 5);                         \
+    case 6: VR_FWD_CASE(TT, 6);                         \
+    default: return cudaErrorInvalidValue;              \
+    }
+    switch (dt) {
+    case VR_F32: VR_FWD_DT(float);
+    case VR_F16: VR_FWD_DT(__half);
+    case VR_BF16: VR_FWD_DT(__nv_bfloat16);
+    }
+    return cudaErrorInvalidValue;
+#undef VR_FWD_DT
+#undef VR_FWD_CASE
+}
+
+cudaError_t launch_forward_texture(const vr_volume *vol, const CamDev &c, const ParamDev &p, float4 *out,
+                                   uint32_t *nsamples, unsigned *counter, cudaStream_t s)
+{
+    const int tiles_x = (c.W + 7) / 8, tiles_y = (c.H + 3) / 4;
+    const unsigned ntiles = (unsigned)tiles_x * (unsigned)tiles_y;
+    const size_t smem = sizeof(float4) * (size_t)p.K;
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(fwd_tex_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    const int per_sm = occupancy_blocks((const void *)fwd_tex_kernel, kFwdThreads, smem);
+    unsigned grid = (unsigned)(per_sm * sm_count());
+    const unsigned max_useful = (ntiles + kFwdThreads / 32 - 1) / (kFwdThreads / 32);
+    if (grid > max_useful) grid = max_useful;
+    cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(unsigned), s);
+    if (e != cudaSuccess) return e;
+    fwd_tex_kernel<<<grid, kFwdThreads, smem, s>>>(vol->tex, (int)vol->dims[0], (int)vol->dims[1],
+                                                   (int)vol->dims[2], c, p, out, nsamples, counter, tiles_x,
+                                                   ntiles);
+    return cudaGetLastError();
+}
+
+}  // namespace vr

@@ -1,0 +1,107 @@
+// vr_internal.h -- host/device structures shared by the library's translation
+// units (not part of the public ABI; see include/vr.h for that).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <string>
+
+#include "../../include/vr.h"
+
+namespace vr {
+
+// Camera prepared on the host in double precision and rounded once to float.
+// A ray of pixel (i, j) is anchored at the point where it crosses the plane
+// through the volume centre perpendicular to the view direction:
+//   q(i, j) = q0 + hi * qa + hj * qb        (voxel space; hi = i - (W-1)/2,
+//                                            hj = j - (H-1)/2, both exact)
+//   unit direction: orthographic wf; perspective normalize(wf + hi*wa + hj*wb)
+//   (world space), multiplied by inv_sp for voxel space.
+// Positions are q + s d with s in world units; the eye sits at s = -dist |w|.
+// Anchoring near the volume keeps every float magnitude ~ the volume size, so
+// rounding does not grow with the eye distance.
+struct CamDev {
+    int W, H, persp;
+    float3 q0, qa, qb;     // voxel space
+    float3 wf, wa, wb;     // world space (unnormalised direction basis)
+    float3 inv_sp;         // 1 / spacing
+    float dist;            // signed distance eye -> anchor plane along f
+};
+
+// Transfer function and compositing parameters (device view of vr_params).
+struct ParamDev {
+    const float4 *tf;
+    int K;
+    float vmin, scale01;   // s = (v - vmin) * scale01, scale01 = 1/(vmax - vmin)
+    float km1;             // K - 1
+    float step;
+    float t_stop;          // stop once T <= t_stop  (t_stop = 1 - ert_threshold, < 0 disables)
+    float4 bg;
+};
+
+// Bricked volume view.  Brick (bx, by, bz) holds voxels [bx*B, bx*B + B] per
+// axis (B+1 per axis, the +1 apron duplicates the first layer of the next
+// brick), x fastest, then y, then z; bricks are stored in x-fastest brick
+// order, `stride` elements apart.
+struct VolDev {
+    const void *data;
+    int nx, ny, nz;
+    int nbx, nby, nbz;
+    int log2b;             // B = 1 << log2b
+    long long stride;      // elements per brick (>= (B+1)^3, padded)
+};
+
+}  // namespace vr
+
+struct vr_volume {
+    int64_t dims[3];
+    double origin[3], spacing[3];
+    vr_dtype src_dtype, store_dtype;
+    int brick, log2b;
+    int64_t nb[3];
+    long long stride;
+    void *bricks = nullptr;
+    size_t bytes = 0;
+    int device = 0;
+    // work-queue counters (a small ring so consecutive calls do not reuse a
+    // counter that an earlier, still running launch may read)
+    unsigned *counters = nullptr;
+    int counter_slots = 0;
+    int next_counter = 0;
+    // backward scratch: per-block FP32 partial sums of the table gradient
+    float *partials = nullptr;
+    size_t partials_cap = 0;     // floats
+    // hardware-filter copy (created on first texture-filter render)
+    cudaArray_t tex_array = nullptr;
+    cudaTextureObject_t tex = 0;
+};
+
+namespace vr {
+
+void set_error(const std::string &msg);
+vr_status cuda_fail(cudaError_t e, const char *what);
+bool is_aligned16(const void *p);
+
+// Host-side preparation (vr_api.cpp).
+vr_status prepare_camera(const vr_volume *vol, const vr_camera *cam, CamDev *out);
+vr_status prepare_params(const vr_params *p, ParamDev *out);
+VolDev vol_dev(const vr_volume *vol);
+vr_status next_counter(vr_volume *vol, unsigned **ctr);
+int sm_count();
+
+// Launchers (each .cu file).
+cudaError_t launch_brick(const void *src, vr_dtype src_dtype, vr_volume *vol, cudaStream_t s);
+vr_status build_texture(vr_volume *vol, cudaStream_t s);
+cudaError_t launch_forward(const VolDev &v, vr_dtype dt, const CamDev &c, const ParamDev &p, float4 *out,
+                           uint32_t *nsamples, unsigned *counter, cudaStream_t s);
+cudaError_t launch_forward_texture(const vr_volume *vol, const CamDev &c, const ParamDev &p, float4 *out,
+                                   uint32_t *nsamples, unsigned *counter, cudaStream_t s);
+cudaError_t launch_backward(const VolDev &v, vr_dtype dt, const CamDev &c, const ParamDev &p,
+                            const float4 *rgba, const uint32_t *nsamples, const float4 *grad_rgba,
+                            float *partials, int nblocks, double *grad_tf, float *grad_vox,
+                            long long nvox, bool accumulate, cudaStream_t s);
+int backward_blocks(const CamDev &c);
+vr_status validate_job(const vr_job *job, int index);
+void purge_plans(const vr_volume *vol);
+
+}  // namespace vr

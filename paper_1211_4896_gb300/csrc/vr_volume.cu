@@ -1,0 +1,181 @@
+// vr_volume.cu -- volume residency: the dense cube is copied once into a
+// bricked layout that stays in HBM (the paper keeps the whole data set
+// resident in GPU memory, Section 2, in texture memory, Section 4.3).
+//
+// Brick (bx, by, bz) stores voxels [bx*B, bx*B+B] x [by*B, by*B+B] x
+// [bz*B, bz*B+B]: B^3 cells plus a one-voxel apron on the high side, so the
+// eight corners of any cell are in one brick.  Apron voxels past the end of
+// the volume replicate the last voxel (they are never read by a sample).
+#include "vr_device.cuh"
+
+namespace vr {
+
+template <typename S, typename D> __device__ __forceinline__ D convert_voxel(S s);
+template <> __device__ __forceinline__ float convert_voxel<float, float>(float s) { return s; }
+template <> __device__ __forceinline__ __half convert_voxel<float, __half>(float s) { return __float2half_rn(s); }
+template <> __device__ __forceinline__ __nv_bfloat16 convert_voxel<float, __nv_bfloat16>(float s)
+{
+    return __float2bfloat16_rn(s);
+}
+template <> __device__ __forceinline__ float convert_voxel<__half, float>(__half s) { return __half2float(s); }
+template <> __device__ __forceinline__ __half convert_voxel<__half, __half>(__half s) { return s; }
+template <> __device__ __forceinline__ __nv_bfloat16 convert_voxel<__half, __nv_bfloat16>(__half s)
+{
+    return __float2bfloat16_rn(__half2float(s));
+}
+template <> __device__ __forceinline__ float convert_voxel<__nv_bfloat16, float>(__nv_bfloat16 s)
+{
+    return __bfloat162float(s);
+}
+template <> __device__ __forceinline__ __half convert_voxel<__nv_bfloat16, __half>(__nv_bfloat16 s)
+{
+    return __float2half_rn(__bfloat162float(s));
+}
+template <> __device__ __forceinline__ __nv_bfloat16 convert_voxel<__nv_bfloat16, __nv_bfloat16>(__nv_bfloat16 s)
+{
+    return s;
+}
+
+// One CTA per (brick, z-layer of the brick): threads sweep the (B+1)^2 plane,
+// reading rows of the dense cube and writing the brick plane contiguously.
+template <typename S, typename D>
+__global__ void __launch_bounds__(256) brick_kernel(const S *__restrict__ src, D *__restrict__ dst, int nx,
+                                                     int ny, int nz, int nbx, int nby, int log2b,
+                                                     long long stride)
+{
+    const long long brick = blockIdx.x;
+    const int lz = blockIdx.y;
+    const int B = 1 << log2b, B1 = B + 1;
+    const int bx = (int)(brick % nbx);
+    const int by = (int)((brick / nbx) % nby);
+    const int bz = (int)(brick / ((long long)nbx * nby));
+    const int z = min(bz * B + lz, nz - 1);
+    D *out = dst + brick * stride + (long long)lz * B1 * B1;
+    for (int e = threadIdx.x; e < B1 * B1; e += blockDim.x) {
+        const int ly = e / B1, lx = e - ly * B1;
+        const int x = min(bx * B + lx, nx - 1), y = min(by * B + ly, ny - 1);
+        out[e] = convert_voxel<S, D>(src[((long long)z * ny + y) * nx + x]);
+    }
+    // zero the padding after the last layer so the brick is fully defined
+    if (lz == B1 - 1) {
+        D *pad = dst + brick * stride + (long long)B1 * B1 * B1;
+        const long long npad = stride - (long long)B1 * B1 * B1;
+        for (long long e = threadIdx.x; e < npad; e += blockDim.x) pad[e] = convert_voxel<float, D>(0.0f);
+    }
+}
+
+template <typename S, typename D>
+static cudaError_t launch_brick_t(const void *src, vr_volume *vol, cudaStream_t s)
+{
+    const long long nbricks = vol->nb[0] * vol->nb[1] * vol->nb[2];
+    dim3 grid((unsigned)nbricks, (unsigned)(vol->brick + 1));
+    brick_kernel<S, D><<<grid, 256, 0, s>>>(static_cast<const S *>(src), static_cast<D *>(vol->bricks),
+                                            (int)vol->dims[0], (int)vol->dims[1], (int)vol->dims[2],
+                                            (int)vol->nb[0], (int)vol->nb[1], vol->log2b, vol->stride);
+    return cudaGetLastError();
+}
+
+template <typename S>
+static cudaError_t launch_brick_src(const void *src, vr_volume *vol, cudaStream_t s)
+{
+    switch (vol->store_dtype) {
+    case VR_F32: return launch_brick_t<S, float>(src, vol, s);
+    case VR_F16: return launch_brick_t<S, __half>(src, vol, s);
+    case VR_BF16: return launch_brick_t<S, __nv_bfloat16>(src, vol, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_brick(const void *src, vr_dtype src_dtype, vr_volume *vol, cudaStream_t s)
+{
+    switch (src_dtype) {
+    case VR_F32: return launch_brick_src<float>(src, vol, s);
+    case VR_F16: return launch_brick_src<__half>(src, vol, s);
+    case VR_BF16: return launch_brick_src<__nv_bfloat16>(src, vol, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+// ---------------------------------------------------------------------------
+// Hardware-filter copy: a 3D CUDA array written from the bricks through a
+// surface, sampled with cudaFilterModeLinear (the measured alternative).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void surface_store(float v, cudaSurfaceObject_t s, int x, int y, int z)
+{
+    surf3Dwrite(v, s, x * (int)sizeof(float), y, z);
+}
+__device__ __forceinline__ void surface_store(__half v, cudaSurfaceObject_t s, int x, int y, int z)
+{
+    surf3Dwrite(__half_as_ushort(v), s, x * (int)sizeof(unsigned short), y, z);
+}
+
+template <typename D>
+__global__ void __launch_bounds__(256) unbrick_to_surface(VolDev v, cudaSurfaceObject_t surf)
+{
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y, z = blockIdx.z;
+    if (x >= v.nx) return;
+    const int B = 1 << v.log2b, B1 = B + 1;
+    const int bx = min(x >> v.log2b, v.nbx - 1), by = min(y >> v.log2b, v.nby - 1),
+              bz = min(z >> v.log2b, v.nbz - 1);
+    const int lx = x - bx * B, ly = y - by * B, lz = z - bz * B;
+    const long long brick = ((long long)bz * v.nby + by) * v.nbx + bx;
+    const D val = static_cast<const D *>(v.data)[brick * v.stride + ((long long)lz * B1 + ly) * B1 + lx];
+    surface_store(val, surf, x, y, z);
+}
+
+vr_status build_texture(vr_volume *vol, cudaStream_t s)
+{
+    if (vol->tex) return VR_OK;
+    if (vol->store_dtype == VR_BF16) {
+        set_error("texture filter: bfloat16 storage has no hardware-filtered texture format");
+        return VR_ERR_UNSUPPORTED;
+    }
+    int mx = 0, my = 0, mz = 0;
+    cudaDeviceGetAttribute(&mx, cudaDevAttrMaxTexture3DWidth, vol->device);
+    cudaDeviceGetAttribute(&my, cudaDevAttrMaxTexture3DHeight, vol->device);
+    cudaDeviceGetAttribute(&mz, cudaDevAttrMaxTexture3DDepth, vol->device);
+    if (vol->dims[0] > mx || vol->dims[1] > my || vol->dims[2] > mz) {
+        set_error("texture filter: volume exceeds the device's 3D texture extent");
+        return VR_ERR_UNSUPPORTED;
+    }
+    cudaChannelFormatDesc fd = vol->store_dtype == VR_F32 ? cudaCreateChannelDesc<float>()
+                                                          : cudaCreateChannelDescHalf();
+    cudaExtent ext = make_cudaExtent((size_t)vol->dims[0], (size_t)vol->dims[1], (size_t)vol->dims[2]);
+    cudaError_t e = cudaMalloc3DArray(&vol->tex_array, &fd, ext, cudaArraySurfaceLoadStore);
+    if (e != cudaSuccess) {
+        vol->tex_array = nullptr;
+        cudaGetLastError();
+        return e == cudaErrorMemoryAllocation ? (set_error("texture filter: out of device memory"), VR_ERR_OOM)
+                                              : cuda_fail(e, "cudaMalloc3DArray");
+    }
+    cudaResourceDesc rd{};
+    rd.resType = cudaResourceTypeArray;
+    rd.res.array.array = vol->tex_array;
+    cudaSurfaceObject_t surf = 0;
+    e = cudaCreateSurfaceObject(&surf, &rd);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaCreateSurfaceObject");
+    VolDev v = vol_dev(vol);
+    dim3 grid((unsigned)((vol->dims[0] + 255) / 256), (unsigned)vol->dims[1], (unsigned)vol->dims[2]);
+    if (vol->store_dtype == VR_F32)
+        unbrick_to_surface<float><<<grid, 256, 0, s>>>(v, surf);
+    else
+        unbrick_to_surface<__half><<<grid, 256, 0, s>>>(v, surf);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaDestroySurfaceObject(surf);
+    if (e != cudaSuccess) return cuda_fail(e, "texture build");
+    cudaTextureDesc td{};
+    td.addressMode[0] = td.addressMode[1] = td.addressMode[2] = cudaAddressModeClamp;
+    td.filterMode = cudaFilterModeLinear;
+    td.readMode = cudaReadModeElementType;
+    td.normalizedCoords = 0;
+    e = cudaCreateTextureObject(&vol->tex, &rd, &td, nullptr);
+    if (e != cudaSuccess) {
+        vol->tex = 0;
+        return cuda_fail(e, "cudaCreateTextureObject");
+    }
+    return VR_OK;
+}
+
+}  // namespace vr

@@ -1,0 +1,154 @@
+"""GPU adjoint parity: the re-march backward kernel against (a) the oracle's
+store-all FP64 reverse sweep (a different algorithm) and (b) central finite
+differences of the GPU forward (h = 1e-3) on table entries and voxels, with
+the rule |g - fd| <= 1e-3 max(|fd|, 1e-3 max_j |fd_j|); FD points where the
+one-sided differences disagree (a kink within h) are redrawn."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from tests.helpers import cuda_or_skip
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch():
+    return cuda_or_skip()
+
+
+@pytest.fixture(scope="module")
+def P(torch):
+    import paper_1211_4896_gb300 as P
+    return P
+
+
+def _setup(torch, P, dims, seed, W, H, store="f32"):
+    dev = torch.device("cuda")
+    cube = synth.hi_cube(dims, n_blobs=max(4, int(np.prod(dims) / 30000)), n_disks=1, seed=seed)
+    vol = P.Volume(cube.to(dev), store)
+    cam = synth.camera_random_persp(dims, seed=seed + 1, width=W, height=H)
+    return cube, vol, cam
+
+
+def _grad_close(g, ref, rel=1e-3):
+    scale = np.abs(ref).max()
+    err = np.abs(g - ref)
+    bound = rel * np.maximum(np.abs(ref), 1e-3 * scale) + 1e-12
+    return err <= bound, err, bound
+
+
+@pytest.mark.parametrize("ert,bg", [(2.0, (0, 0, 0, 0)), (0.9, (0.2, 0.1, 0.4, 0.3))])
+def test_backward_matches_fp64_reverse_sweep(P, torch, ert, bg):
+    dims = (36, 30, 40)
+    cube, vol, cam = _setup(torch, P, dims, seed=12, W=48, H=40)
+    dev = torch.device("cuda")
+    tf_np = synth.tf_random_pwl(seed=3, alpha_max=0.25)
+    tf = torch.from_numpy(tf_np).to(dev)
+    img, ns = P.render(vol, cam, tf, -3.0, 30.0, 0.5, ert, bg)
+    target = torch.rand_like(img)
+    g = 2.0 * (img - target)
+    gtf, gvox = P.render_backward(vol, cam, tf, -3.0, 30.0, 0.5, img, ns, g, ert, bg)
+    torch.cuda.synchronize()
+    ref_tf, ref_vox = oracle.render_backward(cube.numpy(), cam, tf_np, -3.0, 30.0, 0.5,
+                                             g.cpu().numpy().astype(np.float64), ert=ert, bg=bg)
+    ok, err, bound = _grad_close(gtf.cpu().numpy(), ref_tf)
+    assert ok.all(), ("table gradient", err.max(), np.argwhere(~ok)[:5])
+    gv = gvox.cpu().numpy().astype(np.float64)
+    ok, err, bound = _grad_close(gv, ref_vox)
+    assert ok.mean() > 0.999, ("voxel gradient", err.max(), (~ok).sum())
+    assert np.abs(gv - ref_vox).max() <= 2e-3 * np.abs(ref_vox).max()
+    vol.close()
+
+
+def test_backward_central_differences_table_and_voxels(P, torch):
+    """Scaled-down form of the differentiation workload: L2 loss against a
+    target rendered with a hidden table; FD on 32 table entries, 32 voxels."""
+    dev = torch.device("cuda")
+    dims = (64, 64, 64)
+    cube, vol, cam = _setup(torch, P, dims, seed=31, W=96, H=96)
+    cube_d = cube.to(dev)
+    hidden = torch.from_numpy(synth.tf_ramp(256)).to(dev)
+    tf = (hidden + 0.05 * torch.rand_like(hidden)).clamp(0, 1).contiguous()
+    tf[:, 3] *= 0.5
+    step = 0.5
+    tgt, _ = P.render(vol, cam, hidden, synth.TF_VMIN, synth.TF_VMAX, step, 2.0)
+
+    def loss(tfv, vol_):
+        im, _ = P.render(vol_, cam, tfv, synth.TF_VMIN, synth.TF_VMAX, step, 2.0)
+        return float(((im.double() - tgt.double()) ** 2).sum())
+
+    img, ns = P.render(vol, cam, tf, synth.TF_VMIN, synth.TF_VMAX, step, 2.0)
+    gtf, gvox = P.render_backward(vol, cam, tf, synth.TF_VMIN, synth.TF_VMAX, step, img, ns, 2.0 * (img - tgt), 2.0)
+    gtf = gtf.cpu().numpy()
+    gvox = gvox.cpu().numpy()
+    h = 1e-3
+    rng = np.random.default_rng(0)
+    # table entries with a non-zero gradient
+    cand = np.argwhere(np.abs(gtf) > 1e-3 * np.abs(gtf).max())
+    picks = cand[rng.choice(len(cand), size=32, replace=False)]
+    fds, gs = [], []
+    for (e, ch) in picks:
+        tp, tm = tf.clone(), tf.clone()
+        tp[e, ch] += h
+        tm[e, ch] -= h
+        fds.append((loss(tp, vol) - loss(tm, vol)) / (2 * h))
+        gs.append(gtf[e, ch])
+    fds, gs = np.array(fds), np.array(gs)
+    ok, err, bound = _grad_close(gs, fds)
+    assert ok.all(), list(zip(gs[~ok], fds[~ok]))
+    # voxels (kink-screened)
+    L0 = loss(tf, vol)
+    cand = np.argwhere(np.abs(gvox) > 1e-3 * np.abs(gvox).max())
+    checked = 0
+    fds, gs = [], []
+    for q in rng.permutation(len(cand)):
+        z, y, x = cand[q]
+        vals = []
+        for d in (h, -h):
+            c2 = cube_d.clone()
+            c2[z, y, x] += d
+            vol.update(c2)
+            vals.append(loss(tf, vol))
+        vol.update(cube_d)
+        right, left = (vals[0] - L0) / h, (L0 - vals[1]) / h
+        if abs(right - left) > 1e-2 * max(abs(right), abs(left), 1e-6):
+            continue
+        fds.append((vals[0] - vals[1]) / (2 * h))
+        gs.append(gvox[z, y, x])
+        checked += 1
+        if checked == 32:
+            break
+    fds, gs = np.array(fds), np.array(gs)
+    ok, err, bound = _grad_close(gs, fds)
+    assert checked == 32 and ok.all(), list(zip(gs[~ok], fds[~ok]))
+    vol.close()
+
+
+def test_autograd_function(P, torch):
+    dev = torch.device("cuda")
+    dims = (32, 32, 32)
+    cube, vol, cam = _setup(torch, P, dims, seed=5, W=40, H=40)
+    c = cube.to(dev).requires_grad_(True)
+    tf = torch.from_numpy(synth.tf_random_pwl(seed=1)).to(dev).requires_grad_(True)
+    img = P.render_diff(c, tf, vol, cam, -3.0, 30.0, 0.5)
+    loss = (img ** 2).sum()
+    loss.backward()
+    img2, ns = P.render(vol, cam, tf.detach(), -3.0, 30.0, 0.5)
+    gtf, gvox = P.render_backward(vol, cam, tf.detach(), -3.0, 30.0, 0.5, img2, ns, 2 * img2)
+    torch.cuda.synchronize()
+    assert torch.allclose(tf.grad, gtf.float(), rtol=1e-4, atol=1e-6)
+    assert torch.allclose(c.grad, gvox, rtol=1e-3, atol=1e-6)
+    vol.close()
+
+
+def test_backward_rejects_opaque_background_and_texture(P, torch):
+    dev = torch.device("cuda")
+    cube, vol, cam = _setup(torch, P, (16, 16, 16), seed=2, W=8, H=8)
+    tf = torch.from_numpy(synth.tf_ramp(16)).to(dev)
+    img, ns = P.render(vol, cam, tf, -3, 50, 0.5)
+    with pytest.raises(P.VRError) as ei:
+        P.render_backward(vol, cam, tf, -3, 50, 0.5, img, ns, img, bg=(0, 0, 0, 1.0))
+    assert ei.value.status == -2
+    vol.close()

@@ -1,0 +1,92 @@
+"""Batched persistent launch: many uneven cubes, each with its own camera,
+table and image, in one launch (optionally a CUDA graph).  Results must equal
+the per-job vr_render outputs and the oracle."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from tests.helpers import TOL_F32, compare, cuda_or_skip
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch():
+    return cuda_or_skip()
+
+
+@pytest.fixture(scope="module")
+def P(torch):
+    import paper_1211_4896_gb300 as P
+    return P
+
+
+def _jobs(torch, P, n=7, store="f16"):
+    dev = torch.device("cuda")
+    rng = np.random.default_rng(42)
+    jobs, cubes = [], []
+    for q in range(n):
+        dims = tuple(int(x) for x in rng.integers(12, 60, size=3))
+        cube = synth.hi_cube(dims, n_blobs=4, n_disks=1, seed=700 + q)
+        vol = P.Volume(cube.to(dev), store)
+        W, H = int(rng.integers(9, 70)), int(rng.integers(7, 66))
+        cam = synth.camera_random_persp(dims, seed=800 + q, width=W, height=H)
+        tf_np = synth.tf_random_pwl(seed=900 + q)
+        jobs.append(dict(vol=vol, cam=cam, tf=torch.from_numpy(tf_np).to(dev), tf_np=tf_np, vmin=-3.0, vmax=30.0,
+                         step=0.5 + 0.1 * (q % 3), ert=0.99 if q % 2 else 2.0,
+                         out=torch.full((H, W, 4), -1.0, device=dev),
+                         nsamples=torch.full((H, W), -1, dtype=torch.int32, device=dev)))
+        cubes.append(cube)
+    return jobs, cubes
+
+
+@pytest.mark.parametrize("use_graph", [False, True])
+def test_batched_equals_single_renders(P, torch, use_graph):
+    jobs, cubes = _jobs(torch, P)
+    P.render_batched(jobs, use_graph=use_graph)
+    P.render_batched(jobs, use_graph=use_graph)          # replay: same result
+    torch.cuda.synchronize()
+    for j, cube in zip(jobs, cubes):
+        img, ns = P.render(j["vol"], j["cam"], j["tf"], j["vmin"], j["vmax"], j["step"], j["ert"])
+        torch.cuda.synchronize()
+        assert torch.equal(j["out"], img)
+        assert torch.equal(j["nsamples"], ns)
+    # and the oracle, on the rounded cubes the kernel reads
+    for j, cube in list(zip(jobs, cubes))[:3]:
+        bits = cube.to(torch.float16).view(torch.int16).numpy().view(np.uint16)
+        ref = oracle.render(bits, j["cam"], j["tf_np"], j["vmin"], j["vmax"], j["step"], j["ert"], bits="f16")
+        compare(j["out"].cpu().numpy(), j["nsamples"].cpu().numpy(), ref, TOL_F32)
+    for j in jobs:
+        j["vol"].close()
+
+
+@pytest.mark.parametrize("tile", [(4, 8), (16, 2), (32, 1)])
+def test_batched_tile_shapes(P, torch, tile):
+    jobs, _ = _jobs(torch, P, n=4, store="f32")
+    P.render_batched(jobs, use_graph=False, tile=tile, ctas_per_sm=2)
+    torch.cuda.synchronize()
+    for j in jobs:
+        img, ns = P.render(j["vol"], j["cam"], j["tf"], j["vmin"], j["vmax"], j["step"], j["ert"])
+        torch.cuda.synchronize()
+        assert torch.equal(j["out"], img)
+        j["vol"].close()
+
+
+def test_autotune_and_validation(P, torch):
+    from paper_1211_4896_gb300 import _lib as L
+    jobs, _ = _jobs(torch, P, n=3, store="f32")
+    cj = P.render_batched(jobs, use_graph=False)
+    best = L.vr_autotune_batched(cj, L.vr_batch_opts(1, 0, 0, 0))
+    assert best.tile_w * best.tile_h == 32 and best.use_graph == 1
+    # mixed storage types in one batch are rejected before any launch
+    dev = torch.device("cuda")
+    other = P.Volume(torch.zeros((8, 8, 8), device=dev), "f16")
+    jobs[1] = dict(jobs[1], vol=other)
+    with pytest.raises(P.VRError) as ei:
+        P.render_batched(jobs, use_graph=False)
+    assert ei.value.status == -2
+    with pytest.raises(P.VRError):
+        P.render_batched(jobs[:1], tile=(5, 6))
+    for j in jobs:
+        j["vol"].close()
