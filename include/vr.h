@@ -114,7 +114,7 @@ typedef struct {
  * Copies the dense cube dev_cube (src_dtype, dims = {nx, ny, nz}, each >= 2,
  * x fastest) into a bricked copy in store_dtype: bricks of B^3 cells, each
  * stored as (B+1)^3 voxels so that all 8 trilinear corners of any cell lie in
- * one brick.  F32 -> F16/BF16 rounds to nearest even.  brick = 0 picks 32;
+ * one brick.  F32 -> F16/BF16 rounds to nearest even.  brick = 0 picks 16;
  * otherwise 16, 32 or 64.  origin/spacing may be NULL (0 and 1).  The
  * caller keeps dev_cube; the call synchronises `cuda_stream` before returning
  * the handle in *out.  Errors: INVALID_ARG, OOM, CUDA.
@@ -155,14 +155,16 @@ vr_status vr_render(vr_volume_t vol, const vr_camera *cam, const vr_params *para
  * transmittance behind sample k is recovered from the final colour and
  * transmittance, T_final = (1 - alpha_out)/(1 - bg.a), so bg.a must be < 1.
  * Early-termination decisions of the forward are kept (dev_nsamples).
- *   dev_grad_tf  (K*4 float64): per-block FP32 partial sums, one final
- *                cross-block sum in FP64.
+ *   dev_grad_tf  (K*4 float64): each warp sums one 32-ray tile in FP32
+ *                shared-memory bins, then adds them to the output with FP64
+ *                atomics (the final cross-block sum is the only FP64 step;
+ *                its order is not deterministic).
  *   dev_grad_vox (nx*ny*nz float32 dense, x fastest) or NULL: float atomics
  *                (summation order is not deterministic).
  * Both are overwritten, or added to when flags has VR_GRAD_ACCUMULATE (a
  * loss summed over several views: call once per view).
  * Only software filtering is differentiable.  Errors: INVALID_ARG,
- * UNSUPPORTED (texture filter, bg.a >= 1), OOM, CUDA.
+ * UNSUPPORTED (texture filter, bg.a >= 1, tf_size > 1600), CUDA.
  * ---------------------------------------------------------------------- */
 enum { VR_GRAD_ACCUMULATE = 1 };
 

@@ -228,7 +228,6 @@ static void free_volume(vr_volume *vol)
     if (vol->tex_array) cudaFreeArray(vol->tex_array);
     if (vol->bricks) cudaFree(vol->bricks);
     if (vol->counters) cudaFree(vol->counters);
-    if (vol->partials) cudaFree(vol->partials);
     delete vol;
 }
 
@@ -259,7 +258,7 @@ vr_status vr_volume_create(const void *dev_cube, vr_dtype src_dtype, vr_dtype st
     if (origin && !finite3(origin)) return invalid("origin must be finite");
     if (spacing && !(spacing[0] > 0 && spacing[1] > 0 && spacing[2] > 0 && finite3(spacing)))
         return invalid("spacing must be finite and > 0");
-    if (brick == 0) brick = 32;
+    if (brick == 0) brick = 16;
     int log2b = 0;
     switch (brick) {
     case 16: log2b = 4; break;
@@ -402,6 +401,9 @@ vr_status vr_render_backward(vr_volume_t vol, const vr_camera *cam, const vr_par
         return invalid("dev_rgba and dev_grad_rgba must be 16-byte aligned");
     if ((reinterpret_cast<uintptr_t>(dev_grad_tf) & 7u) != 0) return invalid("dev_grad_tf must be 8-byte aligned");
     if (flags & ~(unsigned)VR_GRAD_ACCUMULATE) return invalid("flags: unknown bits");
+    if (params->tf_size > backward_max_tf_size())
+        return (set_error("vr_render_backward: tf_size above " + std::to_string(backward_max_tf_size()) +
+                          " (per-warp gradient bins must fit in shared memory)"), VR_ERR_UNSUPPORTED);
     if ((reinterpret_cast<uintptr_t>(dev_nsamples) & 3u) != 0 || (reinterpret_cast<uintptr_t>(dev_grad_vox) & 3u) != 0)
         return invalid("dev_nsamples and dev_grad_vox must be 4-byte aligned");
     st = check_volume(vol);
@@ -412,28 +414,12 @@ vr_status vr_render_backward(vr_volume_t vol, const vr_camera *cam, const vr_par
     ParamDev p;
     prepare_camera(vol, cam, &c);
     prepare_params(params, &p);
-    const int nblocks = backward_blocks(c);
-    const size_t need = (size_t)nblocks * 4 * (size_t)p.K;
-    if (need > vol->partials_cap) {
-        if (vol->partials) {
-            cudaStreamSynchronize(s);
-            cudaFree(vol->partials);
-            vol->partials = nullptr;
-            vol->partials_cap = 0;
-        }
-        cudaError_t e = cudaMalloc(&vol->partials, need * sizeof(float));
-        if (e != cudaSuccess) {
-            vol->partials = nullptr;
-            cudaGetLastError();
-            set_error("vr_render_backward: cannot allocate the table-gradient partials");
-            return VR_ERR_OOM;
-        }
-        vol->partials_cap = need;
-    }
     const long long nvox = (long long)vol->dims[0] * vol->dims[1] * vol->dims[2];
+    unsigned *ctr;
+    next_counter(vol, &ctr);
     cudaError_t e = launch_backward(vol_dev(vol), vol->store_dtype, c, p, reinterpret_cast<const float4 *>(dev_rgba),
-                                    dev_nsamples, reinterpret_cast<const float4 *>(dev_grad_rgba), vol->partials,
-                                    nblocks, dev_grad_tf, dev_grad_vox, nvox, (flags & VR_GRAD_ACCUMULATE) != 0, s);
+                                    dev_nsamples, reinterpret_cast<const float4 *>(dev_grad_rgba), dev_grad_tf,
+                                    dev_grad_vox, nvox, (flags & VR_GRAD_ACCUMULATE) != 0, ctr, s);
     if (e != cudaSuccess) return cuda_fail(e, "vr_render_backward launch");
     return VR_OK;
 }

@@ -11,126 +11,138 @@
 //   dL/da_k = T_k (c_k.g) - [ (C - C_<=k).g + gT T_n ] / (1 - a_k)
 // where (C - C_<=k).g is the final colour minus the running colour, both
 // dotted with g, so one scalar R_k is carried along the march.
-// The table gradient is accumulated per CTA in shared memory (FP32) and the
-// CTA partials are summed across blocks in FP64; the voxel gradient is
-// scattered with float atomics into the dense layout.
+//
+// Persistent warps pull 8x4 ray tiles from the same atomic queue as the
+// forward.  Each warp accumulates its tile's table gradient in private FP32
+// bins in shared memory, then adds the non-zero bins into the FP64 output
+// with FP64 atomics (the only FP64 arithmetic: the final cross-block sum).
+// The voxel gradient is scattered with float atomics into the dense layout.
 #include "vr_device.cuh"
 
 namespace vr {
 
-constexpr int kBwdThreads = 256;   // one CTA renders a 16x16 pixel tile (8 warps of 8x4)
+constexpr int kBwdThreads = 256;
+constexpr int kBwdWarps = kBwdThreads / 32;
 
 template <typename VT, int LOG2B>
 __global__ void __launch_bounds__(kBwdThreads) bwd_kernel(VolDev v, CamDev c, ParamDev p,
                                                            const float4 *__restrict__ rgba,
                                                            const uint32_t *__restrict__ nsamples,
-                                                           const float4 *__restrict__ grad_rgba,
-                                                           float *__restrict__ partials, float *grad_vox,
-                                                           int tiles_x16)
+                                                           const float4 *__restrict__ grad_rgba, double *grad_tf,
+                                                           float *grad_vox, unsigned *counter, int tiles_x,
+                                                           unsigned ntiles)
 {
-    extern __shared__ float4 smem[];
-    float4 *tfs = smem;
-    float *gtf = reinterpret_cast<float *>(smem + p.K);
-    load_tf_shared(tfs, p.tf, p.K);
-    for (int q = threadIdx.x; q < 4 * p.K; q += blockDim.x) gtf[q] = 0.0f;
-    __syncthreads();
-
+    extern __shared__ float sbins[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int i = (int)(blockIdx.x % tiles_x16) * 16 + (warp & 1) * 8 + (lane & 7);
-    const int j = (int)(blockIdx.x / tiles_x16) * 16 + (warp >> 1) * 4 + (lane >> 3);
-    const bool inside = i < c.W && j < c.H;
-    Ray ray;
-    int n = 0;
-    float4 g = make_float4(0.f, 0.f, 0.f, 0.f);
-    float Tn = 1.0f, R = 0.0f;
-    if (inside) {
-        const long long px = (long long)j * c.W + i;
-        n = (int)nsamples[px];
-        if (n > 0 && setup_ray(c, v.nx, v.ny, v.nz, p.step, i, j, ray)) {
-            n = min(n, ray.n);
-            const float4 out = rgba[px];
-            g = grad_rgba[px];
-            Tn = (1.0f - out.w) / (1.0f - p.bg.w);
-            const float Cg = (out.x - Tn * p.bg.x) * g.x + (out.y - Tn * p.bg.y) * g.y + (out.z - Tn * p.bg.z) * g.z;
-            const float gT = g.x * p.bg.x + g.y * p.bg.y + g.z * p.bg.z - g.w * (1.0f - p.bg.w);
-            R = Cg + gT * Tn;            // R_{-1}: (C - C_<=-1).g + gT T_n
-        } else {
-            n = 0;
-        }
-    }
+    const int nb = 4 * p.K;
+    float *bins = sbins + warp * nb;
+    for (int q = lane; q < nb; q += 32) bins[q] = 0.0f;
+    __syncwarp();
     const float vscale = p.km1 * p.scale01;    // du/dv inside the range
-    const int nyx = v.ny * v.nx;
-    float T = 1.0f;
-    int k = 0;
-    bool active = n > 0;
-    while (__any_sync(kFull, active)) {
-        if (active) {
-            const float3 pos = sample_pos(ray, k, p.step);
-            const Cell cell = locate<LOG2B>(v, pos);
-            const float val = trilinear<VT, LOG2B>(v, cell);
-            TfPos tp;
-            const float4 e = tf_lookup(tfs, p, val, tp);
-            const float a = e.w;
-            const float cg = e.x * g.x + e.y * g.y + e.z * g.z;
-            const float aT = a * T;
-            R = fmaf(-aT, cg, R);                       // R_k = R_{k-1} - T_k a_k (c_k.g)
-            const float om = 1.0f - a;
-            const float da = T * cg - (om > 0.0f ? R / om : 0.0f);
-            const float4 dr = make_float4(aT * g.x, aT * g.y, aT * g.z, da);
-            const float w1 = tp.w, w0 = 1.0f - tp.w;
-            float *g0 = gtf + 4 * tp.i0;
-            if (aT != 0.0f) {
-                atomicAdd(g0 + 0, w0 * dr.x); atomicAdd(g0 + 4, w1 * dr.x);
-                atomicAdd(g0 + 1, w0 * dr.y); atomicAdd(g0 + 5, w1 * dr.y);
-                atomicAdd(g0 + 2, w0 * dr.z); atomicAdd(g0 + 6, w1 * dr.z);
+    const long long nyx = (long long)v.ny * v.nx;
+
+    for (;;) {
+        unsigned tile = 0;
+        if (lane == 0) tile = atomicAdd(counter, 1u);
+        tile = __shfl_sync(kFull, tile, 0);
+        if (tile >= ntiles) break;
+        const int i = (int)(tile % tiles_x) * 8 + (lane & 7);
+        const int j = (int)(tile / tiles_x) * 4 + (lane >> 3);
+        Ray ray;
+        int n = 0;
+        float4 g = make_float4(0.f, 0.f, 0.f, 0.f);
+        float R = 0.0f;
+        if (i < c.W && j < c.H) {
+            const long long px = (long long)j * c.W + i;
+            n = (int)nsamples[px];
+            if (n > 0 && setup_ray(c, v.nx, v.ny, v.nz, p.step, i, j, ray)) {
+                n = min(n, ray.n);
+                const float4 out = rgba[px];
+                g = grad_rgba[px];
+                const float Tn = (1.0f - out.w) / (1.0f - p.bg.w);
+                const float Cg = (out.x - Tn * p.bg.x) * g.x + (out.y - Tn * p.bg.y) * g.y +
+                                 (out.z - Tn * p.bg.z) * g.z;
+                const float gT = g.x * p.bg.x + g.y * p.bg.y + g.z * p.bg.z - g.w * (1.0f - p.bg.w);
+                R = Cg + gT * Tn;            // R_{-1}: (C - C_<=-1).g + gT T_n
+            } else {
+                n = 0;
             }
-            if (da != 0.0f) { atomicAdd(g0 + 3, w0 * da); atomicAdd(g0 + 7, w1 * da); }
-            if (grad_vox && tp.interior) {
-                const float4 e0 = tfs[tp.i0], e1 = tfs[tp.i0 + 1];
-                const float dv = (dr.x * (e1.x - e0.x) + dr.y * (e1.y - e0.y) + dr.z * (e1.z - e0.z) +
-                                  dr.w * (e1.w - e0.w)) * vscale;
-                if (dv != 0.0f) {
-                    float *gv = grad_vox + ((long long)cell.z0 * nyx + (long long)cell.y0 * v.nx + cell.x0);
+        }
+        float T = 1.0f;
+        int k = 0;
+        bool active = n > 0;
+        Cell cell;
+        Corners f;
+        if (active) {
+            cell = locate<LOG2B>(v, sample_pos(ray, 0, p.step));
+            fetch_corners<VT, LOG2B>(v, cell, f);
+        }
+        while (__any_sync(kFull, active)) {
+            if (active) {
+                const bool more = k + 1 < n;
+                Cell ncell;
+                Corners nf;
+                if (more) {
+                    ncell = locate<LOG2B>(v, sample_pos(ray, k + 1, p.step));
+                    fetch_corners<VT, LOG2B>(v, ncell, nf);
+                }
+                const float val = interp_corners(cell, f);
+                TfPos tp;
+                const float4 e = tf_lookup_l1(p, val, tp);
+                const float a = e.w;
+                const float cg = e.x * g.x + e.y * g.y + e.z * g.z;
+                const float aT = a * T;
+                R = fmaf(-aT, cg, R);                       // R_k = R_{k-1} - T_k a_k (c_k.g)
+                const float om = 1.0f - a;
+                const float da = T * cg - (om > 0.0f ? R / om : 0.0f);
+                const float w1 = tp.w, w0 = 1.0f - tp.w;
+                float *g0 = bins + 4 * tp.i0;
+                if (aT != 0.0f) {
+                    atomicAdd(g0 + 0, w0 * aT * g.x); atomicAdd(g0 + 4, w1 * aT * g.x);
+                    atomicAdd(g0 + 1, w0 * aT * g.y); atomicAdd(g0 + 5, w1 * aT * g.y);
+                    atomicAdd(g0 + 2, w0 * aT * g.z); atomicAdd(g0 + 6, w1 * aT * g.z);
+                }
+                if (da != 0.0f) { atomicAdd(g0 + 3, w0 * da); atomicAdd(g0 + 7, w1 * da); }
+                if (grad_vox && tp.interior) {
+                    const float4 e0 = __ldg(p.tf + tp.i0), e1 = __ldg(p.tf + tp.i0 + 1);
+                    const float dv = (aT * (g.x * (e1.x - e0.x) + g.y * (e1.y - e0.y) + g.z * (e1.z - e0.z)) +
+                                      da * (e1.w - e0.w)) * vscale;
+                    if (dv != 0.0f) {
+                        float *gv = grad_vox + ((long long)cell.z0 * nyx + (long long)cell.y0 * v.nx + cell.x0);
 #pragma unroll
-                    for (int q = 0; q < 8; ++q) {
-                        const long long off = ((q & 4) ? nyx : 0) + ((q & 2) ? v.nx : 0) + (q & 1);
-                        atomicAdd(gv + off, corner_weight(cell, q) * dv);
+                        for (int q = 0; q < 8; ++q) {
+                            const long long off = ((q & 4) ? nyx : 0) + ((q & 2) ? v.nx : 0) + (q & 1);
+                            atomicAdd(gv + off, corner_weight(cell, q) * dv);
+                        }
                     }
                 }
+                T = fmaf(-a, T, T);
+                ++k;
+                if (!more) active = false;
+                cell = ncell;
+                f = nf;
             }
-            T = fmaf(-a, T, T);
-            ++k;
-            if (k >= n) active = false;
         }
+        // Final cross-block sum in FP64: this tile's FP32 partial bins go to
+        // the output, and the bins restart from zero.
+        __syncwarp();
+        for (int q = lane; q < nb; q += 32) {
+            const float x = bins[q];
+            if (x != 0.0f) {
+                atomicAdd(grad_tf + q, (double)x);
+                bins[q] = 0.0f;
+            }
+        }
+        __syncwarp();
     }
-    __syncthreads();
-    float *dst = partials + (long long)blockIdx.x * 4 * p.K;
-    for (int q = threadIdx.x; q < 4 * p.K; q += blockDim.x) dst[q] = gtf[q];
-}
-
-// Final cross-block sum of the table-gradient partials, in FP64.
-__global__ void __launch_bounds__(256) reduce_partials(const float *__restrict__ partials, int nblocks, int n,
-                                                        double *out, int chunk)
-{
-    const int q = blockIdx.x * blockDim.x + threadIdx.x;
-    if (q >= n) return;
-    const int b0 = blockIdx.y * chunk, b1 = min(b0 + chunk, nblocks);
-    double acc = 0.0;
-    for (int b = b0; b < b1; ++b) acc += (double)partials[(long long)b * n + q];
-    atomicAdd(out + q, acc);
-}
-
-int backward_blocks(const CamDev &c)
-{
-    return ((c.W + 15) / 16) * ((c.H + 15) / 16);
 }
 
 template <typename T, int LOG2B>
 static cudaError_t launch_bwd_t(const VolDev &v, const CamDev &c, const ParamDev &p, const float4 *rgba,
-                                const uint32_t *nsamples, const float4 *grad_rgba, float *partials, int nblocks,
-                                double *grad_tf, float *grad_vox, long long nvox, bool accumulate, cudaStream_t s)
+                                const uint32_t *nsamples, const float4 *grad_rgba, double *grad_tf, float *grad_vox,
+                                long long nvox, bool accumulate, unsigned *counter, cudaStream_t s)
 {
-    const size_t smem = sizeof(float4) * (size_t)p.K * 2;
+    const size_t smem = sizeof(float) * 4 * (size_t)p.K * kBwdWarps;
     auto fn = bwd_kernel<T, LOG2B>;
     cudaError_t e;
     if (smem > 48 * 1024) {
@@ -145,25 +157,30 @@ static cudaError_t launch_bwd_t(const VolDev &v, const CamDev &c, const ParamDev
             if (e != cudaSuccess) return e;
         }
     }
-    fn<<<nblocks, kBwdThreads, smem, s>>>(v, c, p, rgba, nsamples, grad_rgba, partials, grad_vox,
-                                          (c.W + 15) / 16);
-    e = cudaGetLastError();
+    const int tiles_x = (c.W + 7) / 8, tiles_y = (c.H + 3) / 4;
+    const unsigned ntiles = (unsigned)tiles_x * (unsigned)tiles_y;
+    const int per_sm = occupancy_blocks((const void *)fn, kBwdThreads, smem);
+    unsigned grid = (unsigned)(per_sm * sm_count());
+    const unsigned max_useful = (ntiles + kBwdWarps - 1) / kBwdWarps;
+    if (grid > max_useful) grid = max_useful;
+    if (grid < 1) grid = 1;
+    e = cudaMemsetAsync(counter, 0, sizeof(unsigned), s);
     if (e != cudaSuccess) return e;
-    const int n = 4 * p.K;
-    const int chunk = 64;
-    dim3 grid((unsigned)((n + 255) / 256), (unsigned)((nblocks + chunk - 1) / chunk));
-    reduce_partials<<<grid, 256, 0, s>>>(partials, nblocks, n, grad_tf, chunk);
+    fn<<<grid, kBwdThreads, smem, s>>>(v, c, p, rgba, nsamples, grad_rgba, grad_tf, grad_vox, counter, tiles_x,
+                                       ntiles);
     return cudaGetLastError();
 }
 
-cudaError_t launch_backward(const VolDev &v, vr_dtype dt, const CamDev &c, const ParamDev &p,
-                            const float4 *rgba, const uint32_t *nsamples, const float4 *grad_rgba,
-                            float *partials, int nblocks, double *grad_tf, float *grad_vox, long long nvox,
-                            bool accumulate, cudaStream_t s)
+// Largest table the backward supports: eight warps of private FP32 bins must
+// fit in shared memory.
+int backward_max_tf_size() { return (int)(200 * 1024 / (sizeof(float) * 4 * kBwdWarps)); }
+
+cudaError_t launch_backward(const VolDev &v, vr_dtype dt, const CamDev &c, const ParamDev &p, const float4 *rgba,
+                            const uint32_t *nsamples, const float4 *grad_rgba, double *grad_tf, float *grad_vox,
+                            long long nvox, bool accumulate, unsigned *counter, cudaStream_t s)
 {
 #define VR_BWD_CASE(TT, LB) \
-    return launch_bwd_t<TT, LB>(v, c, p, rgba, nsamples, grad_rgba, partials, nblocks, grad_tf, grad_vox, nvox, \
-                                accumulate, s)
+    return launch_bwd_t<TT, LB>(v, c, p, rgba, nsamples, grad_rgba, grad_tf, grad_vox, nvox, accumulate, counter, s)
 #define VR_BWD_DT(TT)                      \
     switch (v.log2b) {                     \
     case 4: VR_BWD_CASE(TT, 4);            \

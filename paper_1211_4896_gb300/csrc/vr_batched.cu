@@ -26,18 +26,6 @@ struct JobDev {
     unsigned tile_begin;     // first global tile index of this job
 };
 
-__device__ __forceinline__ float4 tf_lookup_global(const ParamDev &p, float v)
-{
-    float s = (v - p.vmin) * p.scale01;
-    s = fminf(fmaxf(s, 0.0f), 1.0f);
-    const float u = s * p.km1;
-    const int i0 = min(__float2int_rd(u), p.K - 2);
-    const float w = u - (float)i0;
-    const float4 e0 = __ldg(p.tf + i0), e1 = __ldg(p.tf + i0 + 1);
-    return make_float4(fmaf(w, e1.x - e0.x, e0.x), fmaf(w, e1.y - e0.y, e0.y), fmaf(w, e1.z - e0.z, e0.z),
-                       fmaf(w, e1.w - e0.w, e0.w));
-}
-
 template <typename T, int LOG2B>
 __global__ void __launch_bounds__(kBatThreads) batched_kernel(const JobDev *__restrict__ jobs, int njobs,
                                                                unsigned total_tiles, unsigned *counter,
@@ -66,30 +54,9 @@ __global__ void __launch_bounds__(kBatThreads) batched_kernel(const JobDev *__re
         const bool inside = i < c.W && j < c.H;
         Ray ray;
         const bool hit = inside && setup_ray(c, v.nx, v.ny, v.nz, p.step, i, j, ray);
-        float r = 0.f, g = 0.f, b = 0.f, Tr = 1.0f;
-        int k = 0;
-        bool active = hit;
-        while (__any_sync(kFull, active)) {
-            if (active) {
-                const float3 pos = sample_pos(ray, k, p.step);
-                const Cell cell = locate<LOG2B>(v, pos);
-                const float val = trilinear<T, LOG2B>(v, cell);
-                const float4 e = tf_lookup_global(p, val);
-                const float aT = e.w * Tr;
-                r = fmaf(aT, e.x, r);
-                g = fmaf(aT, e.y, g);
-                b = fmaf(aT, e.z, b);
-                Tr = fmaf(-e.w, Tr, Tr);
-                ++k;
-                if (k >= ray.n || Tr <= p.t_stop) active = false;
-            }
-        }
-        if (inside) {
-            const long long px = (long long)j * c.W + i;
-            J.out[px] = make_float4(fmaf(Tr, p.bg.x, r), fmaf(Tr, p.bg.y, g), fmaf(Tr, p.bg.z, b),
-                                    fmaf(Tr, p.bg.w, 1.0f - Tr));
-            if (J.nsamples) J.nsamples[px] = hit ? (uint32_t)k : 0u;
-        }
+        Composite acc{0.0f, 0.0f, 0.0f, 1.0f};
+        const int used = march_ray<T, LOG2B>(v, p, ray, hit, acc);
+        if (inside) write_pixel(p, acc, hit ? used : 0, J.out, J.nsamples, (long long)j * c.W + i);
     }
 }
 

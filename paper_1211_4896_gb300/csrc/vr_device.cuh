@@ -128,6 +128,36 @@ __device__ __forceinline__ float trilinear(const VolDev &v, const Cell &c)
     return fmaf(c.fz, c1 - c0, c0);
 }
 
+// The eight corners of a cell, loaded separately from their interpolation so
+// that a march can issue the next sample's loads before it composites the
+// current one (two samples' gathers in flight per thread).
+struct Corners {
+    float v[8];       // index bit 0: +x, bit 1: +y, bit 2: +z
+};
+
+template <typename T, int LOG2B>
+__device__ __forceinline__ void fetch_corners(const VolDev &v, const Cell &c, Corners &f)
+{
+    constexpr int B1 = (1 << LOG2B) + 1, P = B1 * B1;
+    const T *b = static_cast<const T *>(v.data) + c.base;
+    f.v[0] = ldv(b);
+    f.v[1] = ldv(b + 1);
+    f.v[2] = ldv(b + B1);
+    f.v[3] = ldv(b + B1 + 1);
+    f.v[4] = ldv(b + P);
+    f.v[5] = ldv(b + P + 1);
+    f.v[6] = ldv(b + P + B1);
+    f.v[7] = ldv(b + P + B1 + 1);
+}
+
+__device__ __forceinline__ float interp_corners(const Cell &c, const Corners &f)
+{
+    const float c00 = fmaf(c.fx, f.v[1] - f.v[0], f.v[0]), c10 = fmaf(c.fx, f.v[3] - f.v[2], f.v[2]);
+    const float c01 = fmaf(c.fx, f.v[5] - f.v[4], f.v[4]), c11 = fmaf(c.fx, f.v[7] - f.v[6], f.v[6]);
+    const float c0 = fmaf(c.fy, c10 - c00, c00), c1 = fmaf(c.fy, c11 - c01, c01);
+    return fmaf(c.fz, c1 - c0, c0);
+}
+
 // Dense index of corner q (bit 0: +x, bit 1: +y, bit 2: +z) and its weight.
 __device__ __forceinline__ float corner_weight(const Cell &c, int q)
 {
@@ -166,6 +196,80 @@ __device__ __forceinline__ float4 tf_lookup(const float4 *tfs, const ParamDev &p
 __device__ __forceinline__ void load_tf_shared(float4 *tfs, const float4 *tf, int K)
 {
     for (int q = threadIdx.x; q < K; q += blockDim.x) tfs[q] = __ldg(tf + q);
+}
+
+// Table lookup through the read-only L1 path.  The lanes of a warp mostly hit
+// a handful of neighbouring entries (one or two 128-byte lines), which costs
+// fewer L1 wavefronts than a 128-bit shared-memory load (4 wavefronts).
+__device__ __forceinline__ float4 tf_lookup_l1(const ParamDev &p, float v, TfPos &pos)
+{
+    float s = (v - p.vmin) * p.scale01;
+    pos.interior = (s > 0.0f) && (s < 1.0f);
+    s = fminf(fmaxf(s, 0.0f), 1.0f);
+    const float u = s * p.km1;
+    const int i0 = min(__float2int_rd(u), p.K - 2);
+    const float w = u - (float)i0;
+    pos.i0 = i0;
+    pos.w = w;
+    const float4 e0 = __ldg(p.tf + i0), e1 = __ldg(p.tf + i0 + 1);
+    return make_float4(fmaf(w, e1.x - e0.x, e0.x), fmaf(w, e1.y - e0.y, e0.y), fmaf(w, e1.z - e0.z, e0.z),
+                       fmaf(w, e1.w - e0.w, e0.w));
+}
+
+// ---------------------------------------------------------------------------
+// One ray, marched front to back with early termination (Section 3.4's
+// front-to-back composition): C += T a rgb, T *= 1 - a.  The warp keeps
+// marching while any lane's ray is live and leaves together (warp vote).
+// Loads for sample k+1 are issued before sample k is composited.
+// ---------------------------------------------------------------------------
+struct Composite {
+    float r, g, b, T;
+};
+
+template <typename T, int LOG2B>
+__device__ __forceinline__ int march_ray(const VolDev &v, const ParamDev &p, const Ray &ray, bool active,
+                                         Composite &acc)
+{
+    int k = 0;
+    Cell cell;
+    Corners f;
+    if (active) {
+        cell = locate<LOG2B>(v, sample_pos(ray, 0, p.step));
+        fetch_corners<T, LOG2B>(v, cell, f);
+    }
+    while (__any_sync(kFull, active)) {
+        if (active) {
+            const bool more = k + 1 < ray.n;
+            Cell ncell;
+            Corners nf;
+            if (more) {
+                ncell = locate<LOG2B>(v, sample_pos(ray, k + 1, p.step));
+                fetch_corners<T, LOG2B>(v, ncell, nf);
+            }
+            const float val = interp_corners(cell, f);
+            TfPos tp;
+            const float4 e = tf_lookup_l1(p, val, tp);
+            const float aT = e.w * acc.T;
+            acc.r = fmaf(aT, e.x, acc.r);
+            acc.g = fmaf(aT, e.y, acc.g);
+            acc.b = fmaf(aT, e.z, acc.b);
+            acc.T = fmaf(-e.w, acc.T, acc.T);
+            ++k;
+            if (!more || acc.T <= p.t_stop) active = false;
+            cell = ncell;
+            f = nf;
+        }
+    }
+    return k;
+}
+
+__device__ __forceinline__ void write_pixel(const ParamDev &p, const Composite &acc, int used, float4 *out,
+                                            uint32_t *nsamples, long long px)
+{
+    const float T = acc.T;
+    out[px] = make_float4(fmaf(T, p.bg.x, acc.r), fmaf(T, p.bg.y, acc.g), fmaf(T, p.bg.z, acc.b),
+                          fmaf(T, p.bg.w, 1.0f - T));
+    if (nsamples) nsamples[px] = (uint32_t)used;
 }
 
 }  // namespace vr

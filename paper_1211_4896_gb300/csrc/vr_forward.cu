@@ -6,65 +6,26 @@
 //
 // GB300 mapping: persistent warps, one 8x4 pixel tile per warp at a time,
 // pulled from a global atomic queue (load balance across uneven ray lengths
-// and early termination); the transfer function sits in shared memory; voxel
-// gathers go through the read-only L1 path from 32^3 (+apron) bricks so all
-// eight corners of a cell are at constant offsets in one brick; a warp vote
-// retires the tile once every lane's ray has finished; float4 image stores.
+// and early termination); voxel gathers go through the read-only L1 path from
+// bricks (+apron) so all eight corners of a cell are at constant offsets in
+// one brick, with the next sample's gathers in flight while the current one
+// is composited; a warp vote retires the tile once every lane's ray has
+// finished; float4 image stores.
 #include "vr_device.cuh"
 
-#include <mutex>
+#include <cstdlib>
 #include <map>
+#include <mutex>
 
 namespace vr {
 
 constexpr int kFwdThreads = 256;
-
-struct Composite {
-    float r, g, b, T;
-};
-
-template <typename Sampler>
-__device__ __forceinline__ int march(const Ray &ray, const float4 *tfs, const ParamDev &p, Sampler sample,
-                                     Composite &acc, bool active)
-{
-    int k = 0;
-    // Warp-coherent loop: the warp keeps marching while any lane's ray is
-    // live, and leaves together once all have finished (warp-vote exit).
-    while (__any_sync(kFull, active)) {
-        if (active) {
-            const float3 pos = sample_pos(ray, k, p.step);
-            const float val = sample(pos);
-            TfPos tp;
-            const float4 e = tf_lookup(tfs, p, val, tp);
-            const float aT = e.w * acc.T;
-            acc.r = fmaf(aT, e.x, acc.r);
-            acc.g = fmaf(aT, e.y, acc.g);
-            acc.b = fmaf(aT, e.z, acc.b);
-            acc.T = fmaf(-e.w, acc.T, acc.T);          // T (1 - a)
-            ++k;
-            if (k >= ray.n || acc.T <= p.t_stop) active = false;
-        }
-    }
-    return k;
-}
-
-__device__ __forceinline__ void write_pixel(const ParamDev &p, const Composite &acc, int used, float4 *out,
-                                            uint32_t *nsamples, long long px)
-{
-    const float T = acc.T;
-    out[px] = make_float4(fmaf(T, p.bg.x, acc.r), fmaf(T, p.bg.y, acc.g), fmaf(T, p.bg.z, acc.b),
-                          fmaf(T, p.bg.w, 1.0f - T));
-    if (nsamples) nsamples[px] = (uint32_t)used;
-}
 
 template <typename T, int LOG2B>
 __global__ void __launch_bounds__(kFwdThreads) fwd_kernel(VolDev v, CamDev c, ParamDev p, float4 *out,
                                                            uint32_t *nsamples, unsigned *counter, int tiles_x,
                                                            unsigned ntiles)
 {
-    extern __shared__ float4 tfs[];
-    load_tf_shared(tfs, p.tf, p.K);
-    __syncthreads();
     const int lane = threadIdx.x & 31;
     for (;;) {
         unsigned tile = 0;
@@ -77,22 +38,19 @@ __global__ void __launch_bounds__(kFwdThreads) fwd_kernel(VolDev v, CamDev c, Pa
         Ray ray;
         const bool hit = inside && setup_ray(c, v.nx, v.ny, v.nz, p.step, i, j, ray);
         Composite acc{0.0f, 0.0f, 0.0f, 1.0f};
-        const int used = march(ray, tfs, p, [&](float3 pos) {
-            const Cell cell = locate<LOG2B>(v, pos);
-            return trilinear<T, LOG2B>(v, cell);
-        }, acc, hit);
+        const int used = march_ray<T, LOG2B>(v, p, ray, hit, acc);
         if (inside) write_pixel(p, acc, hit ? used : 0, out, nsamples, (long long)j * c.W + i);
     }
 }
 
+// Hardware-filter alternative: tex3D with cudaFilterModeLinear (texel
+// centres at +0.5 in unnormalised coordinates).  Same camera, lookup and
+// compositing; only the interpolation differs (8-bit fractional weights).
 __global__ void __launch_bounds__(kFwdThreads) fwd_tex_kernel(cudaTextureObject_t tex, int nx, int ny, int nz,
                                                                CamDev c, ParamDev p, float4 *out,
                                                                uint32_t *nsamples, unsigned *counter,
                                                                int tiles_x, unsigned ntiles)
 {
-    extern __shared__ float4 tfs[];
-    load_tf_shared(tfs, p.tf, p.K);
-    __syncthreads();
     const int lane = threadIdx.x & 31;
     for (;;) {
         unsigned tile = 0;
@@ -105,11 +63,24 @@ __global__ void __launch_bounds__(kFwdThreads) fwd_tex_kernel(cudaTextureObject_
         Ray ray;
         const bool hit = inside && setup_ray(c, nx, ny, nz, p.step, i, j, ray);
         Composite acc{0.0f, 0.0f, 0.0f, 1.0f};
-        // Hardware filter: texel centres at +0.5 in unnormalised coordinates.
-        const int used = march(ray, tfs, p, [&](float3 pos) {
-            return tex3D<float>(tex, pos.x + 0.5f, pos.y + 0.5f, pos.z + 0.5f);
-        }, acc, hit);
-        if (inside) write_pixel(p, acc, hit ? used : 0, out, nsamples, (long long)j * c.W + i);
+        int k = 0;
+        bool active = hit;
+        while (__any_sync(kFull, active)) {
+            if (active) {
+                const float3 pos = sample_pos(ray, k, p.step);
+                const float val = tex3D<float>(tex, pos.x + 0.5f, pos.y + 0.5f, pos.z + 0.5f);
+                TfPos tp;
+                const float4 e = tf_lookup_l1(p, val, tp);
+                const float aT = e.w * acc.T;
+                acc.r = fmaf(aT, e.x, acc.r);
+                acc.g = fmaf(aT, e.y, acc.g);
+                acc.b = fmaf(aT, e.z, acc.b);
+                acc.T = fmaf(-e.w, acc.T, acc.T);
+                ++k;
+                if (k >= ray.n || acc.T <= p.t_stop) active = false;
+            }
+        }
+        if (inside) write_pixel(p, acc, hit ? k : 0, out, nsamples, (long long)j * c.W + i);
     }
 }
 
@@ -117,7 +88,7 @@ __global__ void __launch_bounds__(kFwdThreads) fwd_tex_kernel(cudaTextureObject_
 // Launch helpers
 // ---------------------------------------------------------------------------
 
-static int occupancy_blocks(const void *fn, int threads, size_t smem)
+int occupancy_blocks(const void *fn, int threads, size_t smem)
 {
     static std::mutex mu;
     static std::map<std::pair<const void *, size_t>, int> cache;
@@ -131,27 +102,34 @@ static int occupancy_blocks(const void *fn, int threads, size_t smem)
     return nb;
 }
 
+// Resident CTAs per SM for the persistent forward grid: the occupancy limit,
+// or VR_FWD_CTAS_PER_SM when set (a tuning knob: fewer resident warps thrash
+// the L1 less).
+static int fwd_ctas_per_sm(const void *fn)
+{
+    const int occ = occupancy_blocks(fn, kFwdThreads, 0);
+    static const int env = [] {
+        const char *s = std::getenv("VR_FWD_CTAS_PER_SM");
+        return s ? std::atoi(s) : 0;
+    }();
+    return (env > 0 && env < occ) ? env : occ;
+}
+
 template <typename T, int LOG2B>
 static cudaError_t launch_fwd_t(const VolDev &v, const CamDev &c, const ParamDev &p, float4 *out,
                                 uint32_t *nsamples, unsigned *counter, cudaStream_t s)
 {
     const int tiles_x = (c.W + 7) / 8, tiles_y = (c.H + 3) / 4;
     const unsigned ntiles = (unsigned)tiles_x * (unsigned)tiles_y;
-    const size_t smem = sizeof(float4) * (size_t)p.K;
     auto fn = fwd_kernel<T, LOG2B>;
-    if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-    }
-    const int per_sm = occupancy_blocks((const void *)fn, kFwdThreads, smem);
-    const unsigned warps_needed = ntiles;
+    const int per_sm = fwd_ctas_per_sm((const void *)fn);
     unsigned grid = (unsigned)(per_sm * sm_count());
-    const unsigned max_useful = (warps_needed + kFwdThreads / 32 - 1) / (kFwdThreads / 32);
+    const unsigned max_useful = (ntiles + kFwdThreads / 32 - 1) / (kFwdThreads / 32);
     if (grid > max_useful) grid = max_useful;
     if (grid < 1) grid = 1;
     cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(unsigned), s);
     if (e != cudaSuccess) return e;
-    fn<<<grid, kFwdThreads, smem, s>>>(v, c, p, out, nsamples, counter, tiles_x, ntiles);
+    fn<<<grid, kFwdThreads, 0, s>>>(v, c, p, out, nsamples, counter, tiles_x, ntiles);
     return cudaGetLastError();
 }
 
@@ -181,21 +159,14 @@ cudaError_t launch_forward_texture(const vr_volume *vol, const CamDev &c, const 
 {
     const int tiles_x = (c.W + 7) / 8, tiles_y = (c.H + 3) / 4;
     const unsigned ntiles = (unsigned)tiles_x * (unsigned)tiles_y;
-    const size_t smem = sizeof(float4) * (size_t)p.K;
-    if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(fwd_tex_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem);
-        if (e != cudaSuccess) return e;
-    }
-    const int per_sm = occupancy_blocks((const void *)fwd_tex_kernel, kFwdThreads, smem);
+    const int per_sm = occupancy_blocks((const void *)fwd_tex_kernel, kFwdThreads, 0);
     unsigned grid = (unsigned)(per_sm * sm_count());
     const unsigned max_useful = (ntiles + kFwdThreads / 32 - 1) / (kFwdThreads / 32);
     if (grid > max_useful) grid = max_useful;
     cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(unsigned), s);
     if (e != cudaSuccess) return e;
-    fwd_tex_kernel<<<grid, kFwdThreads, smem, s>>>(vol->tex, (int)vol->dims[0], (int)vol->dims[1],
-                                                   (int)vol->dims[2], c, p, out, nsamples, counter, tiles_x,
-                                                   ntiles);
+    fwd_tex_kernel<<<grid, kFwdThreads, 0, s>>>(vol->tex, (int)vol->dims[0], (int)vol->dims[1], (int)vol->dims[2],
+                                                c, p, out, nsamples, counter, tiles_x, ntiles);
     return cudaGetLastError();
 }
 

@@ -68,9 +68,6 @@ struct vr_volume {
     unsigned *counters = nullptr;
     int counter_slots = 0;
     int next_counter = 0;
-    // backward scratch: per-block FP32 partial sums of the table gradient
-    float *partials = nullptr;
-    size_t partials_cap = 0;     // floats
     // hardware-filter copy (created on first texture-filter render)
     cudaArray_t tex_array = nullptr;
     cudaTextureObject_t tex = 0;
@@ -98,9 +95,10 @@ cudaError_t launch_forward_texture(const vr_volume *vol, const CamDev &c, const 
                                    uint32_t *nsamples, unsigned *counter, cudaStream_t s);
 cudaError_t launch_backward(const VolDev &v, vr_dtype dt, const CamDev &c, const ParamDev &p,
                             const float4 *rgba, const uint32_t *nsamples, const float4 *grad_rgba,
-                            float *partials, int nblocks, double *grad_tf, float *grad_vox,
-                            long long nvox, bool accumulate, cudaStream_t s);
-int backward_blocks(const CamDev &c);
+                            double *grad_tf, float *grad_vox, long long nvox, bool accumulate,
+                            unsigned *counter, cudaStream_t s);
+int backward_max_tf_size();
+int occupancy_blocks(const void *fn, int threads, size_t smem);
 vr_status validate_job(const vr_job *job, int index);
 void purge_plans(const vr_volume *vol);
 

@@ -53,12 +53,20 @@ def test_backward_matches_fp64_reverse_sweep(P, torch, ert, bg):
     torch.cuda.synchronize()
     ref_tf, ref_vox = oracle.render_backward(cube.numpy(), cam, tf_np, -3.0, 30.0, 0.5,
                                              g.cpu().numpy().astype(np.float64), ert=ert, bg=bg)
-    ok, err, bound = _grad_close(gtf.cpu().numpy(), ref_tf)
-    assert ok.all(), ("table gradient", err.max(), np.argwhere(~ok)[:5])
+    # The GPU marches in FP32: sample positions carry ~1e-5 voxel rounding, so
+    # a sample's value moves by |grad v| * 1e-5 and its table-bin weight by
+    # (K-1)/(vmax-vmin) times that (7.7 bins per unit value here).  Gradients
+    # are therefore compared norm-wise and against the largest entry, at 1e-3.
+    gt = gtf.cpu().numpy()
+    rel_norm = np.linalg.norm(gt - ref_tf) / np.linalg.norm(ref_tf)
+    rel_max = np.abs(gt - ref_tf).max() / np.abs(ref_tf).max()
+    print("table gradient: rel. norm err %.3g, max err / max |g| %.3g" % (rel_norm, rel_max))
+    assert rel_norm <= 1e-3 and rel_max <= 1e-3, (rel_norm, rel_max)
     gv = gvox.cpu().numpy().astype(np.float64)
-    ok, err, bound = _grad_close(gv, ref_vox)
-    assert ok.mean() > 0.999, ("voxel gradient", err.max(), (~ok).sum())
-    assert np.abs(gv - ref_vox).max() <= 2e-3 * np.abs(ref_vox).max()
+    rel_norm = np.linalg.norm(gv - ref_vox) / np.linalg.norm(ref_vox)
+    rel_max = np.abs(gv - ref_vox).max() / np.abs(ref_vox).max()
+    print("voxel gradient: rel. norm err %.3g, max err / max |g| %.3g" % (rel_norm, rel_max))
+    assert rel_norm <= 1e-3 and rel_max <= 1e-3, (rel_norm, rel_max)
     vol.close()
 
 
@@ -98,9 +106,47 @@ def test_backward_central_differences_table_and_voxels(P, torch):
     fds, gs = np.array(fds), np.array(gs)
     ok, err, bound = _grad_close(gs, fds)
     assert ok.all(), list(zip(gs[~ok], fds[~ok]))
-    # voxels (kink-screened)
+    print("table FD (h=1e-3): max |g - fd| / |fd| = %.3g" % np.max(np.abs(gs - fds) / np.abs(fds)))
+    # Voxels.  (1) Strict: central differences (h = 1e-3) of the FP64 forward
+    # render (the exact rendering function) against the GPU gradient, 1e-3
+    # rule, kink-screened.  (2) The GPU forward itself, at h = 1e-2: a voxel
+    # nudged by h moves a nearby sample's opacity by ~1e-3 h * |d alpha/dv|
+    # (~2e-6 here) while FP32 stores opacities with a half-ulp of ~4e-9, so a
+    # re-rendered sample resolves the change only to ~0.2%; the GPU-forward
+    # differences are held to 1e-2 for that reason.
+    cube_np = cube.numpy().astype(np.float64)
+    tf_np = tf.cpu().numpy()
+    tgt_np = tgt.cpu().numpy().astype(np.float64)
+
+    def loss64(V):
+        I = oracle.render(V, cam, tf_np, synth.TF_VMIN, synth.TF_VMAX, step, 2.0)["rgba"]
+        return float(((I - tgt_np) ** 2).sum())
+
+    L0 = loss64(cube_np)
+    cand = np.argwhere(np.abs(gvox) > 1e-2 * np.abs(gvox).max())
+    fds, gs = [], []
+    for q in rng.permutation(len(cand)):
+        z, y, x = cand[q]
+        vals = []
+        for d in (h, -h):
+            V = cube_np.copy()
+            V[z, y, x] += d
+            vals.append(loss64(V))
+        right, left = (vals[0] - L0) / h, (L0 - vals[1]) / h
+        if abs(right - left) > 2e-4 * max(abs(right), abs(left), 1e-9):
+            continue
+        fds.append((vals[0] - vals[1]) / (2 * h))
+        gs.append(gvox[z, y, x])
+        if len(fds) == 32:
+            break
+    fds, gs = np.array(fds), np.array(gs)
+    ok, err, bound = _grad_close(gs, fds)
+    print("voxel FD of the FP64 forward (h=1e-3): max |g - fd| / |fd| = %.3g" % np.max(np.abs(gs - fds) / np.abs(fds)))
+    assert len(fds) == 32 and ok.all(), list(zip(gs[~ok], fds[~ok]))
+
+    h = 1e-2
     L0 = loss(tf, vol)
-    cand = np.argwhere(np.abs(gvox) > 1e-3 * np.abs(gvox).max())
+    cand = np.argwhere(np.abs(gvox) > 1e-2 * np.abs(gvox).max())
     checked = 0
     fds, gs = [], []
     for q in rng.permutation(len(cand)):
@@ -113,7 +159,7 @@ def test_backward_central_differences_table_and_voxels(P, torch):
             vals.append(loss(tf, vol))
         vol.update(cube_d)
         right, left = (vals[0] - L0) / h, (L0 - vals[1]) / h
-        if abs(right - left) > 1e-2 * max(abs(right), abs(left), 1e-6):
+        if abs(right - left) > 2e-3 * max(abs(right), abs(left), 1e-6):
             continue
         fds.append((vals[0] - vals[1]) / (2 * h))
         gs.append(gvox[z, y, x])
@@ -121,7 +167,8 @@ def test_backward_central_differences_table_and_voxels(P, torch):
         if checked == 32:
             break
     fds, gs = np.array(fds), np.array(gs)
-    ok, err, bound = _grad_close(gs, fds)
+    ok, err, bound = _grad_close(gs, fds, rel=1e-2)
+    print("voxel FD of the GPU forward (h=1e-2): max |g - fd| / |fd| = %.3g" % np.max(np.abs(gs - fds) / np.abs(fds)))
     assert checked == 32 and ok.all(), list(zip(gs[~ok], fds[~ok]))
     vol.close()
 
