@@ -207,6 +207,32 @@ vr_status vr_render_batched(const vr_job *jobs, int n, const vr_batch_opts *opts
  * fastest into *best.  best->use_graph is left unchanged. */
 vr_status vr_autotune_batched(const vr_job *jobs, int n, vr_batch_opts *best, void *cuda_stream);
 
+/* ------------------------------------------------------------------------
+ * Batched render that allocates nothing (the paper has no counterpart).
+ *
+ * For callers that cannot call cudaMalloc while rendering: code recorded
+ * into a CUDA stream capture (an allocation would break the capture), services
+ * with a fixed device-memory budget, or processes whose device memory belongs
+ * to another allocator's pool.  vr_render_batched allocates a descriptor table
+ * and a work counter for every new job list; this variant keeps both in one
+ * static device array sized for VR_NOALLOC_MAX_JOBS jobs (about 64 KB, held by
+ * every GPU that loads the library until the process exits), uploads the
+ * descriptors with cudaMemcpyAsync and zeroes the counter with
+ * cudaMemsetAsync on cuda_stream.  The caller still passes the volumes and the
+ * outputs.  Jobs are rendered exactly as by vr_render_batched (same kernel);
+ * tile_w x tile_h is the warp's ray tile (0, 0 = 8 x 4).
+ *   - n > VR_NOALLOC_MAX_JOBS returns VR_ERR_INVALID_ARG and launches nothing.
+ *   - The first call on a device looks up the device address of the static
+ *     array (cudaGetSymbolAddress) and the kernel's occupancy; make that first
+ *     call before any stream capture.
+ *   - Every call reuses the same array: calls that overlap on the GPU (two
+ *     streams, or two host threads) race and must be serialised by the caller.
+ * Errors: INVALID_ARG, UNSUPPORTED, CUDA.
+ * ---------------------------------------------------------------------- */
+#define VR_NOALLOC_MAX_JOBS 256
+
+vr_status vr_render_batched_noalloc(const vr_job *jobs, int n, int tile_w, int tile_h, void *cuda_stream);
+
 /* Human-readable message of the last failed call on this thread ("" if none). */
 const char *vr_last_error(void);
 

@@ -53,7 +53,9 @@ class vr_batch_opts(C.Structure):
 
 # every symbol include/vr.h declares
 EXPORTS = ("vr_volume_create", "vr_volume_update", "vr_volume_destroy", "vr_volume_info", "vr_render",
-           "vr_render_backward", "vr_render_batched", "vr_autotune_batched", "vr_last_error", "vr_version")
+           "vr_render_backward", "vr_render_batched", "vr_autotune_batched", "vr_render_batched_noalloc",
+           "vr_last_error", "vr_version")
+VR_NOALLOC_MAX_JOBS = 256
 
 _lock = threading.Lock()
 _lib = None
@@ -86,8 +88,10 @@ def load() -> C.CDLL:
         L.vr_render_backward.argtypes = [vp, P(vr_camera), P(vr_params), vp, vp, vp, vp, vp, C.c_uint, vp]
         L.vr_render_batched.argtypes = [P(vr_job), C.c_int, P(vr_batch_opts), vp]
         L.vr_autotune_batched.argtypes = [P(vr_job), C.c_int, P(vr_batch_opts), vp]
+        L.vr_render_batched_noalloc.argtypes = [P(vr_job), C.c_int, C.c_int, C.c_int, vp]
         for name in ("vr_volume_create", "vr_volume_update", "vr_volume_destroy", "vr_volume_info", "vr_render",
-                     "vr_render_backward", "vr_render_batched", "vr_autotune_batched"):
+                     "vr_render_backward", "vr_render_batched", "vr_autotune_batched",
+                     "vr_render_batched_noalloc"):
             getattr(L, name).restype = C.c_int
         L.vr_last_error.argtypes = []
         L.vr_last_error.restype = C.c_char_p
@@ -179,6 +183,13 @@ def vr_autotune_batched(jobs, opts: vr_batch_opts | None = None, stream: int = 0
     best = opts if opts is not None else vr_batch_opts(0, 0, 0, 0)
     _check("vr_autotune_batched", load().vr_autotune_batched(arr, len(jobs), C.byref(best), stream))
     return best
+
+
+def vr_render_batched_noalloc(jobs, tile_w: int = 0, tile_h: int = 0, stream: int = 0):
+    """Same jobs as vr_render_batched, with no device allocation (static scratch)."""
+    arr = (vr_job * len(jobs))(*jobs)
+    _check("vr_render_batched_noalloc", load().vr_render_batched_noalloc(arr, len(jobs), int(tile_w), int(tile_h),
+                                                                         stream))
 
 
 def vr_version() -> str:

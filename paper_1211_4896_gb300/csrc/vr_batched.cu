@@ -328,3 +328,133 @@ done:
     cudaEventDestroy(e1);
     return result;
 }
+
+// ---------------------------------------------------------------------------
+// Batched render without any allocation.
+//
+// vr_render_batched allocates a descriptor table and a work counter on the
+// device the first time it sees a job list.  Callers that must not allocate
+// device memory at call time -- code running inside a stream capture, where
+// an allocation would break the capture; services with a fixed memory
+// budget; processes whose memory belongs to another allocator's pool -- use
+// vr_render_batched_noalloc instead.  Its scratch (the descriptors of up to
+// kNoAllocMaxJobs jobs and the counter) is one static device array of about
+// 64 KB that every GPU loading this library holds until the process exits.
+// Every call reuses that array, so calls that overlap on the GPU race.
+// ---------------------------------------------------------------------------
+namespace vr {
+
+constexpr int kNoAllocMaxJobs = VR_NOALLOC_MAX_JOBS;
+
+struct NoAllocScratch {
+    unsigned counter;
+    unsigned pad[63];                     // keeps the descriptor table 256-byte aligned
+    JobDev jobs[kNoAllocMaxJobs];
+};
+
+static __device__ __align__(256) NoAllocScratch g_noalloc_scratch;
+
+// Device address of g_noalloc_scratch per device, looked up once per device
+// (host code only sees a stand-in for the symbol, never its device address).
+static NoAllocScratch *noalloc_scratch_ptr(vr_status &st)
+{
+    static std::mutex mu;
+    static NoAllocScratch *ptrs[64] = {nullptr};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) {
+        st = cuda_fail(e, "cudaGetDevice");
+        return nullptr;
+    }
+    if (dev < 0 || dev >= 64) {
+        st = (set_error("vr_render_batched_noalloc: device index out of range"), VR_ERR_UNSUPPORTED);
+        return nullptr;
+    }
+    std::lock_guard<std::mutex> g(mu);
+    if (!ptrs[dev]) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p) {
+            st = cuda_fail(e != cudaSuccess ? e : cudaErrorInvalidSymbol, "cudaGetSymbolAddress(noalloc scratch)");
+            return nullptr;
+        }
+        ptrs[dev] = static_cast<NoAllocScratch *>(p);
+    }
+    st = VR_OK;
+    return ptrs[dev];
+}
+
+}  // namespace vr
+
+extern "C" vr_status vr_render_batched_noalloc(const vr_job *jobs, int n, int tile_w, int tile_h, void *cuda_stream)
+{
+    set_error("");
+    if (!jobs || n < 1) return (set_error("jobs must be non-NULL with n >= 1"), VR_ERR_INVALID_ARG);
+    if (n > kNoAllocMaxJobs)
+        return (set_error("vr_render_batched_noalloc: n = " + std::to_string(n) + " exceeds the maximum of " +
+                          std::to_string(kNoAllocMaxJobs) + " jobs held by its static scratch"),
+                VR_ERR_INVALID_ARG);
+    if (tile_w == 0) tile_w = 8;
+    if (tile_h == 0) tile_h = 32 / tile_w;
+    const int log2_tw = log2_of(tile_w);
+    if (log2_tw < 0 || tile_w * tile_h != 32)
+        return (set_error("tile_w * tile_h must be 32 with tile_w a power of two"), VR_ERR_INVALID_ARG);
+    for (int q = 0; q < n; ++q) {
+        vr_status st = validate_job(&jobs[q], q);
+        if (st != VR_OK) return st;
+    }
+    // descriptors, built in a fixed host buffer (no host allocation either)
+    static thread_local JobDev hj[kNoAllocMaxJobs];
+    vr_dtype dt = VR_F32;
+    int log2b = 5;
+    unsigned total = 0;
+    for (int q = 0; q < n; ++q) {
+        const vr_job &J = jobs[q];
+        if (!J.dev_rgba_out || !is_aligned16(J.dev_rgba_out))
+            return (set_error("jobs[" + std::to_string(q) + "].dev_rgba_out must be non-NULL and 16-byte aligned"),
+                    VR_ERR_INVALID_ARG);
+        if (J.params.filter != VR_FILTER_SOFTWARE)
+            return (set_error("vr_render_batched_noalloc: software filter only"), VR_ERR_UNSUPPORTED);
+        if (q == 0) {
+            dt = J.vol->store_dtype;
+            log2b = J.vol->log2b;
+        } else if (J.vol->store_dtype != dt || J.vol->log2b != log2b) {
+            return (set_error("vr_render_batched_noalloc: all volumes must share store dtype and brick size"),
+                    VR_ERR_UNSUPPORTED);
+        }
+        JobDev &d = hj[q];
+        prepare_camera(J.vol, &J.cam, &d.c);
+        prepare_params(&J.params, &d.p);
+        d.v = vol_dev(J.vol);
+        d.out = reinterpret_cast<float4 *>(J.dev_rgba_out);
+        d.nsamples = J.dev_nsamples_out;
+        d.tiles_x = (J.cam.width + tile_w - 1) / tile_w;
+        const unsigned tiles_y = (unsigned)((J.cam.height + tile_h - 1) / tile_h);
+        d.tile_begin = total;
+        const unsigned long long t = (unsigned long long)total + (unsigned long long)d.tiles_x * tiles_y;
+        if (t > 0xFFFFFFF0ull) return (set_error("vr_render_batched_noalloc: too many ray tiles"), VR_ERR_INVALID_ARG);
+        total = (unsigned)t;
+    }
+    vr_status st;
+    NoAllocScratch *scratch = noalloc_scratch_ptr(st);
+    if (!scratch) return st;
+    BatchFn fn = pick_kernel(dt, log2b);
+    if (!fn) return (set_error("vr_render_batched_noalloc: unsupported brick size"), VR_ERR_UNSUPPORTED);
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void *)fn, kBatThreads, 0) != cudaSuccess ||
+        per_sm < 1)
+        per_sm = 1;
+    unsigned grid = (unsigned)(per_sm * sm_count());
+    const unsigned useful = (total + kBatThreads / 32 - 1) / (kBatThreads / 32);
+    if (grid > useful) grid = useful ? useful : 1;
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    // The counter must start at zero; the descriptors overwrite the last call's.
+    cudaError_t e = cudaMemsetAsync(&scratch->counter, 0, sizeof(unsigned), s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(scratch->jobs, hj, sizeof(JobDev) * (size_t)n, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return cuda_fail(e, "vr_render_batched_noalloc: scratch upload");
+    fn<<<grid, kBatThreads, 0, s>>>(scratch->jobs, n, total, &scratch->counter, log2_tw);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "vr_render_batched_noalloc launch");
+    return VR_OK;
+}
