@@ -406,12 +406,212 @@ def run_ours(args, rank, world, local_rank):
     return 0
 
 
+# ---------------------------------------------------------------------------
+# Other workloads (reported lines; the default workload above is the
+# benchmark's contract line)
+# ---------------------------------------------------------------------------
+
+def _time_ms(torch, fn, reps):
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    fn()
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(reps):
+        fn()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def _px_err(img, ns, ref, rows):
+    g = img.astype(np.float64)
+    errs, excl = [], 0
+    for r in rows:
+        same = ns[r] == ref["n_used"][r]
+        excl += int((~same).sum())
+        errs.append(np.abs(g[r] - ref["rgba"][r])[same])
+    e = np.concatenate(errs)
+    return {"max_abs": float(e.max()), "mean_abs": float(e.mean()), "excluded_ties": excl}
+
+
+def run_plain_128(args):
+    """128^3 f32, orthographic along +z, 256^2, step 0.5, no early termination."""
+    import torch
+    import oracle
+    import paper_1211_4896_gb300 as P
+    pre = synth.preset_plain_128()
+    dev = torch.device("cuda")
+    cube = synth.hi_cube(pre["dims"], pre["n_blobs"], pre["n_disks"], pre["seed"])
+    vol = P.Volume(cube.to(dev), "f32")
+    tf_np = synth.tf_ramp(256)
+    tf = torch.from_numpy(tf_np).to(dev)
+    cam = pre["cameras"][0]
+    out = torch.empty((256, 256, 4), device=dev)
+    ns = torch.empty((256, 256), device=dev, dtype=torch.int32)
+    f = lambda: P.render(vol, cam, tf, synth.TF_VMIN, synth.TF_VMAX, pre["step"], pre["ert"], out=out, nsamples=ns)  # noqa
+    ms = _time_ms(torch, f, max(20, args.steps))
+    samples = int(ns.sum())
+    t0 = time.perf_counter()
+    ref = oracle.render(cube.numpy(), cam, tf_np, synth.TF_VMIN, synth.TF_VMAX, pre["step"], pre["ert"])
+    t_cpu = time.perf_counter() - t0
+    err = _px_err(out.cpu().numpy(), ns.cpu().numpy(), ref, range(256))
+    print(json.dumps({"workload": "plain_128", "gsamples_per_s": samples / ms / 1e6, "ms": ms, "samples": samples,
+                      "px_err": err, "oracle_gsamples_per_s": samples / t_cpu / 1e9, "oracle_cores": os.cpu_count()}))
+
+
+def run_precision_4096(args):
+    """4096x4096x1024 HI-like cube (blob and disk densities of the smaller
+    workloads), stored f32 / f16 / bf16; four 1080p perspective views, step 1,
+    ERT 0.99; pixel error against the FP64 oracle on a 256^3 crop."""
+    import torch
+    import oracle
+    import paper_1211_4896_gb300 as P
+    dev = torch.device("cuda")
+    dims = (4096, 4096, 1024)
+    nb = int(round(20 * (4096 * 4096 * 1024) / 128 ** 3))
+    nd = int(round(200 * (4096 * 4096 * 1024) / 1024 ** 3))
+    cube = synth.hi_cube(dims, nb, nd, seed=3, device=dev)
+    cams = synth.orbit_cameras(dims, 4, 40.0, 1920, 1080)
+    tf_np = synth.tf_ramp(256)
+    tf = torch.from_numpy(tf_np).to(dev)
+    res = {"workload": "precision_4096", "dims": dims, "blobs": nb, "disks": nd}
+    crop = cube[384:640, 1920:2176, 1920:2176].contiguous()          # 256^3 crop (z, y, x)
+    crop_np = crop.cpu().numpy()
+    crop_cams = synth.orbit_cameras((256, 256, 256), 4, 40.0, 1920, 1080, start_deg=30.0)
+    rows = [300 + 60 * q for q in range(8)]
+    refs = []
+    for cam in crop_cams:
+        r = {}
+        for row in rows:
+            o = oracle.render(crop_np, cam, tf_np, synth.TF_VMIN, synth.TF_VMAX, 1.0, 0.99, rows=(row, row + 1))
+            for k, v in o.items():
+                r.setdefault(k, np.zeros_like(v))[row] = v[row]
+        refs.append(r)
+    base = None
+    for store in ("f32", "f16", "bf16"):
+        vol = P.Volume(cube, store)
+        outs = [torch.empty((1080, 1920, 4), device=dev) for _ in cams]
+        nss = [torch.empty((1080, 1920), device=dev, dtype=torch.int32) for _ in cams]
+
+        def f():
+            for c, o, n in zip(cams, outs, nss):
+                P.render(vol, c, tf, synth.TF_VMIN, synth.TF_VMAX, 1.0, 0.99, out=o, nsamples=n)
+        ms = _time_ms(torch, f, 3)
+        samples = sum(int(n.sum()) for n in nss)
+        vol.close()
+        cvol = P.Volume(crop, store)
+        errs = []
+        for cam, ref in zip(crop_cams, refs):
+            img, ns = P.render(cvol, cam, tf, synth.TF_VMIN, synth.TF_VMAX, 1.0, 0.99)
+            errs.append(_px_err(img.cpu().numpy(), ns.cpu().numpy(), ref, rows))
+        cvol.close()
+        gs = samples / ms / 1e6
+        base = base or gs
+        res[store] = {"gsamples_per_s": gs, "ms_4_views": ms, "fps": 4e3 / ms, "vs_f32": gs / base,
+                      "bricked_gb": vol.info["bytes"] / 1e9,
+                      "crop_px_err_max": max(e["max_abs"] for e in errs),
+                      "crop_px_err_mean": float(np.mean([e["mean_abs"] for e in errs]))}
+        torch.cuda.empty_cache()
+    print(json.dumps(res))
+
+
+def run_batch_64(args):
+    """64 uneven f16 HI-like cubes (64^3 .. 512x512x1024), each with its own
+    perspective camera, image (512^2 .. 1024^2) and random piecewise-linear
+    table: one persistent CUDA-graph launch against 64 vr_render launches."""
+    import torch
+    import paper_1211_4896_gb300 as P
+    from paper_1211_4896_gb300 import _lib as L
+    dev = torch.device("cuda")
+    dims_list = synth.batch_dims(seed=4, n=64)
+    jobs = []
+    for q, dims in enumerate(dims_list):
+        vox = dims[0] * dims[1] * dims[2]
+        cube = synth.hi_cube(dims, max(1, int(round(20 * vox / 128 ** 3))), max(0, int(round(200 * vox / 1024 ** 3))),
+                             seed=4000 + q, device=dev)
+        vol = P.Volume(cube, "f16")
+        del cube
+        W, H = synth.batch_image_size(seed=5000 + q)
+        cam = synth.camera_random_persp(dims, seed=6000 + q, width=W, height=H)
+        tf = torch.from_numpy(synth.tf_random_pwl(seed=7000 + q)).to(dev)
+        jobs.append(dict(vol=vol, cam=cam, tf=tf, vmin=-3.0, vmax=50.0, step=1.0, ert=0.99,
+                         out=torch.empty((H, W, 4), device=dev),
+                         nsamples=torch.empty((H, W), device=dev, dtype=torch.int32)))
+    torch.cuda.empty_cache()
+    s = int(torch.cuda.current_stream().cuda_stream)
+    cj = P.render_batched(jobs, use_graph=False)
+    best = L.vr_autotune_batched(cj, L.vr_batch_opts(1, 0, 0, 0), s)
+    opts = L.vr_batch_opts(1, best.tile_w, best.tile_h, best.ctas_per_sm)
+    L.vr_render_batched(cj, opts, s)
+    t_graph = _time_ms(torch, lambda: L.vr_render_batched(cj, opts, s), max(5, args.steps))
+    ccams = [(j["vol"].handle, L.make_camera(j["cam"]),
+              L.make_params(j["tf"].data_ptr(), 256, -3.0, 50.0, 1.0, 0.99), j["out"].data_ptr(),
+              j["nsamples"].data_ptr()) for j in jobs]
+
+    def separate():
+        for h, c, p, o, n in ccams:
+            L.vr_render(h, c, p, o, n, s)
+    t_sep = _time_ms(torch, separate, max(5, args.steps))
+    samples = sum(int(j["nsamples"].sum()) for j in jobs)
+    print(json.dumps({"workload": "batch_64", "jobs": 64, "samples": samples,
+                      "graph_ms": t_graph, "separate_ms": t_sep, "speedup": t_sep / t_graph,
+                      "graph_gsamples_per_s": samples / t_graph / 1e6, "separate_gsamples_per_s": samples / t_sep / 1e6,
+                      "autotuned": {"tile": [best.tile_w, best.tile_h], "ctas_per_sm": best.ctas_per_sm}}))
+    for j in jobs:
+        j["vol"].close()
+
+
+def run_diff_512(args):
+    """512^3 f32, four 1024^2 views, step 0.5, no early termination: L2 loss
+    against targets rendered with a hidden table; forward and backward (table
+    and voxel gradients) per view, and their time ratio."""
+    import torch
+    import paper_1211_4896_gb300 as P
+    dev = torch.device("cuda")
+    pre = synth.preset_diff_512()
+    cube = synth.hi_cube(pre["dims"], pre["n_blobs"], pre["n_disks"], pre["seed"], device=dev)
+    vol = P.Volume(cube, "f32")
+    hidden = torch.from_numpy(synth.tf_ramp(256)).to(dev)
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(5)
+    tf = (hidden + 0.05 * torch.rand(hidden.shape, device=dev, generator=gen)).clamp(0, 1).contiguous()
+    cams = pre["cameras"]
+    tgts = [P.render(vol, c, hidden, synth.TF_VMIN, synth.TF_VMAX, pre["step"], 2.0)[0] for c in cams]
+    outs = [torch.empty((1024, 1024, 4), device=dev) for _ in cams]
+    nss = [torch.empty((1024, 1024), device=dev, dtype=torch.int32) for _ in cams]
+    gtf = torch.empty((256, 4), device=dev, dtype=torch.float64)
+    gvox = torch.empty(vol.shape, device=dev)
+    grads = [torch.empty_like(o) for o in outs]
+
+    def fwd():
+        for c, o, n in zip(cams, outs, nss):
+            P.render(vol, c, tf, synth.TF_VMIN, synth.TF_VMAX, pre["step"], 2.0, out=o, nsamples=n)
+
+    def bwd():
+        for v, (c, o, n, g, t) in enumerate(zip(cams, outs, nss, grads, tgts)):
+            torch.sub(o, t, out=g).mul_(2.0)
+            P.render_backward(vol, c, tf, synth.TF_VMIN, synth.TF_VMAX, pre["step"], o, n, g, 2.0, grad_tf=gtf,
+                              grad_vox=gvox, accumulate=v > 0)
+    t_f = _time_ms(torch, fwd, max(5, args.steps))
+    t_b = _time_ms(torch, bwd, max(5, args.steps))
+    samples = sum(int(n.sum()) for n in nss)
+    print(json.dumps({"workload": "diff_512", "samples": samples, "fwd_ms_4_views": t_f, "bwd_ms_4_views": t_b,
+                      "bwd_over_fwd": t_b / t_f, "fwd_gsamples_per_s": samples / t_f / 1e6,
+                      "fwd_bwd_gsamples_per_s": samples / (t_f + t_b) / 1e6}))
+    vol.close()
+
+
+WORKLOADS = {"plain_128": run_plain_128, "precision_4096": run_precision_4096, "batch_64": run_batch_64,
+             "diff_512": run_diff_512}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="scale_1024", choices=["scale_1024"] + sorted(WORKLOADS))
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -422,6 +622,10 @@ def main():
         return run_reference(args, rank)
     from paper_1211_4896_gb300 import build as B
     B.build()
+    if args.workload != "scale_1024":
+        import oracle
+        oracle.build()
+        return WORKLOADS[args.workload](args) or 0
     return run_ours(args, rank, world, local_rank)
 
 

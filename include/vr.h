@@ -56,7 +56,7 @@ typedef enum {
 typedef enum { VR_F32 = 0, VR_F16 = 1, VR_BF16 = 2 } vr_dtype;
 
 enum { VR_CAMERA_ORTHO = 0, VR_CAMERA_PERSPECTIVE = 1 };
-enum { VR_FILTER_SOFTWARE = 0, VR_FILTER_TEXTURE = 1 };
+enum { VR_FILTER_SOFTWARE = 0, VR_FILTER_TEXTURE = 1, VR_FILTER_SOFTWARE_STAGED = 2 };
 
 typedef struct vr_volume *vr_volume_t;   /* opaque, library-owned */
 
@@ -93,9 +93,13 @@ typedef struct {
     float step;               /* world units along the unit ray, > 0 */
     float ert_threshold;      /* early-termination opacity in (0, 1]; > 1 disables */
     float bg_rgba[4];         /* background, straight RGBA */
-    int filter;               /* VR_FILTER_SOFTWARE (FP32 trilinear, the reference path) or
-                                 VR_FILTER_TEXTURE (hardware filter, 8-bit fractional weights;
-                                 float32/float16 storage only) */
+    int filter;               /* VR_FILTER_SOFTWARE: FP32 trilinear gathered from the bricks through
+                                   L1 (the default, fastest measured path);
+                                 VR_FILTER_SOFTWARE_STAGED: FP32 trilinear with the volume staged
+                                   slab by slab in shared memory by bulk copies (bit-identical
+                                   results; allocates a dense copy on first use);
+                                 VR_FILTER_TEXTURE: hardware filter, 8-bit fractional weights,
+                                   float32/float16 storage only, forward only */
 } vr_params;
 
 typedef struct {
@@ -104,6 +108,8 @@ typedef struct {
     int brick;                /* B: bricks of B^3 cells stored with a +1 apron, (B+1)^3 voxels */
     int64_t bricks[3];        /* bricks per axis */
     int64_t bytes;            /* device bytes held by the bricked copy */
+    int64_t dense_bytes;      /* device bytes of the dense row-padded copy (0 until the first
+                                 staged call) */
 } vr_volume_info_t;
 
 /* ------------------------------------------------------------------------
@@ -114,7 +120,8 @@ typedef struct {
  * Copies the dense cube dev_cube (src_dtype, dims = {nx, ny, nz}, each >= 2,
  * x fastest) into a bricked copy in store_dtype: bricks of B^3 cells, each
  * stored as (B+1)^3 voxels so that all 8 trilinear corners of any cell lie in
- * one brick.  F32 -> F16/BF16 rounds to nearest even.  brick = 0 picks 16;
+ * one brick.  (The first VR_FILTER_SOFTWARE_STAGED call adds a dense copy with
+ * rows padded to 8 elements, streamed slab by slab into shared memory.)  F32 -> F16/BF16 rounds to nearest even.  brick = 0 picks 16;
  * otherwise 16, 32 or 64.  origin/spacing may be NULL (0 and 1).  The
  * caller keeps dev_cube; the call synchronises `cuda_stream` before returning
  * the handle in *out.  Errors: INVALID_ARG, OOM, CUDA.
@@ -140,7 +147,7 @@ vr_status vr_volume_info(vr_volume_t vol, vr_volume_info_t *out);
  * dev_nsamples_out is not NULL, the number of samples composited per pixel
  * (after early termination; 0 when the ray misses the box).  The backward
  * pass needs both.  Errors: INVALID_ARG, UNSUPPORTED (texture filter on
- * bfloat16 storage), OOM (first texture-filter call), CUDA.
+ * bfloat16 storage), OOM (first texture-filter or staged call), CUDA.
  * ---------------------------------------------------------------------- */
 vr_status vr_render(vr_volume_t vol, const vr_camera *cam, const vr_params *params, float *dev_rgba_out,
                     uint32_t *dev_nsamples_out, void *cuda_stream);
@@ -232,6 +239,14 @@ vr_status vr_autotune_batched(const vr_job *jobs, int n, vr_batch_opts *best, vo
 #define VR_NOALLOC_MAX_JOBS 256
 
 vr_status vr_render_batched_noalloc(const vr_job *jobs, int n, int tile_w, int tile_h, void *cuda_stream);
+
+/* Synchronises cuda_stream and reports whether a bounded device-side wait of an
+ * earlier call on this volume gave up (the staged kernels wait on the copy
+ * engine with an iteration limit; a timeout leaves that call's results
+ * invalid).  Returns VR_OK, or VR_ERR_TIMEOUT once per occurrence (the flag is
+ * cleared).  The paper has no such mechanism; it is part of this library's
+ * failure detection. */
+vr_status vr_check(vr_volume_t vol, void *cuda_stream);
 
 /* Human-readable message of the last failed call on this thread ("" if none). */
 const char *vr_last_error(void);

@@ -18,7 +18,7 @@ VR_OK, VR_ERR_INVALID_ARG, VR_ERR_UNSUPPORTED, VR_ERR_OOM, VR_ERR_CUDA, VR_ERR_T
     0, -1, -2, -3, -4, -5, -6
 VR_F32, VR_F16, VR_BF16 = 0, 1, 2
 VR_CAMERA_ORTHO, VR_CAMERA_PERSPECTIVE = 0, 1
-VR_FILTER_SOFTWARE, VR_FILTER_TEXTURE = 0, 1
+VR_FILTER_SOFTWARE, VR_FILTER_TEXTURE, VR_FILTER_SOFTWARE_STAGED = 0, 1, 2
 VR_GRAD_ACCUMULATE = 1
 
 STATUS_NAMES = {0: "VR_OK", -1: "VR_ERR_INVALID_ARG", -2: "VR_ERR_UNSUPPORTED", -3: "VR_ERR_OOM",
@@ -39,7 +39,7 @@ class vr_params(C.Structure):
 
 class vr_volume_info_t(C.Structure):
     _fields_ = [("dims", C.c_int64 * 3), ("store_dtype", C.c_int), ("brick", C.c_int),
-                ("bricks", C.c_int64 * 3), ("bytes", C.c_int64)]
+                ("bricks", C.c_int64 * 3), ("bytes", C.c_int64), ("dense_bytes", C.c_int64)]
 
 
 class vr_job(C.Structure):
@@ -54,7 +54,7 @@ class vr_batch_opts(C.Structure):
 # every symbol include/vr.h declares
 EXPORTS = ("vr_volume_create", "vr_volume_update", "vr_volume_destroy", "vr_volume_info", "vr_render",
            "vr_render_backward", "vr_render_batched", "vr_autotune_batched", "vr_render_batched_noalloc",
-           "vr_last_error", "vr_version")
+           "vr_check", "vr_last_error", "vr_version")
 VR_NOALLOC_MAX_JOBS = 256
 
 _lock = threading.Lock()
@@ -89,9 +89,10 @@ def load() -> C.CDLL:
         L.vr_render_batched.argtypes = [P(vr_job), C.c_int, P(vr_batch_opts), vp]
         L.vr_autotune_batched.argtypes = [P(vr_job), C.c_int, P(vr_batch_opts), vp]
         L.vr_render_batched_noalloc.argtypes = [P(vr_job), C.c_int, C.c_int, C.c_int, vp]
+        L.vr_check.argtypes = [vp, vp]
         for name in ("vr_volume_create", "vr_volume_update", "vr_volume_destroy", "vr_volume_info", "vr_render",
                      "vr_render_backward", "vr_render_batched", "vr_autotune_batched",
-                     "vr_render_batched_noalloc"):
+                     "vr_render_batched_noalloc", "vr_check"):
             getattr(L, name).restype = C.c_int
         L.vr_last_error.argtypes = []
         L.vr_last_error.restype = C.c_char_p
@@ -155,7 +156,7 @@ def vr_volume_info(vol: int) -> dict:
     info = vr_volume_info_t()
     _check("vr_volume_info", load().vr_volume_info(vol, C.byref(info)))
     return dict(dims=tuple(info.dims), store_dtype=info.store_dtype, brick=info.brick,
-                bricks=tuple(info.bricks), bytes=info.bytes)
+                bricks=tuple(info.bricks), bytes=info.bytes, dense_bytes=info.dense_bytes)
 
 
 def vr_render(vol: int, cam: vr_camera, params: vr_params, dev_rgba_out: int, dev_nsamples_out: int | None,
@@ -190,6 +191,11 @@ def vr_render_batched_noalloc(jobs, tile_w: int = 0, tile_h: int = 0, stream: in
     arr = (vr_job * len(jobs))(*jobs)
     _check("vr_render_batched_noalloc", load().vr_render_batched_noalloc(arr, len(jobs), int(tile_w), int(tile_h),
                                                                          stream))
+
+
+def vr_check(vol: int, stream: int = 0):
+    """Raises VRError(VR_ERR_TIMEOUT) if a bounded device wait of an earlier call gave up."""
+    _check("vr_check", load().vr_check(vol, stream))
 
 
 def vr_version() -> str:

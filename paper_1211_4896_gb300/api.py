@@ -86,7 +86,7 @@ def render(vol: Volume, cam: dict, tf: torch.Tensor, vmin: float, vmax: float, s
 
 def render_backward(vol: Volume, cam: dict, tf: torch.Tensor, vmin, vmax, step, rgba, nsamples, grad_rgba,
                     ert: float = 2.0, bg=(0.0, 0.0, 0.0, 0.0), want_vox: bool = True, grad_tf=None, grad_vox=None,
-                    accumulate: bool = False, stream=None):
+                    accumulate: bool = False, filter: int = L.VR_FILTER_SOFTWARE, stream=None):
     """Adjoint: returns (grad_tf (K, 4) float64, grad_vox (nz, ny, nx) float32 or None)."""
     for t, n in ((rgba, "rgba"), (nsamples, "nsamples"), (grad_rgba, "grad_rgba")):
         _need_cuda(t, n)
@@ -94,7 +94,7 @@ def render_backward(vol: Volume, cam: dict, tf: torch.Tensor, vmin, vmax, step, 
         grad_tf = torch.empty(tuple(tf.shape), device=vol.device, dtype=torch.float64)
     if want_vox and grad_vox is None:
         grad_vox = torch.empty(vol.shape, device=vol.device, dtype=torch.float32)
-    p = _params(tf, vmin, vmax, step, ert, bg, L.VR_FILTER_SOFTWARE)
+    p = _params(tf, vmin, vmax, step, ert, bg, filter)
     L.vr_render_backward(vol.handle, L.make_camera(cam), p, rgba.data_ptr(), nsamples.data_ptr(),
                          grad_rgba.data_ptr(), grad_tf.data_ptr(), grad_vox.data_ptr() if want_vox else None,
                          L.VR_GRAD_ACCUMULATE if accumulate else 0, _stream(stream))

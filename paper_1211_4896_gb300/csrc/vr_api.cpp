@@ -91,8 +91,9 @@ static vr_status check_params(const vr_params *p)
     if (!(p->ert_threshold > 0.0f)) return invalid("params.ert_threshold must be > 0 (values > 1 disable it)");
     for (int c = 0; c < 4; ++c)
         if (!std::isfinite(p->bg_rgba[c])) return invalid("params.bg_rgba must be finite");
-    if (p->filter != VR_FILTER_SOFTWARE && p->filter != VR_FILTER_TEXTURE)
-        return invalid("params.filter must be VR_FILTER_SOFTWARE (0) or VR_FILTER_TEXTURE (1)");
+    if (p->filter != VR_FILTER_SOFTWARE && p->filter != VR_FILTER_TEXTURE && p->filter != VR_FILTER_SOFTWARE_STAGED)
+        return invalid("params.filter must be VR_FILTER_SOFTWARE (0), VR_FILTER_TEXTURE (1) or "
+                       "VR_FILTER_SOFTWARE_STAGED (2)");
     return VR_OK;
 }
 
@@ -202,10 +203,34 @@ VolDev vol_dev(const vr_volume *vol)
     return v;
 }
 
+// The last slot of the ring is the volume's device status word.
 vr_status next_counter(vr_volume *vol, unsigned **ctr)
 {
     *ctr = vol->counters + vol->next_counter;
-    vol->next_counter = (vol->next_counter + 1) % vol->counter_slots;
+    vol->next_counter = (vol->next_counter + 1) % (vol->counter_slots - 1);
+    return VR_OK;
+}
+
+static unsigned *status_word(vr_volume *vol) { return vol->counters + vol->counter_slots - 1; }
+
+// The dense row-padded copy used by the staged kernels, built from the bricks
+// on first use.
+static vr_status ensure_dense(vr_volume *vol, cudaStream_t s)
+{
+    if (vol->dense) return VR_OK;
+    const int px = (int)((vol->dims[0] + 7) / 8 * 8);
+    const size_t bytes = (size_t)px * (size_t)vol->dims[1] * (size_t)vol->dims[2] * (vol->store_dtype == VR_F32 ? 4 : 2);
+    void *p = nullptr;
+    if (cudaMalloc(&p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        set_error("staged filter: cannot allocate the dense copy (" + std::to_string(bytes) + " bytes)");
+        return VR_ERR_OOM;
+    }
+    vol->dense = p;
+    vol->dense_px = px;
+    vol->dense_bytes = bytes;
+    cudaError_t e = launch_dense_from_bricks(vol, s);
+    if (e != cudaSuccess) return cuda_fail(e, "staged filter: dense copy");
     return VR_OK;
 }
 
@@ -227,6 +252,7 @@ static void free_volume(vr_volume *vol)
     if (vol->tex) cudaDestroyTextureObject(vol->tex);
     if (vol->tex_array) cudaFreeArray(vol->tex_array);
     if (vol->bricks) cudaFree(vol->bricks);
+    if (vol->dense) cudaFree(vol->dense);
     if (vol->counters) cudaFree(vol->counters);
     delete vol;
 }
@@ -298,6 +324,7 @@ vr_status vr_volume_create(const void *dev_cube, vr_dtype src_dtype, vr_dtype st
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
     e = cudaMemsetAsync(vol->counters, 0, sizeof(unsigned) * vol->counter_slots, s);
     if (e == cudaSuccess) e = launch_brick(dev_cube, src_dtype, vol, s);
+    if (e == cudaSuccess && vol->dense) e = launch_densify(dev_cube, src_dtype, vol, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) { free_volume(vol); return cuda_fail(e, "vr_volume_create: bricking"); }
     *out = vol;
@@ -320,6 +347,7 @@ vr_status vr_volume_update(vr_volume_t vol, const void *dev_cube, vr_dtype src_d
         vol->tex_array = nullptr;
     }
     cudaError_t e = launch_brick(dev_cube, src_dtype, vol, s);
+    if (e == cudaSuccess && vol->dense) e = launch_densify(dev_cube, src_dtype, vol, s);
     if (e != cudaSuccess) return cuda_fail(e, "vr_volume_update");
     return VR_OK;
 }
@@ -346,6 +374,7 @@ vr_status vr_volume_info(vr_volume_t vol, vr_volume_info_t *out)
     out->store_dtype = vol->store_dtype;
     out->brick = vol->brick;
     out->bytes = (int64_t)vol->bytes;
+    out->dense_bytes = (int64_t)vol->dense_bytes;
     return VR_OK;
 }
 
@@ -374,6 +403,11 @@ vr_status vr_render(vr_volume_t vol, const vr_camera *cam, const vr_params *para
         st = build_texture(vol, s);
         if (st != VR_OK) return st;
         e = launch_forward_texture(vol, c, p, reinterpret_cast<float4 *>(dev_rgba_out), dev_nsamples_out, ctr, s);
+    } else if (params->filter == VR_FILTER_SOFTWARE_STAGED) {
+        st = ensure_dense(vol, s);
+        if (st != VR_OK) return st;
+        e = launch_forward_staged(dense_dev(vol), vol->store_dtype, c, p, reinterpret_cast<float4 *>(dev_rgba_out),
+                                  dev_nsamples_out, ctr, status_word(vol), s);
     } else {
         e = launch_forward(vol_dev(vol), vol->store_dtype, c, p, reinterpret_cast<float4 *>(dev_rgba_out),
                            dev_nsamples_out, ctr, s);
@@ -390,8 +424,8 @@ vr_status vr_render_backward(vr_volume_t vol, const vr_camera *cam, const vr_par
     vr_status st = check_camera(cam);
     if (st == VR_OK) st = check_params(params);
     if (st != VR_OK) return st;
-    if (params->filter != VR_FILTER_SOFTWARE)
-        return (set_error("vr_render_backward: only the software filter is differentiable"), VR_ERR_UNSUPPORTED);
+    if (params->filter == VR_FILTER_TEXTURE)
+        return (set_error("vr_render_backward: only the software filters are differentiable"), VR_ERR_UNSUPPORTED);
     if (!(params->bg_rgba[3] < 1.0f))
         return (set_error("vr_render_backward: bg alpha must be < 1 (T_final is recovered from the output alpha)"),
                 VR_ERR_UNSUPPORTED);
@@ -417,10 +451,40 @@ vr_status vr_render_backward(vr_volume_t vol, const vr_camera *cam, const vr_par
     const long long nvox = (long long)vol->dims[0] * vol->dims[1] * vol->dims[2];
     unsigned *ctr;
     next_counter(vol, &ctr);
-    cudaError_t e = launch_backward(vol_dev(vol), vol->store_dtype, c, p, reinterpret_cast<const float4 *>(dev_rgba),
-                                    dev_nsamples, reinterpret_cast<const float4 *>(dev_grad_rgba), dev_grad_tf,
-                                    dev_grad_vox, nvox, (flags & VR_GRAD_ACCUMULATE) != 0, ctr, s);
+    const bool acc = (flags & VR_GRAD_ACCUMULATE) != 0;
+    cudaError_t e;
+    if (params->filter == VR_FILTER_SOFTWARE_STAGED) {
+        st = ensure_dense(vol, s);
+        if (st != VR_OK) return st;
+    }
+    if (params->filter == VR_FILTER_SOFTWARE_STAGED)
+        e = launch_backward_staged(dense_dev(vol), vol->store_dtype, c, p, reinterpret_cast<const float4 *>(dev_rgba),
+                                   dev_nsamples, reinterpret_cast<const float4 *>(dev_grad_rgba), dev_grad_tf,
+                                   dev_grad_vox, nvox, acc, ctr, status_word(vol), s);
+    else
+        e = launch_backward(vol_dev(vol), vol->store_dtype, c, p, reinterpret_cast<const float4 *>(dev_rgba),
+                            dev_nsamples, reinterpret_cast<const float4 *>(dev_grad_rgba), dev_grad_tf, dev_grad_vox,
+                            nvox, acc, ctr, s);
     if (e != cudaSuccess) return cuda_fail(e, "vr_render_backward launch");
+    return VR_OK;
+}
+
+vr_status vr_check(vr_volume_t vol, void *cuda_stream)
+{
+    g_err.clear();
+    vr_status st = check_volume(vol);
+    if (st != VR_OK) return st;
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    unsigned flag = 0;
+    cudaError_t e = cudaMemcpyAsync(&flag, status_word(vol), sizeof flag, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "vr_check");
+    if (flag) {
+        cudaMemsetAsync(status_word(vol), 0, sizeof(unsigned), s);
+        cudaStreamSynchronize(s);
+        set_error("a bounded device-side wait gave up in an earlier call on this volume (its results are invalid)");
+        return VR_ERR_TIMEOUT;
+    }
     return VR_OK;
 }
 

@@ -23,6 +23,16 @@ template <> __device__ __forceinline__ float ldv<__nv_bfloat16>(const __nv_bfloa
     return __bfloat162float(__ldg(p));
 }
 
+__device__ __forceinline__ float to_f(float v) { return v; }
+__device__ __forceinline__ float to_f(__half v) { return __half2float(v); }
+__device__ __forceinline__ float to_f(__nv_bfloat16 v) { return __bfloat162float(v); }
+
+// float -> storage type, round to nearest even
+template <typename D> __device__ __forceinline__ D to_dtype(float v);
+template <> __device__ __forceinline__ float to_dtype<float>(float v) { return v; }
+template <> __device__ __forceinline__ __half to_dtype<__half>(float v) { return __float2half_rn(v); }
+template <> __device__ __forceinline__ __nv_bfloat16 to_dtype<__nv_bfloat16>(float v) { return __float2bfloat16_rn(v); }
+
 // ---------------------------------------------------------------------------
 // Ray setup: camera model of Section 3.1's user-controlled viewport (pinhole
 // or orthographic projection), clipped to the closed box [0, n-1]^3 by the

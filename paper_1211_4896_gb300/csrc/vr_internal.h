@@ -51,6 +51,14 @@ struct VolDev {
     long long stride;      // elements per brick (>= (B+1)^3, padded)
 };
 
+// Dense copy of the volume, x fastest, rows padded to a multiple of 8
+// elements so that 16-byte asynchronous copies of any x-aligned run are legal.
+struct DenseDev {
+    const void *data;
+    int nx, ny, nz;
+    int px;                // row pitch in elements
+};
+
 }  // namespace vr
 
 struct vr_volume {
@@ -65,9 +73,13 @@ struct vr_volume {
     int device = 0;
     // work-queue counters (a small ring so consecutive calls do not reuse a
     // counter that an earlier, still running launch may read)
-    unsigned *counters = nullptr;
+    unsigned *counters = nullptr;      // last slot: device status word (timeouts)
     int counter_slots = 0;
     int next_counter = 0;
+    // dense padded copy used by the shared-memory staged kernels
+    void *dense = nullptr;
+    int dense_px = 0;
+    size_t dense_bytes = 0;
     // hardware-filter copy (created on first texture-filter render)
     cudaArray_t tex_array = nullptr;
     cudaTextureObject_t tex = 0;
@@ -98,6 +110,15 @@ cudaError_t launch_backward(const VolDev &v, vr_dtype dt, const CamDev &c, const
                             double *grad_tf, float *grad_vox, long long nvox, bool accumulate,
                             unsigned *counter, cudaStream_t s);
 int backward_max_tf_size();
+DenseDev dense_dev(const vr_volume *vol);
+cudaError_t launch_densify(const void *src, vr_dtype src_dtype, vr_volume *vol, cudaStream_t s);
+cudaError_t launch_dense_from_bricks(vr_volume *vol, cudaStream_t s);
+cudaError_t launch_forward_staged(const DenseDev &d, vr_dtype dt, const CamDev &c, const ParamDev &p, float4 *out,
+                                  uint32_t *nsamples, unsigned *counter, unsigned *status, cudaStream_t s);
+cudaError_t launch_backward_staged(const DenseDev &d, vr_dtype dt, const CamDev &c, const ParamDev &p,
+                                   const float4 *rgba, const uint32_t *nsamples, const float4 *grad_rgba,
+                                   double *grad_tf, float *grad_vox, long long nvox, bool accumulate,
+                                   unsigned *counter, unsigned *status, cudaStream_t s);
 int occupancy_blocks(const void *fn, int threads, size_t smem);
 vr_status validate_job(const vr_job *job, int index);
 void purge_plans(const vr_volume *vol);

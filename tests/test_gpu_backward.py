@@ -39,17 +39,18 @@ def _grad_close(g, ref, rel=1e-3):
     return err <= bound, err, bound
 
 
+@pytest.mark.parametrize("filt", [0, 2])
 @pytest.mark.parametrize("ert,bg", [(2.0, (0, 0, 0, 0)), (0.9, (0.2, 0.1, 0.4, 0.3))])
-def test_backward_matches_fp64_reverse_sweep(P, torch, ert, bg):
+def test_backward_matches_fp64_reverse_sweep(P, torch, ert, bg, filt):
     dims = (36, 30, 40)
     cube, vol, cam = _setup(torch, P, dims, seed=12, W=48, H=40)
     dev = torch.device("cuda")
     tf_np = synth.tf_random_pwl(seed=3, alpha_max=0.25)
     tf = torch.from_numpy(tf_np).to(dev)
-    img, ns = P.render(vol, cam, tf, -3.0, 30.0, 0.5, ert, bg)
+    img, ns = P.render(vol, cam, tf, -3.0, 30.0, 0.5, ert, bg, filter=filt)
     target = torch.rand_like(img)
     g = 2.0 * (img - target)
-    gtf, gvox = P.render_backward(vol, cam, tf, -3.0, 30.0, 0.5, img, ns, g, ert, bg)
+    gtf, gvox = P.render_backward(vol, cam, tf, -3.0, 30.0, 0.5, img, ns, g, ert, bg, filter=filt)
     torch.cuda.synchronize()
     ref_tf, ref_vox = oracle.render_backward(cube.numpy(), cam, tf_np, -3.0, 30.0, 0.5,
                                              g.cpu().numpy().astype(np.float64), ert=ert, bg=bg)
