@@ -127,6 +127,9 @@ vr_status prepare_params(const vr_params *p, ParamDev *o)
     o->vmin = p->vmin;
     o->scale01 = (float)(1.0 / ((double)p->vmax - (double)p->vmin));
     o->km1 = (float)(p->tf_size - 1);
+    const double su = (double)(p->tf_size - 1) / ((double)p->vmax - (double)p->vmin);
+    o->su = (float)su;
+    o->ou = (float)(-(double)p->vmin * su);
     o->step = p->step;
     o->t_stop = (float)(1.0 - (double)p->ert_threshold);
     o->bg = make_float4(p->bg_rgba[0], p->bg_rgba[1], p->bg_rgba[2], p->bg_rgba[3]);

@@ -71,17 +71,9 @@ __global__ void __launch_bounds__(kBwdThreads) bwd_kernel(VolDev v, CamDev c, Pa
         float T = 1.0f;
         int k = 0;
         bool active = n > 0;
-        Cell cell;
-        Corners f;
-        if (active) {
-            cell = locate<LOG2B>(v, sample_pos(ray, 0, p.step));
-            fetch_corners<VT, LOG2B>(v, cell, f);
-        }
-        while (__any_sync(kFull, active)) {
-            if (active) {
+        // one sample: gradient of (cell, f); the next sample's gathers go to (ncell, nf)
+        auto step = [&](const Cell &cell, const Corners &f, Cell &ncell, Corners &nf) {
                 const bool more = k + 1 < n;
-                Cell ncell;
-                Corners nf;
                 if (more) {
                     ncell = locate<LOG2B>(v, sample_pos(ray, k + 1, p.step));
                     fetch_corners<VT, LOG2B>(v, ncell, nf);
@@ -119,9 +111,18 @@ __global__ void __launch_bounds__(kBwdThreads) bwd_kernel(VolDev v, CamDev c, Pa
                 T = fmaf(-a, T, T);
                 ++k;
                 if (!more) active = false;
-                cell = ncell;
-                f = nf;
-            }
+        };
+        Cell c0, c1;
+        Corners f0, f1;
+        if (active) {
+            c0 = locate<LOG2B>(v, sample_pos(ray, 0, p.step));
+            fetch_corners<VT, LOG2B>(v, c0, f0);
+        }
+        for (;;) {      // two register sets in turn (no copy of the prefetched sample)
+            if (!__any_sync(kFull, active)) break;
+            if (active) step(c0, f0, c1, f1);
+            if (!__any_sync(kFull, active)) break;
+            if (active) step(c1, f1, c0, f0);
         }
         // Final cross-block sum in FP64: this tile's FP32 partial bins go to
         // the output, and the bins restart from zero.

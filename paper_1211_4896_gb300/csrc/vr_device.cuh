@@ -213,10 +213,9 @@ __device__ __forceinline__ void load_tf_shared(float4 *tfs, const float4 *tf, in
 // fewer L1 wavefronts than a 128-bit shared-memory load (4 wavefronts).
 __device__ __forceinline__ float4 tf_lookup_l1(const ParamDev &p, float v, TfPos &pos)
 {
-    float s = (v - p.vmin) * p.scale01;
-    pos.interior = (s > 0.0f) && (s < 1.0f);
-    s = fminf(fmaxf(s, 0.0f), 1.0f);
-    const float u = s * p.km1;
+    float u = fmaf(v, p.su, p.ou);               // (v - vmin) (K-1)/(vmax - vmin)
+    pos.interior = (u > 0.0f) && (u < p.km1);
+    u = fminf(fmaxf(u, 0.0f), p.km1);            // fmaxf maps NaN to 0
     const int i0 = min(__float2int_rd(u), p.K - 2);
     const float w = u - (float)i0;
     pos.i0 = i0;
@@ -236,39 +235,48 @@ struct Composite {
     float r, g, b, T;
 };
 
+// One sample: composites (cur, fc) and, when the ray goes on, issues the
+// gathers of the next sample into (nxt, fn).
+template <typename T, int LOG2B>
+__device__ __forceinline__ void march_step(const VolDev &v, const ParamDev &p, const Ray &ray, int &k, bool &active,
+                                           Composite &acc, const Cell &cur, const Corners &fc, Cell &nxt,
+                                           Corners &fn)
+{
+    const bool more = k + 1 < ray.n;
+    if (more) {
+        nxt = locate<LOG2B>(v, sample_pos(ray, k + 1, p.step));
+        fetch_corners<T, LOG2B>(v, nxt, fn);
+    }
+    const float val = interp_corners(cur, fc);
+    TfPos tp;
+    const float4 e = tf_lookup_l1(p, val, tp);
+    const float aT = e.w * acc.T;
+    acc.r = fmaf(aT, e.x, acc.r);
+    acc.g = fmaf(aT, e.y, acc.g);
+    acc.b = fmaf(aT, e.z, acc.b);
+    acc.T = fmaf(-e.w, acc.T, acc.T);
+    ++k;
+    if (!more || acc.T <= p.t_stop) active = false;
+}
+
+// The loop body is unrolled twice over two register sets (ping-pong), so the
+// prefetched sample never has to be copied into the current one.
 template <typename T, int LOG2B>
 __device__ __forceinline__ int march_ray(const VolDev &v, const ParamDev &p, const Ray &ray, bool active,
                                          Composite &acc)
 {
     int k = 0;
-    Cell cell;
-    Corners f;
+    Cell c0, c1;
+    Corners f0, f1;
     if (active) {
-        cell = locate<LOG2B>(v, sample_pos(ray, 0, p.step));
-        fetch_corners<T, LOG2B>(v, cell, f);
+        c0 = locate<LOG2B>(v, sample_pos(ray, 0, p.step));
+        fetch_corners<T, LOG2B>(v, c0, f0);
     }
-    while (__any_sync(kFull, active)) {
-        if (active) {
-            const bool more = k + 1 < ray.n;
-            Cell ncell;
-            Corners nf;
-            if (more) {
-                ncell = locate<LOG2B>(v, sample_pos(ray, k + 1, p.step));
-                fetch_corners<T, LOG2B>(v, ncell, nf);
-            }
-            const float val = interp_corners(cell, f);
-            TfPos tp;
-            const float4 e = tf_lookup_l1(p, val, tp);
-            const float aT = e.w * acc.T;
-            acc.r = fmaf(aT, e.x, acc.r);
-            acc.g = fmaf(aT, e.y, acc.g);
-            acc.b = fmaf(aT, e.z, acc.b);
-            acc.T = fmaf(-e.w, acc.T, acc.T);
-            ++k;
-            if (!more || acc.T <= p.t_stop) active = false;
-            cell = ncell;
-            f = nf;
-        }
+    for (;;) {
+        if (!__any_sync(kFull, active)) break;
+        if (active) march_step<T, LOG2B>(v, p, ray, k, active, acc, c0, f0, c1, f1);
+        if (!__any_sync(kFull, active)) break;
+        if (active) march_step<T, LOG2B>(v, p, ray, k, active, acc, c1, f1, c0, f0);
     }
     return k;
 }

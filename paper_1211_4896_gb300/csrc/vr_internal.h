@@ -34,6 +34,7 @@ struct ParamDev {
     int K;
     float vmin, scale01;   // s = (v - vmin) * scale01, scale01 = 1/(vmax - vmin)
     float km1;             // K - 1
+    float su, ou;          // table coordinate u = v * su + ou = (v - vmin) (K-1)/(vmax - vmin)
     float step;
     float t_stop;          // stop once T <= t_stop  (t_stop = 1 - ert_threshold, < 0 disables)
     float4 bg;
