@@ -216,6 +216,26 @@ vr_status next_counter(vr_volume *vol, unsigned **ctr)
 
 static unsigned *status_word(vr_volume *vol) { return vol->counters + vol->counter_slots - 1; }
 
+// Backward scratch (per-warp gradient rows), grown on demand.  Growing waits
+// for the stream so that no running kernel still uses the old buffer.
+cudaError_t ensure_wtab(vr_volume *vol, size_t floats, cudaStream_t s)
+{
+    if (floats <= vol->wtab_cap) return cudaSuccess;
+    if (vol->wtab) {
+        cudaStreamSynchronize(s);
+        cudaFree(vol->wtab);
+        vol->wtab = nullptr;
+        vol->wtab_cap = 0;
+    }
+    cudaError_t e = cudaMalloc(&vol->wtab, floats * sizeof(float));
+    if (e != cudaSuccess) {
+        vol->wtab = nullptr;
+        return e;
+    }
+    vol->wtab_cap = floats;
+    return cudaSuccess;
+}
+
 // The dense row-padded copy used by the staged kernels, built from the bricks
 // on first use.
 static vr_status ensure_dense(vr_volume *vol, cudaStream_t s)
@@ -256,6 +276,7 @@ static void free_volume(vr_volume *vol)
     if (vol->tex_array) cudaFreeArray(vol->tex_array);
     if (vol->bricks) cudaFree(vol->bricks);
     if (vol->dense) cudaFree(vol->dense);
+    if (vol->wtab) cudaFree(vol->wtab);
     if (vol->counters) cudaFree(vol->counters);
     delete vol;
 }
@@ -465,9 +486,9 @@ vr_status vr_render_backward(vr_volume_t vol, const vr_camera *cam, const vr_par
                                    dev_nsamples, reinterpret_cast<const float4 *>(dev_grad_rgba), dev_grad_tf,
                                    dev_grad_vox, nvox, acc, ctr, status_word(vol), s);
     else
-        e = launch_backward(vol_dev(vol), vol->store_dtype, c, p, reinterpret_cast<const float4 *>(dev_rgba),
-                            dev_nsamples, reinterpret_cast<const float4 *>(dev_grad_rgba), dev_grad_tf, dev_grad_vox,
-                            nvox, acc, ctr, s);
+        e = launch_backward(vol, c, p, reinterpret_cast<const float4 *>(dev_rgba), dev_nsamples,
+                            reinterpret_cast<const float4 *>(dev_grad_rgba), dev_grad_tf, dev_grad_vox, nvox, acc, ctr,
+                            s);
     if (e != cudaSuccess) return cuda_fail(e, "vr_render_backward launch");
     return VR_OK;
 }

@@ -13,10 +13,12 @@
 // dotted with g, so one scalar R_k is carried along the march.
 //
 // Persistent warps pull 8x4 ray tiles from the same atomic queue as the
-// forward.  Each warp accumulates its tile's table gradient in private FP32
-// bins in shared memory, then adds the non-zero bins into the FP64 output
-// with FP64 atomics (the only FP64 arithmetic: the final cross-block sum).
-// The voxel gradient is scattered with float atomics into the dense layout.
+// forward.  Every warp owns a private FP32 row of K RGBA gradient bins in
+// global memory (L2-resident); a sample adds its two weighted contributions
+// with two fire-and-forget 16-byte vector reductions.  One final kernel sums
+// the warps' rows in FP64 (the only FP64 arithmetic: the cross-block sum).
+// The voxel gradient is scattered into the dense layout with reductions, the
+// two x-neighbours of a corner pair as one 8-byte reduction when aligned.
 #include "vr_device.cuh"
 
 namespace vr {
@@ -24,20 +26,50 @@ namespace vr {
 constexpr int kBwdThreads = 256;
 constexpr int kBwdWarps = kBwdThreads / 32;
 
+__device__ __forceinline__ void red_add_v4(float4 *a, float4 v)
+{
+    asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};\n" ::"l"(a), "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w)
+                 : "memory");
+}
+
+__device__ __forceinline__ void red_add_v2(float *a, float x, float y)
+{
+    asm volatile("red.global.add.v2.f32 [%0], {%1, %2};\n" ::"l"(a), "f"(x), "f"(y) : "memory");
+}
+
+__device__ __forceinline__ void red_add_f32(float *a, float x)
+{
+    asm volatile("red.global.add.f32 [%0], %1;\n" ::"l"(a), "f"(x) : "memory");
+}
+
+// dv distributed to the 8 corners of the cell whose (x0, y0, z0) corner is at gv.
+__device__ __forceinline__ void scatter_corners(float *gv, long long nx, long long nyx, float fx, float fy, float fz,
+                                                float dv)
+{
+    const float wx0 = 1.0f - fx, wy0 = 1.0f - fy, wz0 = 1.0f - fz;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const float a = ((q & 1) ? fy : wy0) * ((q & 2) ? fz : wz0) * dv;
+        float *b = gv + ((q & 1) ? nx : 0) + ((q & 2) ? nyx : 0);
+        if ((reinterpret_cast<uintptr_t>(b) & 7u) == 0) {
+            red_add_v2(b, wx0 * a, fx * a);
+        } else {
+            red_add_f32(b, wx0 * a);
+            red_add_f32(b + 1, fx * a);
+        }
+    }
+}
+
 template <typename VT, int LOG2B>
 __global__ void __launch_bounds__(kBwdThreads) bwd_kernel(VolDev v, CamDev c, ParamDev p,
                                                            const float4 *__restrict__ rgba,
                                                            const uint32_t *__restrict__ nsamples,
-                                                           const float4 *__restrict__ grad_rgba, double *grad_tf,
+                                                           const float4 *__restrict__ grad_rgba, float4 *wtab,
                                                            float *grad_vox, unsigned *counter, int tiles_x,
                                                            unsigned ntiles)
 {
-    extern __shared__ float sbins[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int nb = 4 * p.K;
-    float *bins = sbins + warp * nb;
-    for (int q = lane; q < nb; q += 32) bins[q] = 0.0f;
-    __syncwarp();
+    float4 *row = wtab + ((size_t)blockIdx.x * kBwdWarps + warp) * (size_t)p.K;     // this warp's bins
     const float vscale = p.km1 * p.scale01;    // du/dv inside the range
     const long long nyx = (long long)v.ny * v.nx;
 
@@ -73,44 +105,37 @@ __global__ void __launch_bounds__(kBwdThreads) bwd_kernel(VolDev v, CamDev c, Pa
         bool active = n > 0;
         // one sample: gradient of (cell, f); the next sample's gathers go to (ncell, nf)
         auto step = [&](const Cell &cell, const Corners &f, Cell &ncell, Corners &nf) {
-                const bool more = k + 1 < n;
-                if (more) {
-                    ncell = locate<LOG2B>(v, sample_pos(ray, k + 1, p.step));
-                    fetch_corners<VT, LOG2B>(v, ncell, nf);
-                }
-                const float val = interp_corners(cell, f);
-                TfPos tp;
-                const float4 e = tf_lookup_l1(p, val, tp);
-                const float a = e.w;
-                const float cg = e.x * g.x + e.y * g.y + e.z * g.z;
-                const float aT = a * T;
-                R = fmaf(-aT, cg, R);                       // R_k = R_{k-1} - T_k a_k (c_k.g)
-                const float om = 1.0f - a;
-                const float da = T * cg - (om > 0.0f ? R / om : 0.0f);
+            const bool more = k + 1 < n;
+            if (more) {
+                ncell = locate<LOG2B>(v, sample_pos(ray, k + 1, p.step));
+                fetch_corners<VT, LOG2B>(v, ncell, nf);
+            }
+            const float val = interp_corners(cell, f);
+            TfPos tp;
+            const float4 e = tf_lookup_l1(p, val, tp);
+            const float a = e.w;
+            const float cg = e.x * g.x + e.y * g.y + e.z * g.z;
+            const float aT = a * T;
+            R = fmaf(-aT, cg, R);                       // R_k = R_{k-1} - T_k a_k (c_k.g)
+            const float om = 1.0f - a;
+            const float da = T * cg - (om > 0.0f ? R / om : 0.0f);
+            if (aT != 0.0f || da != 0.0f) {
                 const float w1 = tp.w, w0 = 1.0f - tp.w;
-                float *g0 = bins + 4 * tp.i0;
-                if (aT != 0.0f) {
-                    atomicAdd(g0 + 0, w0 * aT * g.x); atomicAdd(g0 + 4, w1 * aT * g.x);
-                    atomicAdd(g0 + 1, w0 * aT * g.y); atomicAdd(g0 + 5, w1 * aT * g.y);
-                    atomicAdd(g0 + 2, w0 * aT * g.z); atomicAdd(g0 + 6, w1 * aT * g.z);
-                }
-                if (da != 0.0f) { atomicAdd(g0 + 3, w0 * da); atomicAdd(g0 + 7, w1 * da); }
+                const float4 dr = make_float4(aT * g.x, aT * g.y, aT * g.z, da);
+                red_add_v4(row + tp.i0, make_float4(w0 * dr.x, w0 * dr.y, w0 * dr.z, w0 * dr.w));
+                red_add_v4(row + tp.i0 + 1, make_float4(w1 * dr.x, w1 * dr.y, w1 * dr.z, w1 * dr.w));
                 if (grad_vox && tp.interior) {
                     const float4 e0 = __ldg(p.tf + tp.i0), e1 = __ldg(p.tf + tp.i0 + 1);
-                    const float dv = (aT * (g.x * (e1.x - e0.x) + g.y * (e1.y - e0.y) + g.z * (e1.z - e0.z)) +
-                                      da * (e1.w - e0.w)) * vscale;
-                    if (dv != 0.0f) {
-                        float *gv = grad_vox + ((long long)cell.z0 * nyx + (long long)cell.y0 * v.nx + cell.x0);
-#pragma unroll
-                        for (int q = 0; q < 8; ++q) {
-                            const long long off = ((q & 4) ? nyx : 0) + ((q & 2) ? v.nx : 0) + (q & 1);
-                            atomicAdd(gv + off, corner_weight(cell, q) * dv);
-                        }
-                    }
+                    const float dv = (dr.x * (e1.x - e0.x) + dr.y * (e1.y - e0.y) + dr.z * (e1.z - e0.z) +
+                                      dr.w * (e1.w - e0.w)) * vscale;
+                    if (dv != 0.0f)
+                        scatter_corners(grad_vox + ((long long)cell.z0 * nyx + (long long)cell.y0 * v.nx + cell.x0),
+                                        v.nx, nyx, cell.fx, cell.fy, cell.fz, dv);
                 }
-                T = fmaf(-a, T, T);
-                ++k;
-                if (!more) active = false;
+            }
+            T = fmaf(-a, T, T);
+            ++k;
+            if (!more) active = false;
         };
         Cell c0, c1;
         Corners f0, f1;
@@ -124,72 +149,75 @@ __global__ void __launch_bounds__(kBwdThreads) bwd_kernel(VolDev v, CamDev c, Pa
             if (!__any_sync(kFull, active)) break;
             if (active) step(c1, f1, c0, f0);
         }
-        // Final cross-block sum in FP64: this tile's FP32 partial bins go to
-        // the output, and the bins restart from zero.
-        __syncwarp();
-        for (int q = lane; q < nb; q += 32) {
-            const float x = bins[q];
-            if (x != 0.0f) {
-                atomicAdd(grad_tf + q, (double)x);
-                bins[q] = 0.0f;
-            }
-        }
-        __syncwarp();
     }
 }
 
+// Final cross-block sum of the warps' FP32 rows, in FP64.
+__global__ void __launch_bounds__(256) reduce_rows(const float *__restrict__ rows, int nrows, int n, double *out,
+                                                    int chunk)
+{
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= n) return;
+    const int r0 = blockIdx.y * chunk, r1 = min(r0 + chunk, nrows);
+    double acc = 0.0;
+    for (int r = r0; r < r1; ++r) acc += (double)rows[(size_t)r * n + q];
+    atomicAdd(out + q, acc);
+}
+
 template <typename T, int LOG2B>
-static cudaError_t launch_bwd_t(const VolDev &v, const CamDev &c, const ParamDev &p, const float4 *rgba,
+static cudaError_t launch_bwd_t(vr_volume *vol, const CamDev &c, const ParamDev &p, const float4 *rgba,
                                 const uint32_t *nsamples, const float4 *grad_rgba, double *grad_tf, float *grad_vox,
                                 long long nvox, bool accumulate, unsigned *counter, cudaStream_t s)
 {
-    const size_t smem = sizeof(float) * 4 * (size_t)p.K * kBwdWarps;
     auto fn = bwd_kernel<T, LOG2B>;
-    cudaError_t e;
-    if (smem > 48 * 1024) {
-        e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-    }
-    if (!accumulate) {
-        e = cudaMemsetAsync(grad_tf, 0, sizeof(double) * 4 * (size_t)p.K, s);
-        if (e != cudaSuccess) return e;
-        if (grad_vox) {
-            e = cudaMemsetAsync(grad_vox, 0, sizeof(float) * (size_t)nvox, s);
-            if (e != cudaSuccess) return e;
-        }
-    }
     const int tiles_x = (c.W + 7) / 8, tiles_y = (c.H + 3) / 4;
     const unsigned ntiles = (unsigned)tiles_x * (unsigned)tiles_y;
-    const int per_sm = occupancy_blocks((const void *)fn, kBwdThreads, smem);
+    const int per_sm = occupancy_blocks((const void *)fn, kBwdThreads, 0);
     unsigned grid = (unsigned)(per_sm * sm_count());
     const unsigned max_useful = (ntiles + kBwdWarps - 1) / kBwdWarps;
     if (grid > max_useful) grid = max_useful;
     if (grid < 1) grid = 1;
+    const int nrows = (int)grid * kBwdWarps;
+    const size_t need = (size_t)nrows * 4 * (size_t)p.K;          // floats
+    cudaError_t e = ensure_wtab(vol, need, s);
+    if (e != cudaSuccess) return e;
+    e = cudaMemsetAsync(vol->wtab, 0, need * sizeof(float), s);
+    if (e != cudaSuccess) return e;
+    if (!accumulate) {
+        e = cudaMemsetAsync(grad_tf, 0, sizeof(double) * 4 * (size_t)p.K, s);
+        if (e == cudaSuccess && grad_vox) e = cudaMemsetAsync(grad_vox, 0, sizeof(float) * (size_t)nvox, s);
+        if (e != cudaSuccess) return e;
+    }
     e = cudaMemsetAsync(counter, 0, sizeof(unsigned), s);
     if (e != cudaSuccess) return e;
-    fn<<<grid, kBwdThreads, smem, s>>>(v, c, p, rgba, nsamples, grad_rgba, grad_tf, grad_vox, counter, tiles_x,
-                                       ntiles);
+    fn<<<grid, kBwdThreads, 0, s>>>(vol_dev(vol), c, p, rgba, nsamples, grad_rgba,
+                                    reinterpret_cast<float4 *>(vol->wtab), grad_vox, counter, tiles_x, ntiles);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const int n = 4 * p.K, chunk = 64;
+    dim3 rgrid((unsigned)((n + 255) / 256), (unsigned)((nrows + chunk - 1) / chunk));
+    reduce_rows<<<rgrid, 256, 0, s>>>(vol->wtab, nrows, n, grad_tf, chunk);
     return cudaGetLastError();
 }
 
-// Largest table the backward supports: eight warps of private FP32 bins must
-// fit in shared memory.
+// Largest table the backward supports (the staged kernel keeps eight warps of
+// bins in shared memory).
 int backward_max_tf_size() { return (int)(200 * 1024 / (sizeof(float) * 4 * kBwdWarps)); }
 
-cudaError_t launch_backward(const VolDev &v, vr_dtype dt, const CamDev &c, const ParamDev &p, const float4 *rgba,
+cudaError_t launch_backward(vr_volume *vol, const CamDev &c, const ParamDev &p, const float4 *rgba,
                             const uint32_t *nsamples, const float4 *grad_rgba, double *grad_tf, float *grad_vox,
                             long long nvox, bool accumulate, unsigned *counter, cudaStream_t s)
 {
 #define VR_BWD_CASE(TT, LB) \
-    return launch_bwd_t<TT, LB>(v, c, p, rgba, nsamples, grad_rgba, grad_tf, grad_vox, nvox, accumulate, counter, s)
+    return launch_bwd_t<TT, LB>(vol, c, p, rgba, nsamples, grad_rgba, grad_tf, grad_vox, nvox, accumulate, counter, s)
 #define VR_BWD_DT(TT)                      \
-    switch (v.log2b) {                     \
+    switch (vol->log2b) {                  \
     case 4: VR_BWD_CASE(TT, 4);            \
     case 5: VR_BWD_CASE(TT, 5);            \
     case 6: VR_BWD_CASE(TT, 6);            \
     default: return cudaErrorInvalidValue; \
     }
-    switch (dt) {
+    switch (vol->store_dtype) {
     case VR_F32: VR_BWD_DT(float);
     case VR_F16: VR_BWD_DT(__half);
     case VR_BF16: VR_BWD_DT(__nv_bfloat16);

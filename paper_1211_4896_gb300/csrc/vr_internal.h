@@ -77,6 +77,9 @@ struct vr_volume {
     unsigned *counters = nullptr;      // last slot: device status word (timeouts)
     int counter_slots = 0;
     int next_counter = 0;
+    // backward scratch: one FP32 row of K RGBA gradient bins per warp
+    float *wtab = nullptr;
+    size_t wtab_cap = 0;         // floats
     // dense padded copy used by the shared-memory staged kernels
     void *dense = nullptr;
     int dense_px = 0;
@@ -106,10 +109,10 @@ cudaError_t launch_forward(const VolDev &v, vr_dtype dt, const CamDev &c, const 
                            uint32_t *nsamples, unsigned *counter, cudaStream_t s);
 cudaError_t launch_forward_texture(const vr_volume *vol, const CamDev &c, const ParamDev &p, float4 *out,
                                    uint32_t *nsamples, unsigned *counter, cudaStream_t s);
-cudaError_t launch_backward(const VolDev &v, vr_dtype dt, const CamDev &c, const ParamDev &p,
-                            const float4 *rgba, const uint32_t *nsamples, const float4 *grad_rgba,
-                            double *grad_tf, float *grad_vox, long long nvox, bool accumulate,
-                            unsigned *counter, cudaStream_t s);
+cudaError_t launch_backward(vr_volume *vol, const CamDev &c, const ParamDev &p, const float4 *rgba,
+                            const uint32_t *nsamples, const float4 *grad_rgba, double *grad_tf, float *grad_vox,
+                            long long nvox, bool accumulate, unsigned *counter, cudaStream_t s);
+cudaError_t ensure_wtab(vr_volume *vol, size_t floats, cudaStream_t s);
 int backward_max_tf_size();
 DenseDev dense_dev(const vr_volume *vol);
 cudaError_t launch_densify(const void *src, vr_dtype src_dtype, vr_volume *vol, cudaStream_t s);
