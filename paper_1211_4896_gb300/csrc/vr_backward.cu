@@ -60,6 +60,88 @@ __device__ __forceinline__ void scatter_corners(float *gv, long long nx, long lo
     }
 }
 
+__device__ __forceinline__ float4 f4_axpy(float a, float4 x, float4 y)
+{
+    return make_float4(fmaf(a, x.x, y.x), fmaf(a, x.y, y.y), fmaf(a, x.z, y.z), fmaf(a, x.w, y.w));
+}
+
+// A ray's pending table-gradient contributions: bins b and b+1 of this
+// thread's row.  Consecutive samples whose bin pair coincides or overlaps are
+// added here and reach memory once.
+struct BinRun {
+    int b = -1;
+    float4 lo = {0.f, 0.f, 0.f, 0.f}, hi = {0.f, 0.f, 0.f, 0.f};
+    __device__ __forceinline__ void add(float4 *row, int i0, float w0, float w1, float4 dr)
+    {
+        if (i0 == b) {
+            lo = f4_axpy(w0, dr, lo);
+            hi = f4_axpy(w1, dr, hi);
+            return;
+        }
+        if (i0 == b + 1) {                 // new lower bin == pending upper bin
+            red_add_v4(row + b, lo);
+            lo = f4_axpy(w0, dr, hi);
+        } else if (i0 + 1 == b) {          // new upper bin == pending lower bin
+            red_add_v4(row + b + 1, hi);
+            hi = f4_axpy(w1, dr, lo);
+            lo = make_float4(w0 * dr.x, w0 * dr.y, w0 * dr.z, w0 * dr.w);
+            b = i0;
+            return;
+        } else {
+            flush(row);
+            lo = make_float4(w0 * dr.x, w0 * dr.y, w0 * dr.z, w0 * dr.w);
+        }
+        hi = make_float4(w1 * dr.x, w1 * dr.y, w1 * dr.z, w1 * dr.w);
+        b = i0;
+    }
+    __device__ __forceinline__ void flush(float4 *row)
+    {
+        if (b >= 0) {
+            red_add_v4(row + b, lo);
+            red_add_v4(row + b + 1, hi);
+        }
+        b = -1;
+    }
+};
+
+// A ray's pending voxel-gradient contributions to the 8 corners of one cell.
+struct CellRun {
+    float *base = nullptr;             // corner (x0, y0, z0) in the dense gradient
+    float acc[8];
+    __device__ __forceinline__ void add(float *gv, float fx, float fy, float fz, float dv, long long nx,
+                                        long long nyx)
+    {
+        if (gv != base) {
+            flush(nx, nyx);
+            base = gv;
+#pragma unroll
+            for (int q = 0; q < 8; ++q) acc[q] = 0.0f;
+        }
+        const float wx0 = 1.0f - fx, wy0 = 1.0f - fy, wz0 = 1.0f - fz;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const float a = ((q & 1) ? fy : wy0) * ((q & 2) ? fz : wz0) * dv;
+            acc[2 * q] = fmaf(wx0, a, acc[2 * q]);
+            acc[2 * q + 1] = fmaf(fx, a, acc[2 * q + 1]);
+        }
+    }
+    __device__ __forceinline__ void flush(long long nx, long long nyx)
+    {
+        if (!base) return;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            float *b = base + ((q & 1) ? nx : 0) + ((q & 2) ? nyx : 0);
+            if ((reinterpret_cast<uintptr_t>(b) & 7u) == 0) {
+                red_add_v2(b, acc[2 * q], acc[2 * q + 1]);
+            } else {
+                red_add_f32(b, acc[2 * q]);
+                red_add_f32(b + 1, acc[2 * q + 1]);
+            }
+        }
+        base = nullptr;
+    }
+};
+
 template <typename VT, int LOG2B>
 __global__ void __launch_bounds__(kBwdThreads) bwd_kernel(VolDev v, CamDev c, ParamDev p,
                                                            const float4 *__restrict__ rgba,
@@ -103,6 +185,8 @@ __global__ void __launch_bounds__(kBwdThreads) bwd_kernel(VolDev v, CamDev c, Pa
         float T = 1.0f;
         int k = 0;
         bool active = n > 0;
+        BinRun bins;
+        CellRun cells;
         // one sample: gradient of (cell, f); the next sample's gathers go to (ncell, nf)
         auto step = [&](const Cell &cell, const Corners &f, Cell &ncell, Corners &nf) {
             const bool more = k + 1 < n;
@@ -120,17 +204,15 @@ __global__ void __launch_bounds__(kBwdThreads) bwd_kernel(VolDev v, CamDev c, Pa
             const float om = 1.0f - a;
             const float da = T * cg - (om > 0.0f ? R / om : 0.0f);
             if (aT != 0.0f || da != 0.0f) {
-                const float w1 = tp.w, w0 = 1.0f - tp.w;
                 const float4 dr = make_float4(aT * g.x, aT * g.y, aT * g.z, da);
-                red_add_v4(row + tp.i0, make_float4(w0 * dr.x, w0 * dr.y, w0 * dr.z, w0 * dr.w));
-                red_add_v4(row + tp.i0 + 1, make_float4(w1 * dr.x, w1 * dr.y, w1 * dr.z, w1 * dr.w));
+                bins.add(row, tp.i0, 1.0f - tp.w, tp.w, dr);
                 if (grad_vox && tp.interior) {
                     const float4 e0 = __ldg(p.tf + tp.i0), e1 = __ldg(p.tf + tp.i0 + 1);
                     const float dv = (dr.x * (e1.x - e0.x) + dr.y * (e1.y - e0.y) + dr.z * (e1.z - e0.z) +
                                       dr.w * (e1.w - e0.w)) * vscale;
                     if (dv != 0.0f)
-                        scatter_corners(grad_vox + ((long long)cell.z0 * nyx + (long long)cell.y0 * v.nx + cell.x0),
-                                        v.nx, nyx, cell.fx, cell.fy, cell.fz, dv);
+                        cells.add(grad_vox + ((long long)cell.z0 * nyx + (long long)cell.y0 * v.nx + cell.x0),
+                                  cell.fx, cell.fy, cell.fz, dv, v.nx, nyx);
                 }
             }
             T = fmaf(-a, T, T);
@@ -149,6 +231,8 @@ __global__ void __launch_bounds__(kBwdThreads) bwd_kernel(VolDev v, CamDev c, Pa
             if (!__any_sync(kFull, active)) break;
             if (active) step(c1, f1, c0, f0);
         }
+        bins.flush(row);
+        cells.flush(v.nx, nyx);
     }
 }
 
