@@ -58,6 +58,34 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
+def kernel_sources_sha256() -> str:
+    """Digest of the CUDA sources, to tell whether recorded counters still
+    describe the kernels being run."""
+    import hashlib
+    d = os.path.join(ROOT, "paper_1211_4896_gb300", "csrc")
+    h = hashlib.sha256()
+    for name in sorted(os.listdir(d)):
+        if name.endswith((".cu", ".cuh", ".h", ".cpp")):
+            with open(os.path.join(d, name), "rb") as f:
+                h.update(name.encode() + b"\0" + f.read())
+    return h.hexdigest()
+
+
+def recorded_traffic(kernel: str):
+    """DRAM bytes (read + write) per launch of `kernel` on this workload, from
+    the ncu capture summarised in profiles/traffic_scale_1024.json; None when
+    the kernels have changed since that capture."""
+    p = os.path.join(ROOT, "profiles", "traffic_scale_1024.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        rec = json.load(f)
+    if rec.get("sources_sha256") != kernel_sources_sha256():
+        return None
+    v = rec.get("dram_bytes_per_launch", {}).get(kernel)
+    return None if v is None else float(v)
+
+
 class ClockSampler:
     """nvidia-smi clock/throttle sampling during the timed region."""
 
@@ -371,12 +399,14 @@ def run_ours(args, rank, world, local_rank):
     peak, peak_kind = measured_peaks()
     bwd_total = bwd_ms * nv
     if bwd_total >= fwd_ms:
-        dom, dom_ms, per = "bwd_kernel (+ FP64 table-gradient reduce), per view", bwd_ms, samples_per_step / nv
+        dom, dom_key, dom_ms, per = ("bwd_kernel (one view; timed with its scratch clear and FP64 row sum)",
+                                     "bwd_kernel", bwd_ms, samples_per_step / nv)
     else:
-        dom, dom_ms, per = "batched_kernel (8 views, one launch)", fwd_ms, samples_per_step
+        dom, dom_key, dom_ms, per = "batched_kernel (8 views, one launch)", "batched_kernel", fwd_ms, samples_per_step
     achieved = per * GATHER_BYTES_F32 / (dom_ms * 1e-3) / 1e9
+    traffic = recorded_traffic(dom_key)
     roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
-            "frac": achieved / peak, "traffic": None, "peak_source": peak_kind,
+            "frac": achieved / peak, "traffic": traffic, "peak_source": peak_kind,
             "per_unit": "8 x 4 B trilinear gathers per composited sample"}
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,

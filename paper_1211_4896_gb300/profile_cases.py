@@ -1,0 +1,56 @@
+"""Small, self-contained cases for profiling one kernel launch with ncu
+(inputs larger than L2, a few GB on the device at most):
+
+  python -m paper_1211_4896_gb300.profile_cases fwd   # 512^3 f32, 4 orbit views at 960x540, step 1, ERT 0.99
+  python -m paper_1211_4896_gb300.profile_cases bwd   # 256^3 f32, 2 views at 512^2, step 0.5, table = ramp + 5% noise
+
+Each case renders its views forward then backward on cuda:0, so capture the
+kernel of interest with -k and -c.
+"""
+import os
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+
+def case_fwd():
+    import torch
+    import synth
+    import paper_1211_4896_gb300 as P
+    dev = torch.device("cuda")
+    dims = (512, 512, 512)
+    vol = P.Volume(synth.hi_cube(dims, 250, 25, 9, device=dev), "f32")
+    tf = torch.from_numpy(synth.tf_ramp(256)).to(dev)
+    ns = None
+    for c in synth.orbit_cameras(dims, 4, 40.0, 960, 540, start_deg=20.0):
+        img, ns = P.render(vol, c, tf, -3.0, 50.0, 1.0, 0.99)
+        P.render_backward(vol, c, tf, -3.0, 50.0, 1.0, img, ns, torch.randn_like(img), 0.99)
+    torch.cuda.synchronize()
+    print("ok", int(ns.sum()))
+
+
+def case_bwd():
+    import torch
+    import synth
+    import paper_1211_4896_gb300 as P
+    dev = torch.device("cuda")
+    dims = (256, 256, 256)
+    vol = P.Volume(synth.hi_cube(dims, 160, 0, 5, device=dev), "f32")
+    hidden = torch.from_numpy(synth.tf_ramp(256)).to(dev)
+    g = torch.Generator(device=dev)
+    g.manual_seed(5)
+    tf = (hidden + 0.05 * torch.rand(hidden.shape, device=dev, generator=g)).clamp(0, 1).contiguous()
+    ns = None
+    for c in synth.orbit_cameras(dims, 2, 40.0, 512, 512, start_deg=20.0):
+        img, ns = P.render(vol, c, tf, -3.0, 50.0, 0.5, 2.0)
+        P.render_backward(vol, c, tf, -3.0, 50.0, 0.5, img, ns, torch.randn_like(img), 2.0)
+    torch.cuda.synchronize()
+    print("ok", int(ns.sum()))
+
+
+if __name__ == "__main__":
+    from paper_1211_4896_gb300 import build
+    build.build()
+    {"fwd": case_fwd, "bwd": case_bwd}[sys.argv[1] if len(sys.argv) > 1 else "fwd"]()
