@@ -110,6 +110,8 @@ typedef struct {
     int64_t bytes;            /* device bytes held by the bricked copy */
     int64_t dense_bytes;      /* device bytes of the dense row-padded copy (0 until the first
                                  staged call) */
+    int64_t copy_bytes;       /* device bytes of the brick copies (see vr_volume_create) */
+    int copies;               /* which copies exist: bit 0 x-, bit 1 y-, bit 2 z-fastest */
 } vr_volume_info_t;
 
 /* ------------------------------------------------------------------------
@@ -120,9 +122,25 @@ typedef struct {
  * Copies the dense cube dev_cube (src_dtype, dims = {nx, ny, nz}, each >= 2,
  * x fastest) into a bricked copy in store_dtype: bricks of B^3 cells, each
  * stored as (B+1)^3 voxels so that all 8 trilinear corners of any cell lie in
- * one brick.  (The first VR_FILTER_SOFTWARE_STAGED call adds a dense copy with
- * rows padded to 8 elements, streamed slab by slab into shared memory.)  F32 -> F16/BF16 rounds to nearest even.  brick = 0 picks 16;
- * otherwise 16, 32 or 64.  origin/spacing may be NULL (0 and 1).  The
+ * one brick, x fastest inside a brick.  F32 -> F16/BF16 rounds to nearest
+ * even.  brick = 0 picks 16; otherwise 16, 32 or 64.  origin/spacing may be
+ * NULL (0 and 1).
+ *
+ * Copies made later, on first use: the first VR_FILTER_SOFTWARE_STAGED call
+ * adds a dense copy with rows padded to 8 elements, streamed slab by slab
+ * into shared memory.  The first software-filter call (render, backward or
+ * batched) with a view whose image rows run closest to an axis adds a copy of
+ * the bricks with that axis fastest inside each brick, so that the rays of
+ * one warp read neighbouring elements: for float storage a plain copy for the
+ * y or z axis (the bricks serve the x axis), as many bytes as the bricks; for
+ * 16-bit storage a paired copy for any axis, each element holding its own
+ * value and the next one along that axis so that four loads fetch a cell's
+ * eight corners (twice the bricks' bytes).  A copy is built only outside
+ * stream capture, while the device keeps as much memory again free (else the
+ * bricks themselves serve), synchronising cuda_stream once; environment
+ * variable VR_BRICK_COPIES=0 turns copies off.  Results do not depend on
+ * which copy a view reads.  vr_volume_update refreshes every copy;
+ * vr_volume_info reports them.  The
  * caller keeps dev_cube; the call synchronises `cuda_stream` before returning
  * the handle in *out.  Errors: INVALID_ARG, OOM, CUDA.
  * ---------------------------------------------------------------------- */
@@ -184,8 +202,9 @@ vr_status vr_render_backward(vr_volume_t vol, const vr_camera *cam, const vr_par
  * Batched render (not in the paper; its "many smaller cubes" future-work
  * item motivates it): n jobs, each with its own volume, camera, parameters
  * and output, rendered by ONE persistent kernel launch whose CTAs pull ray
- * tiles of all jobs from a shared work queue.  Results equal n vr_render
- * calls.  Software filter only.
+ * tiles of all jobs from a shared work queue (one launch per brick copy
+ * the views read, so at most four).  Results equal n vr_render calls.
+ * Software filter only.
  * ---------------------------------------------------------------------- */
 typedef struct {
     vr_volume_t vol;
@@ -224,10 +243,12 @@ vr_status vr_autotune_batched(const vr_job *jobs, int n, vr_batch_opts *best, vo
  * and a work counter for every new job list; this variant keeps both in one
  * static device array sized for VR_NOALLOC_MAX_JOBS jobs (about 64 KB, held by
  * every GPU that loads the library until the process exits), uploads the
- * descriptors with cudaMemcpyAsync and zeroes the counter with
+ * descriptors with cudaMemcpyAsync and zeroes the work counters with
  * cudaMemsetAsync on cuda_stream.  The caller still passes the volumes and the
- * outputs.  Jobs are rendered exactly as by vr_render_batched (same kernel);
- * tile_w x tile_h is the warp's ray tile (0, 0 = 8 x 4).
+ * outputs.  Jobs are rendered exactly as by vr_render_batched (same kernels);
+ * tile_w x tile_h is the warp's ray tile (0, 0 = 8 x 4).  It never builds a
+ * brick copy (see vr_volume_create): a view reads such a copy only when an
+ * earlier call built it.
  *   - n > VR_NOALLOC_MAX_JOBS returns VR_ERR_INVALID_ARG and launches nothing.
  *   - The first call on a device looks up the device address of the static
  *     array (cudaGetSymbolAddress) and the kernel's occupancy; make that first

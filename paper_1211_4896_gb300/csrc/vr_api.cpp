@@ -1,6 +1,7 @@
 // vr_api.cpp -- host side of the C ABI declared in include/vr.h: argument
 // validation, volume handles, camera preparation and kernel dispatch.
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <new>
@@ -203,7 +204,75 @@ VolDev vol_dev(const vr_volume *vol)
     v.nbz = (int)vol->nb[2];
     v.log2b = vol->log2b;
     v.stride = vol->stride;
+    v.order = 0;
+    v.paired = 0;
     return v;
+}
+
+VolDev vol_dev_copy(const vr_volume *vol, int copy)
+{
+    VolDev v = vol_dev(vol);
+    if (copy >= 0 && copy < 3 && vol->copies[copy]) {
+        v.data = vol->copies[copy];
+        v.order = copy;
+        v.paired = vol->store_dtype != VR_F32;
+    }
+    return v;
+}
+
+// Brick copy for a camera: the copy whose fastest axis is the one along
+// which the image's horizontal direction (in voxel units) is longest, so that
+// a warp's row of eight rays reads neighbouring elements (and, paired, every
+// load brings two corners).  A float view along x reads the bricks
+// themselves.  The copy is built on first use when `may_build`, the stream is
+// not being captured and the device keeps as much memory again free; it is
+// complete before the call returns, so any stream may read it.  Otherwise (or
+// with VR_BRICK_COPIES=0 in the environment) the bricks themselves serve (-1).
+int preferred_copy(vr_volume *vol, const vr_camera *cam, bool may_build, cudaStream_t s)
+{
+    static const bool enabled = [] {
+        const char *e = std::getenv("VR_BRICK_COPIES");
+        return !(e && e[0] == '0');
+    }();
+    if (!enabled) return -1;
+    double f[3] = {cam->forward[0], cam->forward[1], cam->forward[2]}, r[3];
+    cross3(f, cam->up, r);
+    double best = -1.0;
+    int axis = 0;
+    for (int a = 0; a < 3; ++a) {
+        const double c = std::fabs(r[a]) / vol->spacing[a];
+        if (c > best * (1.0 + 1e-9)) {
+            best = c;
+            axis = a;
+        }
+    }
+    if (vol->store_dtype == VR_F32 && axis == 0) return -1;
+    if (vol->copies[axis]) return axis;
+    if (!may_build) return -1;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
+        cudaGetLastError();
+        return -1;
+    }
+    const size_t bytes = copy_bytes(vol);
+    size_t free_b = 0, total_b = 0;
+    if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess || free_b < 2 * bytes) {
+        cudaGetLastError();
+        return -1;
+    }
+    void *p = nullptr;
+    if (cudaMalloc(&p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return -1;
+    }
+    vol->copies[axis] = p;
+    if (launch_copy(vol, axis, s) != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(p);
+        vol->copies[axis] = nullptr;
+        return -1;
+    }
+    return axis;
 }
 
 // The last slot of the ring is the volume's device status word.
@@ -277,6 +346,8 @@ static void free_volume(vr_volume *vol)
     if (vol->bricks) cudaFree(vol->bricks);
     if (vol->dense) cudaFree(vol->dense);
     if (vol->wtab) cudaFree(vol->wtab);
+    for (void *o : vol->copies)
+        if (o) cudaFree(o);
     if (vol->counters) cudaFree(vol->counters);
     delete vol;
 }
@@ -371,6 +442,8 @@ vr_status vr_volume_update(vr_volume_t vol, const void *dev_cube, vr_dtype src_d
         vol->tex_array = nullptr;
     }
     cudaError_t e = launch_brick(dev_cube, src_dtype, vol, s);
+    for (int o = 0; o < 3 && e == cudaSuccess; ++o)
+        if (vol->copies[o]) e = launch_copy(vol, o, s);
     if (e == cudaSuccess && vol->dense) e = launch_densify(dev_cube, src_dtype, vol, s);
     if (e != cudaSuccess) return cuda_fail(e, "vr_volume_update");
     return VR_OK;
@@ -399,6 +472,13 @@ vr_status vr_volume_info(vr_volume_t vol, vr_volume_info_t *out)
     out->brick = vol->brick;
     out->bytes = (int64_t)vol->bytes;
     out->dense_bytes = (int64_t)vol->dense_bytes;
+    out->copy_bytes = 0;
+    out->copies = 0;
+    for (int o = 0; o < 3; ++o)
+        if (vol->copies[o]) {
+            out->copy_bytes += (int64_t)copy_bytes(vol);
+            out->copies |= 1 << o;
+        }
     return VR_OK;
 }
 
@@ -433,7 +513,8 @@ vr_status vr_render(vr_volume_t vol, const vr_camera *cam, const vr_params *para
         e = launch_forward_staged(dense_dev(vol), vol->store_dtype, c, p, reinterpret_cast<float4 *>(dev_rgba_out),
                                   dev_nsamples_out, ctr, status_word(vol), s);
     } else {
-        e = launch_forward(vol_dev(vol), vol->store_dtype, c, p, reinterpret_cast<float4 *>(dev_rgba_out),
+        e = launch_forward(vol_dev_copy(vol, preferred_copy(vol, cam, true, s)), vol->store_dtype, c, p,
+                           reinterpret_cast<float4 *>(dev_rgba_out),
                            dev_nsamples_out, ctr, s);
     }
     if (e != cudaSuccess) return cuda_fail(e, "vr_render launch");
@@ -486,7 +567,9 @@ vr_status vr_render_backward(vr_volume_t vol, const vr_camera *cam, const vr_par
                                    dev_nsamples, reinterpret_cast<const float4 *>(dev_grad_rgba), dev_grad_tf,
                                    dev_grad_vox, nvox, acc, ctr, status_word(vol), s);
     else
-        e = launch_backward(vol, c, p, reinterpret_cast<const float4 *>(dev_rgba), dev_nsamples,
+        e = launch_backward(vol_dev_copy(vol, preferred_copy(vol, cam, true, s)), vol, c, p,
+                            reinterpret_cast<const float4 *>(dev_rgba),
+                            dev_nsamples,
                             reinterpret_cast<const float4 *>(dev_grad_rgba), dev_grad_tf, dev_grad_vox, nvox, acc, ctr,
                             s);
     if (e != cudaSuccess) return cuda_fail(e, "vr_render_backward launch");

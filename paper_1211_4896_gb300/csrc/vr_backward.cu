@@ -142,7 +142,7 @@ struct CellRun {
     }
 };
 
-template <typename VT, int LOG2B>
+template <typename VT, int LOG2B, int L>
 __global__ void __launch_bounds__(kBwdThreads) bwd_kernel(VolDev v, CamDev c, ParamDev p,
                                                            const float4 *__restrict__ rgba,
                                                            const uint32_t *__restrict__ nsamples,
@@ -188,11 +188,11 @@ __global__ void __launch_bounds__(kBwdThreads) bwd_kernel(VolDev v, CamDev c, Pa
         BinRun bins;
         CellRun cells;
         // one sample: gradient of (cell, f); the next sample's gathers go to (ncell, nf)
-        auto step = [&](const Cell &cell, const Corners &f, Cell &ncell, Corners &nf) {
+        auto step = [&](const Cell &cell, const Gathered<VT, L> &f, Cell &ncell, Gathered<VT, L> &nf) {
             const bool more = k + 1 < n;
             if (more) {
-                ncell = locate<LOG2B>(v, sample_pos(ray, k + 1, p.step));
-                fetch_corners<VT, LOG2B>(v, ncell, nf);
+                ncell = locate<LOG2B, L>(v, sample_pos(ray, k + 1, p.step));
+                fetch_corners<VT, LOG2B, L>(v, ncell, nf);
             }
             const float val = interp_corners(cell, f);
             TfPos tp;
@@ -220,10 +220,10 @@ __global__ void __launch_bounds__(kBwdThreads) bwd_kernel(VolDev v, CamDev c, Pa
             if (!more) active = false;
         };
         Cell c0, c1;
-        Corners f0, f1;
+        Gathered<VT, L> f0, f1;
         if (active) {
-            c0 = locate<LOG2B>(v, sample_pos(ray, 0, p.step));
-            fetch_corners<VT, LOG2B>(v, c0, f0);
+            c0 = locate<LOG2B, L>(v, sample_pos(ray, 0, p.step));
+            fetch_corners<VT, LOG2B, L>(v, c0, f0);
         }
         for (;;) {      // two register sets in turn (no copy of the prefetched sample)
             if (!__any_sync(kFull, active)) break;
@@ -248,12 +248,12 @@ __global__ void __launch_bounds__(256) reduce_rows(const float *__restrict__ row
     atomicAdd(out + q, acc);
 }
 
-template <typename T, int LOG2B>
-static cudaError_t launch_bwd_t(vr_volume *vol, const CamDev &c, const ParamDev &p, const float4 *rgba,
+template <typename T, int LOG2B, int L>
+static cudaError_t launch_bwd_t(const VolDev &v, vr_volume *vol, const CamDev &c, const ParamDev &p, const float4 *rgba,
                                 const uint32_t *nsamples, const float4 *grad_rgba, double *grad_tf, float *grad_vox,
                                 long long nvox, bool accumulate, unsigned *counter, cudaStream_t s)
 {
-    auto fn = bwd_kernel<T, LOG2B>;
+    auto fn = bwd_kernel<T, LOG2B, L>;
     const int tiles_x = (c.W + 7) / 8, tiles_y = (c.H + 3) / 4;
     const unsigned ntiles = (unsigned)tiles_x * (unsigned)tiles_y;
     const int per_sm = occupancy_blocks((const void *)fn, kBwdThreads, 0);
@@ -274,7 +274,7 @@ static cudaError_t launch_bwd_t(vr_volume *vol, const CamDev &c, const ParamDev 
     }
     e = cudaMemsetAsync(counter, 0, sizeof(unsigned), s);
     if (e != cudaSuccess) return e;
-    fn<<<grid, kBwdThreads, 0, s>>>(vol_dev(vol), c, p, rgba, nsamples, grad_rgba,
+    fn<<<grid, kBwdThreads, 0, s>>>(v, c, p, rgba, nsamples, grad_rgba,
                                     reinterpret_cast<float4 *>(vol->wtab), grad_vox, counter, tiles_x, ntiles);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -288,27 +288,19 @@ static cudaError_t launch_bwd_t(vr_volume *vol, const CamDev &c, const ParamDev 
 // bins in shared memory).
 int backward_max_tf_size() { return (int)(200 * 1024 / (sizeof(float) * 4 * kBwdWarps)); }
 
-cudaError_t launch_backward(vr_volume *vol, const CamDev &c, const ParamDev &p, const float4 *rgba,
+cudaError_t launch_backward(const VolDev &v, vr_volume *vol, const CamDev &c, const ParamDev &p, const float4 *rgba,
                             const uint32_t *nsamples, const float4 *grad_rgba, double *grad_tf, float *grad_vox,
                             long long nvox, bool accumulate, unsigned *counter, cudaStream_t s)
 {
-#define VR_BWD_CASE(TT, LB) \
-    return launch_bwd_t<TT, LB>(vol, c, p, rgba, nsamples, grad_rgba, grad_tf, grad_vox, nvox, accumulate, counter, s)
-#define VR_BWD_DT(TT)                      \
-    switch (vol->log2b) {                  \
-    case 4: VR_BWD_CASE(TT, 4);            \
-    case 5: VR_BWD_CASE(TT, 5);            \
-    case 6: VR_BWD_CASE(TT, 6);            \
-    default: return cudaErrorInvalidValue; \
-    }
-    switch (vol->store_dtype) {
-    case VR_F32: VR_BWD_DT(float);
-    case VR_F16: VR_BWD_DT(__half);
-    case VR_BF16: VR_BWD_DT(__nv_bfloat16);
-    }
-    return cudaErrorInvalidValue;
-#undef VR_BWD_DT
-#undef VR_BWD_CASE
+    return visit_layout(
+        v, vol->store_dtype,
+        [&](auto lay) {
+            using Y = decltype(lay);
+            return launch_bwd_t<typename Y::type, Y::log2b, Y::order>(v, vol, c, p, rgba, nsamples, grad_rgba,
+                                                                       grad_tf, grad_vox, nvox, accumulate, counter,
+                                                                       s);
+        },
+        cudaErrorInvalidValue);
 }
 
 }  // namespace vr

@@ -26,8 +26,18 @@ struct JobDev {
     unsigned tile_begin;     // first global tile index of this job
 };
 
-template <typename T, int LOG2B>
-__global__ void __launch_bounds__(kBatThreads) batched_kernel(const JobDev *__restrict__ jobs, int njobs,
+// One launch serves the jobs that read one brick copy (element type T, order
+// L; template parameters, so each instance keeps the register budget of a
+// single march; a batch reading several copies launches once per copy).
+// CTAs per SM the register budget is sized for: paired 16-bit copies fit
+// four (64 registers) without spills and gain from it; the other kernels keep
+// the compiler's choice (for float, three CTAs measured faster than four).
+template <typename T> struct BatMinBlocks { static constexpr int value = 0; };   // 0: no minimum
+template <> struct BatMinBlocks<Pair<__half>> { static constexpr int value = 4; };
+template <> struct BatMinBlocks<Pair<__nv_bfloat16>> { static constexpr int value = 4; };
+
+template <typename T, int LOG2B, int L>
+__global__ void __launch_bounds__(kBatThreads, BatMinBlocks<T>::value) batched_kernel(const JobDev *__restrict__ jobs, int njobs,
                                                                unsigned total_tiles, unsigned *counter,
                                                                int log2_tw)
 {
@@ -55,42 +65,45 @@ __global__ void __launch_bounds__(kBatThreads) batched_kernel(const JobDev *__re
         Ray ray;
         const bool hit = inside && setup_ray(c, v.nx, v.ny, v.nz, p.step, i, j, ray);
         Composite acc{0.0f, 0.0f, 0.0f, 1.0f};
-        const int used = march_ray<T, LOG2B>(v, p, ray, hit, acc);
+        const int used = march_ray<T, LOG2B, L>(v, p, ray, hit, acc);
         if (inside) write_pixel(p, acc, hit ? used : 0, J.out, J.nsamples, (long long)j * c.W + i);
     }
 }
 
 using BatchFn = void (*)(const JobDev *, int, unsigned, unsigned *, int);
 
-static BatchFn pick_kernel(vr_dtype dt, int log2b)
+// Kernel for the brick layout v reads (see Layout).
+static BatchFn pick_kernel(const VolDev &v, vr_dtype dt)
 {
-#define VR_BAT_DT(TT)                                 \
-    switch (log2b) {                                  \
-    case 4: return batched_kernel<TT, 4>;             \
-    case 5: return batched_kernel<TT, 5>;             \
-    case 6: return batched_kernel<TT, 6>;             \
-    default: return nullptr;                          \
-    }
-    switch (dt) {
-    case VR_F32: VR_BAT_DT(float);
-    case VR_F16: VR_BAT_DT(__half);
-    case VR_BF16: VR_BAT_DT(__nv_bfloat16);
-    }
-    return nullptr;
-#undef VR_BAT_DT
+    return visit_layout(
+        v, dt,
+        [](auto lay) -> BatchFn {
+            using Y = decltype(lay);
+            return batched_kernel<typename Y::type, Y::log2b, Y::order>;
+        },
+        (BatchFn) nullptr);
 }
+
+constexpr int kGroups = 4;       // brick copies a batch may read: the bricks + 3 paired copies
+
+// The jobs reading one brick copy: descriptors [first, first + njobs) of the
+// grouped table, tiles numbered from 0 within the group.
+struct Segment {
+    int first = 0, njobs = 0;
+    unsigned total_tiles = 0;
+    BatchFn fn = nullptr;
+    unsigned grid = 0;
+};
 
 // A prepared batch: job descriptors resident on the device, a work counter,
 // and (optionally) the instantiated graph of one launch.
 struct BatchPlan {
     std::vector<unsigned char> key;
     JobDev *djobs = nullptr;
-    unsigned *counter = nullptr;
+    unsigned *counter = nullptr;       // one work counter per group
     int njobs = 0;
-    unsigned total_tiles = 0;
-    BatchFn fn = nullptr;
+    Segment seg[kGroups];
     int log2_tw = 3;
-    unsigned grid = 1;
     cudaGraphExec_t exec = nullptr;
     int device = 0;
 };
@@ -105,12 +118,18 @@ static int log2_of(int x)
     return (1 << l) == x ? l : -1;
 }
 
-static vr_status prepare_jobs(const vr_job *jobs, int n, int tile_w, std::vector<JobDev> &hj, unsigned &total,
-                              vr_dtype &dt, int &log2b)
+// Builds the descriptors of all jobs into hj[0, n), grouped by the brick copy
+// each view reads (group g = copy + 1: the bricks first, then the paired
+// copies in order 0, 1, 2; call order within a group), and fills seg[] with
+// each group's offset, tile count and kernel.  group_of is host scratch of n
+// ints.  may_build allows building a missing copy.
+static vr_status prepare_jobs(const vr_job *jobs, int n, int tile_w, bool may_build, cudaStream_t s, JobDev *hj,
+                              int *group_of, Segment seg[kGroups], const char *who)
 {
     const int tile_h = 32 / tile_w;
-    total = 0;
-    hj.resize((size_t)n);
+    vr_dtype dt = VR_F32;
+    int log2b = 5;
+    for (int g = 0; g < kGroups; ++g) seg[g] = Segment();
     for (int q = 0; q < n; ++q) {
         const vr_job &J = jobs[q];
         if (!J.vol) return (set_error("jobs[" + std::to_string(q) + "].vol is NULL"), VR_ERR_INVALID_ARG);
@@ -118,28 +137,74 @@ static vr_status prepare_jobs(const vr_job *jobs, int n, int tile_w, std::vector
             return (set_error("jobs[" + std::to_string(q) + "].dev_rgba_out must be non-NULL and 16-byte aligned"),
                     VR_ERR_INVALID_ARG);
         if (J.params.filter != VR_FILTER_SOFTWARE)
-            return (set_error("vr_render_batched: software filter only"), VR_ERR_UNSUPPORTED);
+            return (set_error(std::string(who) + ": software filter only"), VR_ERR_UNSUPPORTED);
         if (q == 0) {
             dt = J.vol->store_dtype;
             log2b = J.vol->log2b;
         } else if (J.vol->store_dtype != dt || J.vol->log2b != log2b) {
-            return (set_error("vr_render_batched: all volumes of a batch must share store dtype and brick size"),
+            return (set_error(std::string(who) + ": all volumes of a batch must share store dtype and brick size"),
                     VR_ERR_UNSUPPORTED);
         }
-        JobDev &d = hj[(size_t)q];
+        group_of[q] = preferred_copy(J.vol, &J.cam, may_build, s) + 1;
+        ++seg[group_of[q]].njobs;
+    }
+    int fill[kGroups];
+    for (int g = 0, first = 0; g < kGroups; first += seg[g].njobs, ++g) fill[g] = seg[g].first = first;
+    for (int q = 0; q < n; ++q) {
+        const vr_job &J = jobs[q];
+        Segment &g = seg[group_of[q]];
+        JobDev &d = hj[fill[group_of[q]]++];
         prepare_camera(J.vol, &J.cam, &d.c);
         prepare_params(&J.params, &d.p);
-        d.v = vol_dev(J.vol);
+        d.v = vol_dev_copy(J.vol, group_of[q] - 1);
         d.out = reinterpret_cast<float4 *>(J.dev_rgba_out);
         d.nsamples = J.dev_nsamples_out;
         d.tiles_x = (J.cam.width + tile_w - 1) / tile_w;
         const unsigned tiles_y = (unsigned)((J.cam.height + tile_h - 1) / tile_h);
-        d.tile_begin = total;
-        const unsigned long long t = (unsigned long long)total + (unsigned long long)d.tiles_x * tiles_y;
-        if (t > 0xFFFFFFF0ull) return (set_error("vr_render_batched: too many ray tiles"), VR_ERR_INVALID_ARG);
-        total = (unsigned)t;
+        d.tile_begin = g.total_tiles;
+        const unsigned long long t = (unsigned long long)g.total_tiles + (unsigned long long)d.tiles_x * tiles_y;
+        if (t > 0xFFFFFFF0ull) return (set_error(std::string(who) + ": too many ray tiles"), VR_ERR_INVALID_ARG);
+        g.total_tiles = (unsigned)t;
+    }
+    for (int g = 0; g < kGroups; ++g) {
+        if (!seg[g].njobs) continue;
+        seg[g].fn = pick_kernel(hj[seg[g].first].v, dt);     // one layout per group
+        if (!seg[g].fn) return (set_error(std::string(who) + ": unsupported brick size"), VR_ERR_UNSUPPORTED);
     }
     return VR_OK;
+}
+
+// Persistent grid of each group: ctas_per_sm (0: the occupancy limit) x SMs,
+// capped at one warp per tile.
+static void size_grids(Segment seg[kGroups], int ctas)
+{
+    for (int o = 0; o < kGroups; ++o) {
+        Segment &g = seg[o];
+        if (!g.njobs) continue;
+        int per_sm = ctas;
+        if (per_sm == 0 &&
+            (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void *)g.fn, kBatThreads, 0) !=
+                 cudaSuccess ||
+             per_sm < 1))
+            per_sm = 1;
+        const unsigned grid = (unsigned)(per_sm * sm_count());
+        const unsigned useful = (g.total_tiles + kBatThreads / 32 - 1) / (kBatThreads / 32);
+        g.grid = grid < useful ? grid : (useful ? useful : 1);
+    }
+}
+
+// Counter reset and one launch per non-empty group, in order on stream s.
+static cudaError_t launch_segments(const Segment seg[kGroups], const JobDev *djobs, unsigned *counters,
+                                   int log2_tw, cudaStream_t s)
+{
+    cudaError_t e = cudaMemsetAsync(counters, 0, kGroups * sizeof(unsigned), s);
+    for (int o = 0; o < kGroups && e == cudaSuccess; ++o) {
+        const Segment &g = seg[o];
+        if (!g.njobs) continue;
+        g.fn<<<g.grid, kBatThreads, 0, s>>>(djobs + g.first, g.njobs, g.total_tiles, counters + o, log2_tw);
+        e = cudaGetLastError();
+    }
+    return e;
 }
 
 static vr_status validate_batch(const vr_job *jobs, int n, const vr_batch_opts *opts, int &tile_w, int &ctas)
@@ -215,21 +280,20 @@ extern "C" vr_status vr_render_batched(const vr_job *jobs, int n, const vr_batch
     auto it = g_plans.find(key);
     if (it != g_plans.end()) plan = it->second;
     if (!plan) {
-        std::vector<JobDev> hj;
-        unsigned total = 0;
-        vr_dtype dt = VR_F32;
-        int log2b = 5;
-        st = prepare_jobs(jobs, n, tile_w, hj, total, dt, log2b);
+        std::vector<JobDev> hj((size_t)n);
+        std::vector<int> group_of((size_t)n);
+        Segment seg[kGroups];
+        st = prepare_jobs(jobs, n, tile_w, true, s, hj.data(), group_of.data(), seg, "vr_render_batched");
         if (st != VR_OK) return st;
+        size_grids(seg, ctas);
         plan = new BatchPlan();
         plan->key = key;
         plan->njobs = n;
-        plan->total_tiles = total;
-        plan->fn = pick_kernel(dt, log2b);
+        for (int g = 0; g < kGroups; ++g) plan->seg[g] = seg[g];
         plan->log2_tw = log2_of(tile_w);
         plan->device = dev;
         cudaError_t e = cudaMalloc(&plan->djobs, sizeof(JobDev) * (size_t)n);
-        if (e == cudaSuccess) e = cudaMalloc(&plan->counter, sizeof(unsigned));
+        if (e == cudaSuccess) e = cudaMalloc(&plan->counter, kGroups * sizeof(unsigned));
         if (e == cudaSuccess)
             e = cudaMemcpyAsync(plan->djobs, hj.data(), sizeof(JobDev) * (size_t)n, cudaMemcpyHostToDevice, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
@@ -237,15 +301,6 @@ extern "C" vr_status vr_render_batched(const vr_job *jobs, int n, const vr_batch
             destroy_plan(plan);
             return cuda_fail(e, "vr_render_batched: plan upload");
         }
-        int per_sm = ctas;
-        if (per_sm == 0) {
-            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void *)plan->fn, kBatThreads, 0) !=
-                    cudaSuccess || per_sm < 1)
-                per_sm = 1;
-        }
-        unsigned grid = (unsigned)(per_sm * sm_count());
-        const unsigned useful = (total + kBatThreads / 32 - 1) / (kBatThreads / 32);
-        plan->grid = grid < useful ? grid : (useful ? useful : 1);
         if (g_plans.size() > 64) {           // bound the cache
             cudaStreamSynchronize(s);
             for (auto &kv : g_plans) destroy_plan(kv.second);
@@ -262,10 +317,9 @@ extern "C" vr_status vr_render_batched(const vr_job *jobs, int n, const vr_batch
             cudaGraph_t graph = nullptr;
             e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
             if (e == cudaSuccess) {
-                cudaMemsetAsync(plan->counter, 0, sizeof(unsigned), cap);
-                plan->fn<<<plan->grid, kBatThreads, 0, cap>>>(plan->djobs, plan->njobs, plan->total_tiles,
-                                                             plan->counter, plan->log2_tw);
+                const cudaError_t le = launch_segments(plan->seg, plan->djobs, plan->counter, plan->log2_tw, cap);
                 e = cudaStreamEndCapture(cap, &graph);
+                if (e == cudaSuccess) e = le;
             }
             if (e == cudaSuccess) e = cudaGraphInstantiate(&plan->exec, graph, 0);
             if (graph) cudaGraphDestroy(graph);
@@ -277,12 +331,7 @@ extern "C" vr_status vr_render_batched(const vr_job *jobs, int n, const vr_batch
         }
         e = cudaGraphLaunch(plan->exec, s);
     } else {
-        e = cudaMemsetAsync(plan->counter, 0, sizeof(unsigned), s);
-        if (e == cudaSuccess) {
-            plan->fn<<<plan->grid, kBatThreads, 0, s>>>(plan->djobs, plan->njobs, plan->total_tiles, plan->counter,
-                                                        plan->log2_tw);
-            e = cudaGetLastError();
-        }
+        e = launch_segments(plan->seg, plan->djobs, plan->counter, plan->log2_tw, s);
     }
     if (e != cudaSuccess) return cuda_fail(e, "vr_render_batched launch");
     return VR_OK;
@@ -347,8 +396,8 @@ namespace vr {
 constexpr int kNoAllocMaxJobs = VR_NOALLOC_MAX_JOBS;
 
 struct NoAllocScratch {
-    unsigned counter;
-    unsigned pad[63];                     // keeps the descriptor table 256-byte aligned
+    unsigned counter[kGroups];            // one work counter per brick-copy group
+    unsigned pad[64 - kGroups];           // keeps the descriptor table 256-byte aligned
     JobDev jobs[kNoAllocMaxJobs];
 };
 
@@ -403,58 +452,21 @@ extern "C" vr_status vr_render_batched_noalloc(const vr_job *jobs, int n, int ti
         vr_status st = validate_job(&jobs[q], q);
         if (st != VR_OK) return st;
     }
-    // descriptors, built in a fixed host buffer (no host allocation either)
+    // descriptors, built in fixed host buffers (no host allocation either)
     static thread_local JobDev hj[kNoAllocMaxJobs];
-    vr_dtype dt = VR_F32;
-    int log2b = 5;
-    unsigned total = 0;
-    for (int q = 0; q < n; ++q) {
-        const vr_job &J = jobs[q];
-        if (!J.dev_rgba_out || !is_aligned16(J.dev_rgba_out))
-            return (set_error("jobs[" + std::to_string(q) + "].dev_rgba_out must be non-NULL and 16-byte aligned"),
-                    VR_ERR_INVALID_ARG);
-        if (J.params.filter != VR_FILTER_SOFTWARE)
-            return (set_error("vr_render_batched_noalloc: software filter only"), VR_ERR_UNSUPPORTED);
-        if (q == 0) {
-            dt = J.vol->store_dtype;
-            log2b = J.vol->log2b;
-        } else if (J.vol->store_dtype != dt || J.vol->log2b != log2b) {
-            return (set_error("vr_render_batched_noalloc: all volumes must share store dtype and brick size"),
-                    VR_ERR_UNSUPPORTED);
-        }
-        JobDev &d = hj[q];
-        prepare_camera(J.vol, &J.cam, &d.c);
-        prepare_params(&J.params, &d.p);
-        d.v = vol_dev(J.vol);
-        d.out = reinterpret_cast<float4 *>(J.dev_rgba_out);
-        d.nsamples = J.dev_nsamples_out;
-        d.tiles_x = (J.cam.width + tile_w - 1) / tile_w;
-        const unsigned tiles_y = (unsigned)((J.cam.height + tile_h - 1) / tile_h);
-        d.tile_begin = total;
-        const unsigned long long t = (unsigned long long)total + (unsigned long long)d.tiles_x * tiles_y;
-        if (t > 0xFFFFFFF0ull) return (set_error("vr_render_batched_noalloc: too many ray tiles"), VR_ERR_INVALID_ARG);
-        total = (unsigned)t;
-    }
-    vr_status st;
+    static thread_local int group_of[kNoAllocMaxJobs];
+    Segment seg[kGroups];
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    // only brick copies that exist already are used (building one allocates)
+    vr_status st = prepare_jobs(jobs, n, tile_w, false, s, hj, group_of, seg, "vr_render_batched_noalloc");
+    if (st != VR_OK) return st;
+    size_grids(seg, 0);
     NoAllocScratch *scratch = noalloc_scratch_ptr(st);
     if (!scratch) return st;
-    BatchFn fn = pick_kernel(dt, log2b);
-    if (!fn) return (set_error("vr_render_batched_noalloc: unsupported brick size"), VR_ERR_UNSUPPORTED);
-    int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void *)fn, kBatThreads, 0) != cudaSuccess ||
-        per_sm < 1)
-        per_sm = 1;
-    unsigned grid = (unsigned)(per_sm * sm_count());
-    const unsigned useful = (total + kBatThreads / 32 - 1) / (kBatThreads / 32);
-    if (grid > useful) grid = useful ? useful : 1;
-    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
-    // The counter must start at zero; the descriptors overwrite the last call's.
-    cudaError_t e = cudaMemsetAsync(&scratch->counter, 0, sizeof(unsigned), s);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(scratch->jobs, hj, sizeof(JobDev) * (size_t)n, cudaMemcpyHostToDevice, s);
+    // The counters must start at zero; the descriptors overwrite the last call's.
+    cudaError_t e = cudaMemcpyAsync(scratch->jobs, hj, sizeof(JobDev) * (size_t)n, cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) return cuda_fail(e, "vr_render_batched_noalloc: scratch upload");
-    fn<<<grid, kBatThreads, 0, s>>>(scratch->jobs, n, total, &scratch->counter, log2_tw);
-    e = cudaGetLastError();
+    e = launch_segments(seg, scratch->jobs, scratch->counter, log2_tw, s);
     if (e != cudaSuccess) return cuda_fail(e, "vr_render_batched_noalloc launch");
     return VR_OK;
 }

@@ -6,6 +6,8 @@
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
+#include <type_traits>
+
 #include "vr_internal.h"
 
 namespace vr {
@@ -21,6 +23,74 @@ template <> __device__ __forceinline__ float ldv<__half>(const __half *p) { retu
 template <> __device__ __forceinline__ float ldv<__nv_bfloat16>(const __nv_bfloat16 *p)
 {
     return __bfloat162float(__ldg(p));
+}
+
+// Element of a paired brick copy of a 16-bit volume: the element's own value
+// and the value one step further along the copy's fastest axis, loaded
+// together (4 bytes), so that four loads fetch the eight corners of a cell.  The last layer along
+// that axis (the apron, never a cell origin) repeats its own value.
+template <typename S> struct Pair;
+template <> struct Pair<__half> {
+    using V = __half2;
+    static __device__ __forceinline__ V pack(__half a, __half b) { return __halves2half2(a, b); }
+};
+template <> struct Pair<__nv_bfloat16> {
+    using V = __nv_bfloat162;
+    static __device__ __forceinline__ V pack(__nv_bfloat16 a, __nv_bfloat16 b) { return __halves2bfloat162(a, b); }
+};
+
+template <typename T> struct is_pair { static constexpr bool value = false; };
+template <typename S> struct is_pair<Pair<S>> { static constexpr bool value = true; };
+
+// ---------------------------------------------------------------------------
+// Brick layouts a kernel can read (host-side dispatch).  Every volume has its
+// x-fastest bricks (element type = storage type, order 0).  Copies for views
+// along other axes: float volumes keep plain copies in order 1 or 2 (element
+// type float); 16-bit volumes keep paired copies in any order (element type
+// Pair<S>, as many bytes as float bricks).
+// ---------------------------------------------------------------------------
+template <typename T, int LOG2B_, int L_> struct Layout {
+    using type = T;
+    static constexpr int log2b = LOG2B_, order = L_;
+};
+
+// Calls f(Layout<...>{}) for the layout of v (storage type S); returns
+// `none` for a layout no volume builds.
+template <typename S, int LOG2B, typename F, typename R>
+R visit_layout_b(const VolDev &v, F &&f, R none)
+{
+    if (!v.paired && v.order == 0) return f(Layout<S, LOG2B, 0>{});
+    if constexpr (std::is_same<S, float>::value) {
+        if (!v.paired && v.order == 1) return f(Layout<S, LOG2B, 1>{});
+        if (!v.paired && v.order == 2) return f(Layout<S, LOG2B, 2>{});
+    } else {
+        if (v.paired && v.order == 0) return f(Layout<Pair<S>, LOG2B, 0>{});
+        if (v.paired && v.order == 1) return f(Layout<Pair<S>, LOG2B, 1>{});
+        if (v.paired && v.order == 2) return f(Layout<Pair<S>, LOG2B, 2>{});
+    }
+    return none;
+}
+
+template <typename S, typename F, typename R>
+R visit_layout_s(const VolDev &v, F &&f, R none)
+{
+    switch (v.log2b) {
+    case 4: return visit_layout_b<S, 4>(v, f, none);
+    case 5: return visit_layout_b<S, 5>(v, f, none);
+    case 6: return visit_layout_b<S, 6>(v, f, none);
+    }
+    return none;
+}
+
+template <typename F, typename R>
+R visit_layout(const VolDev &v, vr_dtype dt, F &&f, R none)
+{
+    switch (dt) {
+    case VR_F32: return visit_layout_s<float>(v, f, none);
+    case VR_F16: return visit_layout_s<__half>(v, f, none);
+    case VR_BF16: return visit_layout_s<__nv_bfloat16>(v, f, none);
+    }
+    return none;
 }
 
 __device__ __forceinline__ float to_f(float v) { return v; }
@@ -107,7 +177,19 @@ struct Cell {
     int x0, y0, z0;
 };
 
-template <int LOG2B>
+// Element order inside a brick.  Order 0 is x fastest, then y, then z; order
+// 1 is y fastest, then x, then z; order 2 is z fastest, then y, then x.  A
+// render reads the paired copy whose fastest axis runs closest to the image's
+// horizontal axis, so the lanes of a warp's row of rays read neighbouring
+// elements whatever the view direction.
+template <int LOG2B, int L> struct BrickOrder {
+    static constexpr int B1 = (1 << LOG2B) + 1;
+    static constexpr int SX = L == 0 ? 1 : (L == 1 ? B1 : B1 * B1);
+    static constexpr int SY = L == 1 ? 1 : B1;
+    static constexpr int SZ = L == 2 ? 1 : B1 * B1;
+};
+
+template <int LOG2B, int L = 0>
 __device__ __forceinline__ Cell locate(const VolDev &v, float3 p)
 {
     Cell c;
@@ -117,53 +199,81 @@ __device__ __forceinline__ Cell locate(const VolDev &v, float3 p)
     c.fx = p.x - (float)c.x0;
     c.fy = p.y - (float)c.y0;
     c.fz = p.z - (float)c.z0;
-    constexpr int B = 1 << LOG2B, B1 = B + 1;
+    using O = BrickOrder<LOG2B, L>;
+    constexpr int B = 1 << LOG2B;
     const int bx = c.x0 >> LOG2B, by = c.y0 >> LOG2B, bz = c.z0 >> LOG2B;
     const int lx = c.x0 & (B - 1), ly = c.y0 & (B - 1), lz = c.z0 & (B - 1);
     const long long brick = ((long long)bz * v.nby + by) * v.nbx + bx;
-    c.base = brick * v.stride + (lz * B1 + ly) * B1 + lx;
+    c.base = brick * v.stride + (lx * O::SX + ly * O::SY + lz * O::SZ);
     return c;
 }
 
-template <typename T, int LOG2B>
-__device__ __forceinline__ float trilinear(const VolDev &v, const Cell &c)
-{
-    constexpr int B1 = (1 << LOG2B) + 1, P = B1 * B1;
-    const T *b = static_cast<const T *>(v.data) + c.base;
-    const float v000 = ldv(b), v100 = ldv(b + 1), v010 = ldv(b + B1), v110 = ldv(b + B1 + 1);
-    const float v001 = ldv(b + P), v101 = ldv(b + P + 1), v011 = ldv(b + P + B1), v111 = ldv(b + P + B1 + 1);
-    const float c00 = fmaf(c.fx, v100 - v000, v000), c10 = fmaf(c.fx, v110 - v010, v010);
-    const float c01 = fmaf(c.fx, v101 - v001, v001), c11 = fmaf(c.fx, v111 - v011, v011);
-    const float c0 = fmaf(c.fy, c10 - c00, c00), c1 = fmaf(c.fy, c11 - c01, c01);
-    return fmaf(c.fz, c1 - c0, c0);
-}
-
-// The eight corners of a cell, loaded separately from their interpolation so
-// that a march can issue the next sample's loads before it composites the
-// current one (two samples' gathers in flight per thread).
+// The eight corners of a cell as floats (index bit 0: +x, bit 1: +y, bit 2: +z).
 struct Corners {
-    float v[8];       // index bit 0: +x, bit 1: +y, bit 2: +z
+    float v[8];
 };
 
-template <typename T, int LOG2B>
-__device__ __forceinline__ void fetch_corners(const VolDev &v, const Cell &c, Corners &f)
+__device__ __forceinline__ float2 widen2(__half2 w) { return __half22float2(w); }
+__device__ __forceinline__ float2 widen2(__nv_bfloat162 w) { return __bfloat1622float2(w); }
+
+// The eight corners of a cell as loaded from a brick copy of element type T
+// and order L.  They are widened to float only where they are interpolated,
+// so the loads of a sample can be issued several samples ahead of its use
+// (16-bit pairs stay packed, two corners per register, while in flight).
+template <typename T, int L> struct Gathered {
+    T v[8];
+    __device__ __forceinline__ float at(int q) const { return to_f(v[q]); }
+};
+template <typename S, int L> struct Gathered<Pair<S>, L> {
+    typename Pair<S>::V p[4];     // pairs along the fastest axis of order L
+    __device__ __forceinline__ float at(int q) const
+    {
+        const int i = L == 0 ? (q >> 1) : (L == 1 ? ((q & 1) | ((q >> 2) << 1)) : (q & 3));
+        const int h = L == 0 ? (q & 1) : (L == 1 ? ((q >> 1) & 1) : (q >> 2));
+        const float2 w = widen2(p[i]);
+        return h ? w.y : w.x;
+    }
+};
+
+// T is the stored element: float / __half / __nv_bfloat16 (eight loads) or
+// Pair<...> (four paired loads; each returns a corner and its neighbour along
+// the fastest axis of order L).
+template <typename T, int LOG2B, int L>
+__device__ __forceinline__ void fetch_corners(const VolDev &v, const Cell &c, Gathered<T, L> &f)
 {
-    constexpr int B1 = (1 << LOG2B) + 1, P = B1 * B1;
-    const T *b = static_cast<const T *>(v.data) + c.base;
-    f.v[0] = ldv(b);
-    f.v[1] = ldv(b + 1);
-    f.v[2] = ldv(b + B1);
-    f.v[3] = ldv(b + B1 + 1);
-    f.v[4] = ldv(b + P);
-    f.v[5] = ldv(b + P + 1);
-    f.v[6] = ldv(b + P + B1);
-    f.v[7] = ldv(b + P + B1 + 1);
+    using O = BrickOrder<LOG2B, L>;
+    if constexpr (is_pair<T>::value) {
+        using V = typename T::V;
+        const V *b = static_cast<const V *>(v.data) + c.base;
+        // the three pair bases besides b: the two non-fastest axes and both
+        constexpr int A1 = L == 0 ? O::SY : O::SX;
+        constexpr int A2 = L == 2 ? O::SY : O::SZ;
+        f.p[0] = __ldg(b);
+        f.p[1] = __ldg(b + A1);
+        f.p[2] = __ldg(b + A2);
+        f.p[3] = __ldg(b + A1 + A2);
+    } else {
+        const T *b = static_cast<const T *>(v.data) + c.base;
+        f.v[0] = __ldg(b);
+        f.v[1] = __ldg(b + O::SX);
+        f.v[2] = __ldg(b + O::SY);
+        f.v[3] = __ldg(b + O::SX + O::SY);
+        f.v[4] = __ldg(b + O::SZ);
+        f.v[5] = __ldg(b + O::SZ + O::SX);
+        f.v[6] = __ldg(b + O::SZ + O::SY);
+        f.v[7] = __ldg(b + O::SZ + O::SX + O::SY);
+    }
 }
 
-__device__ __forceinline__ float interp_corners(const Cell &c, const Corners &f)
+// Trilinear interpolation, always along x, then y, then z (so every copy
+// gives the same bits).
+template <typename G>
+__device__ __forceinline__ float interp_corners(const Cell &c, const G &f)
 {
-    const float c00 = fmaf(c.fx, f.v[1] - f.v[0], f.v[0]), c10 = fmaf(c.fx, f.v[3] - f.v[2], f.v[2]);
-    const float c01 = fmaf(c.fx, f.v[5] - f.v[4], f.v[4]), c11 = fmaf(c.fx, f.v[7] - f.v[6], f.v[6]);
+    const float v0 = f.at(0), v1 = f.at(1), v2 = f.at(2), v3 = f.at(3);
+    const float v4 = f.at(4), v5 = f.at(5), v6 = f.at(6), v7 = f.at(7);
+    const float c00 = fmaf(c.fx, v1 - v0, v0), c10 = fmaf(c.fx, v3 - v2, v2);
+    const float c01 = fmaf(c.fx, v5 - v4, v4), c11 = fmaf(c.fx, v7 - v6, v6);
     const float c0 = fmaf(c.fy, c10 - c00, c00), c1 = fmaf(c.fy, c11 - c01, c01);
     return fmaf(c.fz, c1 - c0, c0);
 }
@@ -235,17 +345,27 @@ struct Composite {
     float r, g, b, T;
 };
 
-// One sample: composites (cur, fc) and, when the ray goes on, issues the
-// gathers of the next sample into (nxt, fn).
-template <typename T, int LOG2B>
+// Samples whose gathers are in flight ahead of the one being composited (1
+// or 2).  A deeper pipeline keeps more gathers in flight per warp but costs a
+// Cell and a Gathered set of registers per stage, and so resident warps.
+// Measured on the 1024^3 eight-view workload: 16-bit layouts gain from depth
+// 2 (oblique views 10% faster; packed pairs keep the register cost low),
+// float loses from it (axis views 3% slower), so float keeps depth 1.
+template <typename T> struct Pipeline { static constexpr int depth = 2; };
+template <> struct Pipeline<float> { static constexpr int depth = 1; };
+
+// One sample: composites (cur, fc) and, while the ray goes on, issues the
+// gathers of sample k + depth into (nxt, fn).
+template <typename T, int LOG2B, int L>
 __device__ __forceinline__ void march_step(const VolDev &v, const ParamDev &p, const Ray &ray, int &k, bool &active,
-                                           Composite &acc, const Cell &cur, const Corners &fc, Cell &nxt,
-                                           Corners &fn)
+                                           Composite &acc, const Cell &cur, const Gathered<T, L> &fc, Cell &nxt,
+                                           Gathered<T, L> &fn)
 {
+    constexpr int D = Pipeline<T>::depth;
     const bool more = k + 1 < ray.n;
-    if (more) {
-        nxt = locate<LOG2B>(v, sample_pos(ray, k + 1, p.step));
-        fetch_corners<T, LOG2B>(v, nxt, fn);
+    if (D == 1 ? more : k + D < ray.n) {
+        nxt = locate<LOG2B, L>(v, sample_pos(ray, k + D, p.step));
+        fetch_corners<T, LOG2B, L>(v, nxt, fn);
     }
     const float val = interp_corners(cur, fc);
     TfPos tp;
@@ -259,24 +379,41 @@ __device__ __forceinline__ void march_step(const VolDev &v, const ParamDev &p, c
     if (!more || acc.T <= p.t_stop) active = false;
 }
 
-// The loop body is unrolled twice over two register sets (ping-pong), so the
-// prefetched sample never has to be copied into the current one.
-template <typename T, int LOG2B>
+// The loop body is unrolled over depth + 1 register sets that take turns, so
+// a prefetched sample is never copied.
+template <typename T, int LOG2B, int L>
 __device__ __forceinline__ int march_ray(const VolDev &v, const ParamDev &p, const Ray &ray, bool active,
                                          Composite &acc)
 {
+    constexpr int D = Pipeline<T>::depth;
+    static_assert(D == 1 || D == 2, "pipeline depth 1 or 2");
     int k = 0;
-    Cell c0, c1;
-    Corners f0, f1;
+    Cell c0, c1, c2;
+    Gathered<T, L> f0, f1, f2;
     if (active) {
-        c0 = locate<LOG2B>(v, sample_pos(ray, 0, p.step));
-        fetch_corners<T, LOG2B>(v, c0, f0);
+        c0 = locate<LOG2B, L>(v, sample_pos(ray, 0, p.step));
+        fetch_corners<T, LOG2B, L>(v, c0, f0);
+        if (D == 2 && ray.n > 1) {
+            c1 = locate<LOG2B, L>(v, sample_pos(ray, 1, p.step));
+            fetch_corners<T, LOG2B, L>(v, c1, f1);
+        }
     }
-    for (;;) {
-        if (!__any_sync(kFull, active)) break;
-        if (active) march_step<T, LOG2B>(v, p, ray, k, active, acc, c0, f0, c1, f1);
-        if (!__any_sync(kFull, active)) break;
-        if (active) march_step<T, LOG2B>(v, p, ray, k, active, acc, c1, f1, c0, f0);
+    if constexpr (D == 1) {
+        for (;;) {
+            if (!__any_sync(kFull, active)) break;
+            if (active) march_step<T, LOG2B, L>(v, p, ray, k, active, acc, c0, f0, c1, f1);
+            if (!__any_sync(kFull, active)) break;
+            if (active) march_step<T, LOG2B, L>(v, p, ray, k, active, acc, c1, f1, c0, f0);
+        }
+    } else {
+        for (;;) {
+            if (!__any_sync(kFull, active)) break;
+            if (active) march_step<T, LOG2B, L>(v, p, ray, k, active, acc, c0, f0, c2, f2);
+            if (!__any_sync(kFull, active)) break;
+            if (active) march_step<T, LOG2B, L>(v, p, ray, k, active, acc, c1, f1, c0, f0);
+            if (!__any_sync(kFull, active)) break;
+            if (active) march_step<T, LOG2B, L>(v, p, ray, k, active, acc, c2, f2, c1, f1);
+        }
     }
     return k;
 }

@@ -21,7 +21,7 @@ namespace vr {
 
 constexpr int kFwdThreads = 256;
 
-template <typename T, int LOG2B>
+template <typename T, int LOG2B, int L>
 __global__ void __launch_bounds__(kFwdThreads) fwd_kernel(VolDev v, CamDev c, ParamDev p, float4 *out,
                                                            uint32_t *nsamples, unsigned *counter, int tiles_x,
                                                            unsigned ntiles)
@@ -38,7 +38,7 @@ __global__ void __launch_bounds__(kFwdThreads) fwd_kernel(VolDev v, CamDev c, Pa
         Ray ray;
         const bool hit = inside && setup_ray(c, v.nx, v.ny, v.nz, p.step, i, j, ray);
         Composite acc{0.0f, 0.0f, 0.0f, 1.0f};
-        const int used = march_ray<T, LOG2B>(v, p, ray, hit, acc);
+        const int used = march_ray<T, LOG2B, L>(v, p, ray, hit, acc);
         if (inside) write_pixel(p, acc, hit ? used : 0, out, nsamples, (long long)j * c.W + i);
     }
 }
@@ -115,13 +115,13 @@ static int fwd_ctas_per_sm(const void *fn)
     return (env > 0 && env < occ) ? env : occ;
 }
 
-template <typename T, int LOG2B>
+template <typename T, int LOG2B, int L>
 static cudaError_t launch_fwd_t(const VolDev &v, const CamDev &c, const ParamDev &p, float4 *out,
                                 uint32_t *nsamples, unsigned *counter, cudaStream_t s)
 {
     const int tiles_x = (c.W + 7) / 8, tiles_y = (c.H + 3) / 4;
     const unsigned ntiles = (unsigned)tiles_x * (unsigned)tiles_y;
-    auto fn = fwd_kernel<T, LOG2B>;
+    auto fn = fwd_kernel<T, LOG2B, L>;
     const int per_sm = fwd_ctas_per_sm((const void *)fn);
     unsigned grid = (unsigned)(per_sm * sm_count());
     const unsigned max_useful = (ntiles + kFwdThreads / 32 - 1) / (kFwdThreads / 32);
@@ -136,22 +136,13 @@ static cudaError_t launch_fwd_t(const VolDev &v, const CamDev &c, const ParamDev
 cudaError_t launch_forward(const VolDev &v, vr_dtype dt, const CamDev &c, const ParamDev &p, float4 *out,
                            uint32_t *nsamples, unsigned *counter, cudaStream_t s)
 {
-#define VR_FWD_CASE(TT, LB) return launch_fwd_t<TT, LB>(v, c, p, out, nsamples, counter, s)
-#define VR_FWD_DT(TT)                                   \
-    switch (v.log2b) {                                  \
-    case 4: VR_FWD_CASE(TT, 4);                         \
-    case 5: VR_FWD_CASE(TT, 5);                         \
-    case 6: VR_FWD_CASE(TT, 6);                         \
-    default: return cudaErrorInvalidValue;              \
-    }
-    switch (dt) {
-    case VR_F32: VR_FWD_DT(float);
-    case VR_F16: VR_FWD_DT(__half);
-    case VR_BF16: VR_FWD_DT(__nv_bfloat16);
-    }
-    return cudaErrorInvalidValue;
-#undef VR_FWD_DT
-#undef VR_FWD_CASE
+    return visit_layout(
+        v, dt,
+        [&](auto lay) {
+            using Y = decltype(lay);
+            return launch_fwd_t<typename Y::type, Y::log2b, Y::order>(v, c, p, out, nsamples, counter, s);
+        },
+        cudaErrorInvalidValue);
 }
 
 cudaError_t launch_forward_texture(const vr_volume *vol, const CamDev &c, const ParamDev &p, float4 *out,

@@ -50,6 +50,8 @@ struct VolDev {
     int nbx, nby, nbz;
     int log2b;             // B = 1 << log2b
     long long stride;      // elements per brick (>= (B+1)^3, padded)
+    int order;             // element order inside a brick (0: x, 1: y, 2: z fastest)
+    int paired;            // 1: each element holds (own value, next value along the fastest axis)
 };
 
 // Dense copy of the volume, x fastest, rows padded to a multiple of 8
@@ -77,6 +79,10 @@ struct vr_volume {
     unsigned *counters = nullptr;      // last slot: device status word (timeouts)
     int counter_slots = 0;
     int next_counter = 0;
+    // copies of the bricks in element order 0 (x), 1 (y), 2 (z fastest), built
+    // on the first software-filter call that prefers them: plain float copies
+    // in order 1 or 2 (bytes each), paired 16-bit copies in any order (2 * bytes)
+    void *copies[3] = {nullptr, nullptr, nullptr};
     // backward scratch: one FP32 row of K RGBA gradient bins per warp
     float *wtab = nullptr;
     size_t wtab_cap = 0;         // floats
@@ -109,7 +115,13 @@ cudaError_t launch_forward(const VolDev &v, vr_dtype dt, const CamDev &c, const 
                            uint32_t *nsamples, unsigned *counter, cudaStream_t s);
 cudaError_t launch_forward_texture(const vr_volume *vol, const CamDev &c, const ParamDev &p, float4 *out,
                                    uint32_t *nsamples, unsigned *counter, cudaStream_t s);
-cudaError_t launch_backward(vr_volume *vol, const CamDev &c, const ParamDev &p, const float4 *rgba,
+// Brick copy a software-filter view reads: -1 the bricks themselves, o in
+// {0, 1, 2} the copy in element order o (see vr_volume.copies).
+VolDev vol_dev_copy(const vr_volume *vol, int copy);
+int preferred_copy(vr_volume *vol, const vr_camera *cam, bool may_build, cudaStream_t s);
+size_t copy_bytes(const vr_volume *vol);
+cudaError_t launch_copy(vr_volume *vol, int order, cudaStream_t s);
+cudaError_t launch_backward(const VolDev &v, vr_volume *vol, const CamDev &c, const ParamDev &p, const float4 *rgba,
                             const uint32_t *nsamples, const float4 *grad_rgba, double *grad_tf, float *grad_vox,
                             long long nvox, bool accumulate, unsigned *counter, cudaStream_t s);
 cudaError_t ensure_wtab(vr_volume *vol, size_t floats, cudaStream_t s);

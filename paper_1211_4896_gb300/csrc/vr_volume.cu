@@ -178,4 +178,99 @@ vr_status build_texture(vr_volume *vol, cudaStream_t s)
     return VR_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Brick copies in element order L (see BrickOrder), built brick by brick from
+// the x-fastest bricks, one CTA per brick; reads are coalesced, writes follow
+// the new order.  Float volumes get plain copies in order 1 or 2.  16-bit
+// volumes get paired copies in any order: element (lx, ly, lz) holds its own
+// value and the next one along the order's fastest axis, so that four loads
+// fetch a cell's eight corners.
+// ---------------------------------------------------------------------------
+template <typename D, int LOG2B, int L>
+__global__ void __launch_bounds__(256) reorder_kernel(const D *__restrict__ src, D *__restrict__ dst, long long stride)
+{
+    using O = BrickOrder<LOG2B, L>;
+    constexpr int B1 = O::B1;
+    const D *s = src + (long long)blockIdx.x * stride;
+    D *o = dst + (long long)blockIdx.x * stride;
+    for (int e = threadIdx.x; e < (int)stride; e += blockDim.x) {
+        if (e >= B1 * B1 * B1) {      // padding
+            o[e] = s[e];
+            continue;
+        }
+        const int lz = e / (B1 * B1), r = e - lz * B1 * B1, ly = r / B1, lx = r - ly * B1;
+        o[lx * O::SX + ly * O::SY + lz * O::SZ] = s[e];
+    }
+}
+
+template <typename D, int LOG2B, int L>
+__global__ void __launch_bounds__(256) pair_kernel(const D *__restrict__ src, typename Pair<D>::V *__restrict__ dst,
+                                                   long long stride)
+{
+    using O = BrickOrder<LOG2B, L>;
+    constexpr int B1 = O::B1;
+    constexpr int NB = L == 0 ? 1 : (L == 1 ? B1 : B1 * B1);   // next element along the fastest axis (source)
+    const D *s = src + (long long)blockIdx.x * stride;
+    typename Pair<D>::V *o = dst + (long long)blockIdx.x * stride;
+    for (int e = threadIdx.x; e < (int)stride; e += blockDim.x) {
+        if (e >= B1 * B1 * B1) {      // padding
+            o[e] = Pair<D>::pack(convert_voxel<float, D>(0.0f), convert_voxel<float, D>(0.0f));
+            continue;
+        }
+        const int lz = e / (B1 * B1), r = e - lz * B1 * B1, ly = r / B1, lx = r - ly * B1;
+        const int la = L == 0 ? lx : (L == 1 ? ly : lz);
+        const D a = s[e];
+        const D nxt = la + 1 < B1 ? s[e + NB] : a;
+        o[lx * O::SX + ly * O::SY + lz * O::SZ] = Pair<D>::pack(a, nxt);
+    }
+}
+
+template <typename D, int LOG2B, int L>
+static void copy_t(vr_volume *vol, cudaStream_t s)
+{
+    const unsigned nbricks = (unsigned)(vol->nb[0] * vol->nb[1] * vol->nb[2]);
+    const D *src = static_cast<const D *>(vol->bricks);
+    if constexpr (std::is_same<D, float>::value) {
+        if constexpr (L != 0)
+            reorder_kernel<D, LOG2B, L><<<nbricks, 256, 0, s>>>(src, static_cast<D *>(vol->copies[L]), vol->stride);
+    } else {
+        pair_kernel<D, LOG2B, L><<<nbricks, 256, 0, s>>>(
+            src, static_cast<typename Pair<D>::V *>(vol->copies[L]), vol->stride);
+    }
+}
+
+template <typename D, int LOG2B>
+static void copy_b(vr_volume *vol, int order, cudaStream_t s)
+{
+    switch (order) {
+    case 0: copy_t<D, LOG2B, 0>(vol, s); break;
+    case 1: copy_t<D, LOG2B, 1>(vol, s); break;
+    default: copy_t<D, LOG2B, 2>(vol, s); break;
+    }
+}
+
+template <typename D>
+static void copy_d(vr_volume *vol, int order, cudaStream_t s)
+{
+    switch (vol->log2b) {
+    case 4: copy_b<D, 4>(vol, order, s); break;
+    case 5: copy_b<D, 5>(vol, order, s); break;
+    default: copy_b<D, 6>(vol, order, s); break;
+    }
+}
+
+size_t copy_bytes(const vr_volume *vol) { return vol->store_dtype == VR_F32 ? vol->bytes : 2 * vol->bytes; }
+
+cudaError_t launch_copy(vr_volume *vol, int order, cudaStream_t s)
+{
+    if (order < 0 || order > 2 || !vol->copies[order]) return cudaErrorInvalidValue;
+    if (vol->store_dtype == VR_F32 && order == 0) return cudaErrorInvalidValue;    // the bricks themselves
+    switch (vol->store_dtype) {
+    case VR_F32: copy_d<float>(vol, order, s); break;
+    case VR_F16: copy_d<__half>(vol, order, s); break;
+    case VR_BF16: copy_d<__nv_bfloat16>(vol, order, s); break;
+    }
+    return cudaGetLastError();
+}
+
 }  // namespace vr

@@ -1,0 +1,234 @@
+"""Brick copies.  A software-filter view whose image rows run closest to the
+y (z) axis reads a copy of the bricks stored with that axis fastest, so that
+the rays of one warp read neighbouring elements; for 16-bit storage the copy
+is paired (each element holds its own value and the next one along that
+axis, four loads per cell) and exists for the x axis too.  The arithmetic of
+a sample does not depend on where its corners are stored, so a view and the
+same view rolled by 90 degrees about its forward axis (same rays, image
+transposed; square image, the eye on the axis) agree bit for bit although
+they read different layouts; so do a render from the bricks themselves and
+one from a copy.  Covered: single renders, one batch reading every layout,
+the allocation-free batch, the backward, and a voxel update that must
+refresh the copies.  Both views are also checked against the oracle."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from tests.helpers import TOL_F32, compare, cuda_or_skip
+
+pytestmark = pytest.mark.gpu
+
+DIMS = (40, 36, 44)
+W = 48
+VMIN, VMAX, STEP = -3.0, 30.0, 0.5
+
+
+@pytest.fixture(scope="module")
+def torch():
+    return cuda_or_skip()
+
+
+@pytest.fixture(scope="module")
+def P(torch):
+    import paper_1211_4896_gb300 as P
+    return P
+
+
+def _cam(forward, up, kind):
+    c = [0.5 * (d - 1) for d in DIMS]
+    eye = [c[a] - 180.0 * forward[a] for a in range(3)]
+    if kind == "ortho":
+        return synth.camera_ortho(eye, forward, up, 50.0, W, W)
+    return synth.camera_persp(eye, forward, up, 20.0, W, W)
+
+
+# (camera reading x-fastest bricks, its roll reading order `order`, map from
+#  the x-order image to the rolled one: rolled[j, i] = base[rows, cols])
+_I = np.arange(W)[None, :]
+_J = np.arange(W)[:, None]
+PAIRS = [
+    # forward +z: up +y gives rows along -x; up +x gives rows along +y
+    (((0, 0, 1), (0, 1, 0)), ((0, 0, 1), (1, 0, 0)), 1, (W - 1 - _I, _J)),
+    # forward +y: up +z gives rows along +x; up +x gives rows along -z
+    (((0, 1, 0), (0, 0, 1)), ((0, 1, 0), (1, 0, 0)), 2, (_I, W - 1 - _J)),
+]
+
+
+@pytest.fixture(scope="module")
+def scene():
+    cube = synth.hi_cube(DIMS, n_blobs=8, n_disks=1, seed=7).numpy()
+    tf = synth.tf_random_pwl(seed=3, alpha_max=0.3)
+    return cube, tf
+
+
+def _volume(P, torch, cube, store="f32"):
+    return P.Volume(torch.from_numpy(np.ascontiguousarray(cube)).cuda(), store)
+
+
+def _noalloc(P, torch, vol, cam, tf):
+    """Render through the allocation-free batch (reads whatever copy exists)."""
+    from paper_1211_4896_gb300 import _lib as L
+    out = torch.full((W, W, 4), -1.0, device="cuda")
+    ns = torch.full((W, W), -1, device="cuda", dtype=torch.int32)
+    job = L.vr_job(vol.handle, L.make_camera(cam), L.make_params(tf.data_ptr(), tf.shape[0], VMIN, VMAX, STEP, 2.0),
+                   out.data_ptr(), ns.data_ptr())
+    L.vr_render_batched_noalloc([job], 8, 4, int(torch.cuda.current_stream().cuda_stream))
+    torch.cuda.synchronize()
+    return out, ns
+
+
+def _copies(P, vol):
+    return P._lib.vr_volume_info(vol.handle)["copies"]
+
+
+@pytest.mark.parametrize("store", ["f32", "f16"])
+@pytest.mark.parametrize("kind", ["ortho", "persp"])
+@pytest.mark.parametrize("pair", range(len(PAIRS)))
+def test_rolled_view_reads_a_copy_bit_identically(P, torch, scene, kind, pair, store):
+    cube, tf_np = scene
+    (fa, ua), (fb, ub), order, (rows, cols) = PAIRS[pair]
+    vol = _volume(P, torch, cube, store)
+    tf = torch.from_numpy(tf_np).cuda()
+    x_copy = 0 if store == "f32" else 0b1          # float views along x read the bricks themselves
+    try:
+        assert _copies(P, vol) == 0
+        camA, camB = _cam(fa, ua, kind), _cam(fb, ub, kind)
+        a, na = P.render(vol, camA, tf, VMIN, VMAX, STEP)
+        assert _copies(P, vol) == x_copy
+        b, nb = P.render(vol, camB, tf, VMIN, VMAX, STEP)
+        torch.cuda.synchronize()
+        info = P._lib.vr_volume_info(vol.handle)
+        assert info["copies"] == x_copy | 1 << order
+        per_copy = info["bytes"] * (1 if store == "f32" else 2)
+        assert info["copy_bytes"] == per_copy * bin(info["copies"]).count("1")
+        a, na, b, nb = a.cpu().numpy(), na.cpu().numpy(), b.cpu().numpy(), nb.cpu().numpy()
+        assert np.array_equal(b, a[rows, cols]) and np.array_equal(nb, na[rows, cols])
+        if store == "f32":
+            for cam, img, ns in ((camA, a, na), (camB, b, nb)):
+                compare(img, ns, oracle.render(cube, cam, tf_np, VMIN, VMAX, STEP), TOL_F32)
+        assert a[..., 3].max() > 0.1
+    finally:
+        vol.close()
+
+
+def test_batch_with_every_order_matches_single_renders(P, torch, scene):
+    """One batch holding views of all three axes (one launch per layout, in
+    one graph) equals the single renders bit for bit, replayed."""
+    cube, tf_np = scene
+    vol = _volume(P, torch, cube)
+    tf = torch.from_numpy(tf_np).cuda()
+    try:
+        cams = [_cam(f, u, k) for k in ("persp", "ortho") for (f, u) in
+                [PAIRS[0][0], PAIRS[0][1], PAIRS[1][1], PAIRS[1][0]]]
+        singles = [P.render(vol, c, tf, VMIN, VMAX, STEP) for c in cams]
+        jobs = [dict(vol=vol, cam=c, tf=tf, vmin=VMIN, vmax=VMAX, step=STEP,
+                     out=torch.empty((W, W, 4), device="cuda"),
+                     nsamples=torch.empty((W, W), device="cuda", dtype=torch.int32)) for c in cams]
+        for _ in range(2):
+            for j in jobs:
+                j["out"].fill_(-1.0)
+                j["nsamples"].fill_(-1)
+            P.render_batched(jobs, use_graph=True)
+            torch.cuda.synchronize()
+            for j, (img, ns) in zip(jobs, singles):
+                assert torch.equal(j["out"], img) and torch.equal(j["nsamples"], ns)
+        assert _copies(P, vol) == 0b110
+    finally:
+        vol.close()
+
+
+def test_noalloc_batch_uses_only_existing_copies(P, torch, scene):
+    """The allocation-free batch never builds a copy (it reads the bricks
+    themselves); once a render has built one it reads it.  Either way the
+    images equal the single render bit for bit."""
+    cube, tf_np = scene
+    vol = _volume(P, torch, cube)
+    tf = torch.from_numpy(tf_np).cuda()
+    try:
+        camB = _cam(*PAIRS[0][1], "persp")
+        first, ns_first = _noalloc(P, torch, vol, camB, tf)
+        assert _copies(P, vol) == 0
+        img, ns = P.render(vol, camB, tf, VMIN, VMAX, STEP)
+        torch.cuda.synchronize()
+        assert _copies(P, vol) == 0b10
+        assert torch.equal(first, img) and torch.equal(ns_first, ns)
+        again, ns_again = _noalloc(P, torch, vol, camB, tf)
+        assert torch.equal(again, img) and torch.equal(ns_again, ns)
+    finally:
+        vol.close()
+
+
+@pytest.mark.parametrize("store", ["f16", "bf16"])
+def test_half_paired_copies_match_bricks(P, torch, scene, store):
+    """16-bit storage: paired copies (two halves per load) render exactly what
+    the bricks themselves render, for an x-, y- and z-copy view."""
+    cube, tf_np = scene
+    vol = _volume(P, torch, cube, store)
+    tf = torch.from_numpy(tf_np).cuda()
+    try:
+        cams = [_cam(*PAIRS[0][0], "persp"), _cam(*PAIRS[0][1], "persp"), _cam(*PAIRS[1][1], "ortho")]
+        plain = [_noalloc(P, torch, vol, c, tf) for c in cams]
+        assert _copies(P, vol) == 0
+        for c, (img0, ns0) in zip(cams, plain):
+            img, ns = P.render(vol, c, tf, VMIN, VMAX, STEP)
+            torch.cuda.synchronize()
+            assert torch.equal(img, img0) and torch.equal(ns, ns0)
+        assert _copies(P, vol) == 0b111
+        (fa, ua), (fb, ub), order, (rows, cols) = PAIRS[0]
+        a = plain[0][0].cpu().numpy()
+        b = plain[1][0].cpu().numpy()
+        assert np.array_equal(b, a[rows, cols])
+    finally:
+        vol.close()
+
+
+@pytest.mark.parametrize("pair", range(len(PAIRS)))
+def test_backward_of_rolled_view_matches(P, torch, scene, pair):
+    """Adjoint of the rolled view with the rolled output gradient: the same
+    table and voxel gradients up to FP32 summation order."""
+    cube, tf_np = scene
+    (fa, ua), (fb, ub), order, (rows, cols) = PAIRS[pair]
+    vol = _volume(P, torch, cube)
+    tf = torch.from_numpy(tf_np).cuda()
+    try:
+        camA, camB = _cam(fa, ua, "persp"), _cam(fb, ub, "persp")
+        gA = np.random.default_rng(11).standard_normal((W, W, 4)).astype(np.float32)
+        gB = np.ascontiguousarray(gA[rows, cols])
+        out = []
+        for cam, g in ((camA, gA), (camB, gB)):
+            img, ns = P.render(vol, cam, tf, VMIN, VMAX, STEP)
+            gt, gv = P.render_backward(vol, cam, tf, VMIN, VMAX, STEP, img, ns, torch.from_numpy(g).cuda())
+            torch.cuda.synchronize()
+            out.append((gt.cpu().numpy(), gv.cpu().numpy()))
+        assert _copies(P, vol) == 1 << order
+        (tA, vA), (tB, vB) = out
+        assert np.abs(tA - tB).max() <= 1e-5 * np.abs(tA).max()
+        assert np.abs(vA - vB).max() <= 1e-5 * np.abs(vA).max()
+        assert np.abs(vA).max() > 0
+    finally:
+        vol.close()
+
+
+def test_update_refreshes_reordered_copies(P, torch, scene):
+    """After vr_volume_update a view reading a reordered copy sees the new
+    voxels: it still equals its x-order roll and the oracle on the new cube."""
+    cube, tf_np = scene
+    vol = _volume(P, torch, cube)
+    tf = torch.from_numpy(tf_np).cuda()
+    try:
+        (fa, ua), (fb, ub), order, (rows, cols) = PAIRS[1]
+        camA, camB = _cam(fa, ua, "ortho"), _cam(fb, ub, "ortho")
+        P.render(vol, camB, tf, VMIN, VMAX, STEP)
+        torch.cuda.synchronize()
+        assert _copies(P, vol) == 1 << order
+        cube2 = np.ascontiguousarray(cube[::-1, :, ::-1]) * np.float32(1.3)
+        vol.update(torch.from_numpy(cube2).cuda())
+        a, na = P.render(vol, camA, tf, VMIN, VMAX, STEP)
+        b, nb = P.render(vol, camB, tf, VMIN, VMAX, STEP)
+        torch.cuda.synchronize()
+        a, b = a.cpu().numpy(), b.cpu().numpy()
+        assert np.array_equal(b, a[rows, cols])
+        compare(b, nb.cpu().numpy(), oracle.render(cube2, camB, tf_np, VMIN, VMAX, STEP), TOL_F32)
+    finally:
+        vol.close()
