@@ -213,6 +213,20 @@ def run_reference(args, rank):
 # Our arm
 # ---------------------------------------------------------------------------
 
+def reduce_over_ranks(ms: float, samples: int, device) -> tuple:
+    """Whole-job figures across ranks: the slowest rank's time and the sum of
+    every rank's composited samples (each rank renders its own views)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return ms, samples
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    n = torch.tensor([samples], dtype=torch.int64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(n, op=dist.ReduceOp.SUM)
+    return float(t.item()), int(n.item())
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
     import paper_1211_4896_gb300 as P
@@ -306,12 +320,8 @@ def run_ours(args, rank, world, local_rank):
     ms = t_start.elapsed_time(t_end) / args.steps
     fwd_ms = statistics.mean(a.elapsed_time(b) for a, b in fwd_ev)
     bwd_ms = statistics.mean(a.elapsed_time(b) for a, b in bwd_ev)           # per view
-    ms_max = ms
-    if dist is not None:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_max = float(t.item())
-    value = samples_per_step * world / (ms_max * 1e-3) / 1e9
+    ms_max, samples_all = reduce_over_ranks(ms, samples_per_step, dev)
+    value = samples_all / (ms_max * 1e-3) / 1e9
 
     # ---- forward-only rates (batched graph and plain single-view form) -------------
     e0, e1 = ev(), ev()
@@ -363,8 +373,8 @@ def run_ours(args, rank, world, local_rank):
         e2e_step()
     b.record(stream)
     barrier()
-    e2e_ms = a.elapsed_time(b) / args.steps
-    e2e_value = samples_per_step * world / (e2e_ms * 1e-3) / 1e9
+    e2e_ms, _ = reduce_over_ranks(a.elapsed_time(b) / args.steps, samples_per_step, dev)
+    e2e_value = samples_all / (e2e_ms * 1e-3) / 1e9
 
     # ---- pixel error against the FP64 oracle on sampled rows (view 0) ------------------
     px = None

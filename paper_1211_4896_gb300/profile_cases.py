@@ -1,11 +1,13 @@
 """Small, self-contained cases for profiling one kernel launch with ncu
 (inputs larger than L2, a few GB on the device at most):
 
-  python -m paper_1211_4896_gb300.profile_cases fwd   # 512^3 f32, 4 orbit views at 960x540, step 1, ERT 0.99
-  python -m paper_1211_4896_gb300.profile_cases bwd   # 256^3 f32, 2 views at 512^2, step 0.5, table = ramp + 5% noise
+  python -m paper_1211_4896_gb300.profile_cases fwd    # 512^3 f32, 4 orbit views at 960x540, step 1, ERT 0.99
+  python -m paper_1211_4896_gb300.profile_cases fwd16  # the same views of the cube stored as f16
+  python -m paper_1211_4896_gb300.profile_cases bat    # the same 4 views in one batched call, f32
+  python -m paper_1211_4896_gb300.profile_cases bwd    # 256^3 f32, 2 views at 512^2, step 0.5, table = ramp + 5% noise
 
-Each case renders its views forward then backward on cuda:0, so capture the
-kernel of interest with -k and -c.
+The fwd/fwd16/bwd cases render each view forward then backward on cuda:0,
+so capture the kernel of interest with -k and -c.
 """
 import os
 import sys
@@ -15,13 +17,13 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 
-def case_fwd():
+def case_fwd(store="f32"):
     import torch
     import synth
     import paper_1211_4896_gb300 as P
     dev = torch.device("cuda")
     dims = (512, 512, 512)
-    vol = P.Volume(synth.hi_cube(dims, 250, 25, 9, device=dev), "f32")
+    vol = P.Volume(synth.hi_cube(dims, 250, 25, 9, device=dev), store)
     tf = torch.from_numpy(synth.tf_ramp(256)).to(dev)
     ns = None
     for c in synth.orbit_cameras(dims, 4, 40.0, 960, 540, start_deg=20.0):
@@ -29,6 +31,24 @@ def case_fwd():
         P.render_backward(vol, c, tf, -3.0, 50.0, 1.0, img, ns, torch.randn_like(img), 0.99)
     torch.cuda.synchronize()
     print("ok", int(ns.sum()))
+
+
+def case_bat():
+    import torch
+    import synth
+    import paper_1211_4896_gb300 as P
+    dev = torch.device("cuda")
+    dims = (512, 512, 512)
+    vol = P.Volume(synth.hi_cube(dims, 250, 25, 9, device=dev), "f32")
+    tf = torch.from_numpy(synth.tf_ramp(256)).to(dev)
+    jobs = [dict(vol=vol, cam=c, tf=tf, vmin=-3.0, vmax=50.0, step=1.0, ert=0.99,
+                 out=torch.empty((540, 960, 4), device=dev),
+                 nsamples=torch.empty((540, 960), device=dev, dtype=torch.int32))
+            for c in synth.orbit_cameras(dims, 4, 40.0, 960, 540, start_deg=20.0)]
+    for _ in range(2):
+        P.render_batched(jobs)
+    torch.cuda.synchronize()
+    print("ok", sum(int(j["nsamples"].sum()) for j in jobs))
 
 
 def case_bwd():
@@ -53,4 +73,5 @@ def case_bwd():
 if __name__ == "__main__":
     from paper_1211_4896_gb300 import build
     build.build()
-    {"fwd": case_fwd, "bwd": case_bwd}[sys.argv[1] if len(sys.argv) > 1 else "fwd"]()
+    {"fwd": case_fwd, "fwd16": lambda: case_fwd("f16"), "bat": case_bat,
+     "bwd": case_bwd}[sys.argv[1] if len(sys.argv) > 1 else "fwd"]()
