@@ -196,20 +196,21 @@ __global__ void __launch_bounds__(kBwdThreads) bwd_kernel(VolDev v, CamDev c, Pa
             }
             const float val = interp_corners(cell, f);
             TfPos tp;
-            const float4 e = tf_lookup_l1(p, val, tp);
+            float4 de;
+            const float4 e = tf_lookup_l1(p, val, tp, de);
             const float a = e.w;
             const float cg = e.x * g.x + e.y * g.y + e.z * g.z;
             const float aT = a * T;
             R = fmaf(-aT, cg, R);                       // R_k = R_{k-1} - T_k a_k (c_k.g)
             const float om = 1.0f - a;
-            const float da = T * cg - (om > 0.0f ? R / om : 0.0f);
+            // om is in (0, 1] where it divides: the fast reciprocal-based division is
+            // within 2 ulp there
+            const float da = T * cg - (om > 0.0f ? __fdividef(R, om) : 0.0f);
             if (aT != 0.0f || da != 0.0f) {
                 const float4 dr = make_float4(aT * g.x, aT * g.y, aT * g.z, da);
                 bins.add(row, tp.i0, 1.0f - tp.w, tp.w, dr);
                 if (grad_vox && tp.interior) {
-                    const float4 e0 = __ldg(p.tf + tp.i0), e1 = __ldg(p.tf + tp.i0 + 1);
-                    const float dv = (dr.x * (e1.x - e0.x) + dr.y * (e1.y - e0.y) + dr.z * (e1.z - e0.z) +
-                                      dr.w * (e1.w - e0.w)) * vscale;
+                    const float dv = (dr.x * de.x + dr.y * de.y + dr.z * de.z + dr.w * de.w) * vscale;
                     if (dv != 0.0f)
                         cells.add(grad_vox + ((long long)cell.z0 * nyx + (long long)cell.y0 * v.nx + cell.x0),
                                   cell.fx, cell.fy, cell.fz, dv, v.nx, nyx);

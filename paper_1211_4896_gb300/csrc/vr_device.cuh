@@ -321,6 +321,22 @@ __device__ __forceinline__ void load_tf_shared(float4 *tfs, const float4 *tf, in
 // Table lookup through the read-only L1 path.  The lanes of a warp mostly hit
 // a handful of neighbouring entries (one or two 128-byte lines), which costs
 // fewer L1 wavefronts than a 128-bit shared-memory load (4 wavefronts).
+// The same lookup, also returning the slope of the blend between the two
+// entries (e1 - e0) for the adjoint.
+__device__ __forceinline__ float4 tf_lookup_l1(const ParamDev &p, float v, TfPos &pos, float4 &de)
+{
+    float u = fmaf(v, p.su, p.ou);
+    pos.interior = (u > 0.0f) && (u < p.km1);
+    u = fminf(fmaxf(u, 0.0f), p.km1);
+    const int i0 = min(__float2int_rd(u), p.K - 2);
+    const float w = u - (float)i0;
+    pos.i0 = i0;
+    pos.w = w;
+    const float4 e0 = __ldg(p.tf + i0), e1 = __ldg(p.tf + i0 + 1);
+    de = make_float4(e1.x - e0.x, e1.y - e0.y, e1.z - e0.z, e1.w - e0.w);
+    return make_float4(fmaf(w, de.x, e0.x), fmaf(w, de.y, e0.y), fmaf(w, de.z, e0.z), fmaf(w, de.w, e0.w));
+}
+
 __device__ __forceinline__ float4 tf_lookup_l1(const ParamDev &p, float v, TfPos &pos)
 {
     float u = fmaf(v, p.su, p.ou);               // (v - vmin) (K-1)/(vmax - vmin)
