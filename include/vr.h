@@ -111,7 +111,8 @@ typedef struct {
     int64_t dense_bytes;      /* device bytes of the dense row-padded copy (0 until the first
                                  staged call) */
     int64_t copy_bytes;       /* device bytes of the brick copies (see vr_volume_create) */
-    int copies;               /* which copies exist: bit 0 x-, bit 1 y-, bit 2 z-fastest */
+    int copies;               /* which copies exist: bit 1 / 2 plain y- / z-fastest; bit 3 / 4 / 5
+                                 paired x- / y- / z-fastest (16-bit storage) */
 } vr_volume_info_t;
 
 /* ------------------------------------------------------------------------
@@ -131,16 +132,17 @@ typedef struct {
  * into shared memory.  The first software-filter call (render, backward or
  * batched) with a view whose image rows run closest to an axis adds a copy of
  * the bricks with that axis fastest inside each brick, so that the rays of
- * one warp read neighbouring elements: for float storage a plain copy for the
- * y or z axis (the bricks serve the x axis), as many bytes as the bricks; for
- * 16-bit storage a paired copy for any axis, each element holding its own
- * value and the next one along that axis so that four loads fetch a cell's
- * eight corners (twice the bricks' bytes).  A copy is built only outside
- * stream capture, while the device keeps as much memory again free (else the
- * bricks themselves serve), synchronising cuda_stream once; environment
- * variable VR_BRICK_COPIES=0 turns copies off.  Results do not depend on
- * which copy a view reads.  vr_volume_update refreshes every copy;
- * vr_volume_info reports them.  The
+ * one warp read neighbouring elements: a plain copy for the y or z axis (the
+ * bricks serve the x axis), as many bytes as the bricks.  For 16-bit storage
+ * and rays closer than VR_PAIRED_MAX_PITCH voxels (environment, default 3)
+ * at the volume centre, a paired copy for any axis instead, each element
+ * holding its own value and the next one along that axis so that four loads
+ * fetch a cell's eight corners (twice the bricks' bytes).  A copy is built
+ * only outside stream capture, while the device keeps an eighth of its memory
+ * free besides it (else the bricks themselves serve), synchronising
+ * cuda_stream once; environment variable VR_BRICK_COPIES=0 turns copies off.
+ * Results do not depend on which copy a view reads.  vr_volume_update
+ * refreshes every copy; vr_volume_info reports them.  The
  * caller keeps dev_cube; the call synchronises `cuda_stream` before returning
  * the handle in *out.  Errors: INVALID_ARG, OOM, CUDA.
  * ---------------------------------------------------------------------- */

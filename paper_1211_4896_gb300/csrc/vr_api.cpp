@@ -212,31 +212,62 @@ VolDev vol_dev(const vr_volume *vol)
 VolDev vol_dev_copy(const vr_volume *vol, int copy)
 {
     VolDev v = vol_dev(vol);
-    if (copy >= 0 && copy < 3 && vol->copies[copy]) {
+    if (copy >= 1 && copy < kCopyIds && vol->copies[copy]) {
         v.data = vol->copies[copy];
-        v.order = copy;
-        v.paired = vol->store_dtype != VR_F32;
+        v.order = copy_order(copy);
+        v.paired = copy_paired(copy);
     }
     return v;
 }
 
-// Brick copy for a camera: the copy whose fastest axis is the one along
-// which the image's horizontal direction (in voxel units) is longest, so that
-// a warp's row of eight rays reads neighbouring elements (and, paired, every
-// load brings two corners).  A float view along x reads the bricks
-// themselves.  The copy is built on first use when `may_build`, the stream is
-// not being captured and the device keeps as much memory again free; it is
-// complete before the call returns, so any stream may read it.  Otherwise (or
-// with VR_BRICK_COPIES=0 in the environment) the bricks themselves serve (-1).
+// Distance between neighbouring rays at the volume centre, in voxels along
+// the image's horizontal direction r (world pitch of one pixel there,
+// divided by the spacing along r).
+static double ray_pitch_voxels(const vr_volume *vol, const vr_camera *cam, const double r[3])
+{
+    double pitch = 0.0;
+    if (cam->kind == VR_CAMERA_ORTHO) {
+        pitch = cam->ortho_height / cam->height;
+    } else {
+        double f[3] = {cam->forward[0], cam->forward[1], cam->forward[2]};
+        const double fl = std::sqrt(dot3(f, f));
+        double d = 0.0;
+        for (int a = 0; a < 3; ++a)
+            d += (vol->origin[a] + 0.5 * (double)(vol->dims[a] - 1) * vol->spacing[a] - cam->eye[a]) * f[a] / fl;
+        pitch = 2.0 * std::fabs(d) * std::tan(cam->fov_y_deg * M_PI / 360.0) / cam->height;
+    }
+    double q = 0.0;
+    for (int a = 0; a < 3; ++a) q += (r[a] / vol->spacing[a]) * (r[a] / vol->spacing[a]);
+    return pitch * std::sqrt(q);
+}
+
+// Brick copy for a camera.  Its fastest axis is the one along which the
+// image's horizontal direction (in voxel units) is longest, so that a warp's
+// row of eight rays reads neighbouring elements; a view along x reads the
+// bricks themselves.  16-bit volumes take paired copies (two corners per
+// load) while neighbouring rays are closer than VR_PAIRED_MAX_PITCH voxels
+// (default 3) at the volume centre, where a warp's gathers share cache lines
+// and the number of loads bounds the march; sparser rays each touch their own
+// sectors in DRAM, so the plain copy (half the bytes of a paired one) serves.
+// A copy is built on first use when `may_build`, the stream is not being
+// captured and the device keeps an eighth of its memory free besides it; it
+// is complete before the call returns, so any stream may read it.  Otherwise
+// (or with VR_BRICK_COPIES=0 in the environment) the bricks serve (-1).
 int preferred_copy(vr_volume *vol, const vr_camera *cam, bool may_build, cudaStream_t s)
 {
     static const bool enabled = [] {
         const char *e = std::getenv("VR_BRICK_COPIES");
         return !(e && e[0] == '0');
     }();
+    static const double max_pitch = [] {
+        const char *e = std::getenv("VR_PAIRED_MAX_PITCH");
+        return e ? std::atof(e) : 3.0;
+    }();
     if (!enabled) return -1;
     double f[3] = {cam->forward[0], cam->forward[1], cam->forward[2]}, r[3];
     cross3(f, cam->up, r);
+    const double rl = std::sqrt(dot3(r, r));
+    for (double &x : r) x /= rl;
     double best = -1.0;
     int axis = 0;
     for (int a = 0; a < 3; ++a) {
@@ -246,17 +277,19 @@ int preferred_copy(vr_volume *vol, const vr_camera *cam, bool may_build, cudaStr
             axis = a;
         }
     }
-    if (vol->store_dtype == VR_F32 && axis == 0) return -1;
-    if (vol->copies[axis]) return axis;
+    const bool paired = vol->store_dtype != VR_F32 && ray_pitch_voxels(vol, cam, r) < max_pitch;
+    const int copy = paired ? 3 + axis : axis;
+    if (copy == 0) return -1;
+    if (vol->copies[copy]) return copy;
     if (!may_build) return -1;
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
         cudaGetLastError();
         return -1;
     }
-    const size_t bytes = copy_bytes(vol);
+    const size_t bytes = copy_bytes(vol, copy);
     size_t free_b = 0, total_b = 0;
-    if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess || free_b < 2 * bytes) {
+    if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess || free_b < bytes + total_b / 8) {
         cudaGetLastError();
         return -1;
     }
@@ -265,14 +298,14 @@ int preferred_copy(vr_volume *vol, const vr_camera *cam, bool may_build, cudaStr
         cudaGetLastError();
         return -1;
     }
-    vol->copies[axis] = p;
-    if (launch_copy(vol, axis, s) != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess) {
+    vol->copies[copy] = p;
+    if (launch_copy(vol, copy, s) != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess) {
         cudaGetLastError();
         cudaFree(p);
-        vol->copies[axis] = nullptr;
+        vol->copies[copy] = nullptr;
         return -1;
     }
-    return axis;
+    return copy;
 }
 
 // The last slot of the ring is the volume's device status word.
@@ -442,8 +475,8 @@ vr_status vr_volume_update(vr_volume_t vol, const void *dev_cube, vr_dtype src_d
         vol->tex_array = nullptr;
     }
     cudaError_t e = launch_brick(dev_cube, src_dtype, vol, s);
-    for (int o = 0; o < 3 && e == cudaSuccess; ++o)
-        if (vol->copies[o]) e = launch_copy(vol, o, s);
+    for (int c = 1; c < kCopyIds && e == cudaSuccess; ++c)
+        if (vol->copies[c]) e = launch_copy(vol, c, s);
     if (e == cudaSuccess && vol->dense) e = launch_densify(dev_cube, src_dtype, vol, s);
     if (e != cudaSuccess) return cuda_fail(e, "vr_volume_update");
     return VR_OK;
@@ -474,10 +507,10 @@ vr_status vr_volume_info(vr_volume_t vol, vr_volume_info_t *out)
     out->dense_bytes = (int64_t)vol->dense_bytes;
     out->copy_bytes = 0;
     out->copies = 0;
-    for (int o = 0; o < 3; ++o)
-        if (vol->copies[o]) {
-            out->copy_bytes += (int64_t)copy_bytes(vol);
-            out->copies |= 1 << o;
+    for (int c = 1; c < kCopyIds; ++c)
+        if (vol->copies[c]) {
+            out->copy_bytes += (int64_t)copy_bytes(vol, c);
+            out->copies |= 1 << c;
         }
     return VR_OK;
 }

@@ -84,7 +84,7 @@ static BatchFn pick_kernel(const VolDev &v, vr_dtype dt)
         (BatchFn) nullptr);
 }
 
-constexpr int kGroups = 4;       // brick copies a batch may read: the bricks + 3 paired copies
+constexpr int kGroups = kCopyIds + 1;    // brick copies a batch may read: the bricks + every copy id
 
 // The jobs reading one brick copy: descriptors [first, first + njobs) of the
 // grouped table, tiles numbered from 0 within the group.

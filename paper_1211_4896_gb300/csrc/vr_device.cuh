@@ -45,8 +45,8 @@ template <typename S> struct is_pair<Pair<S>> { static constexpr bool value = tr
 // ---------------------------------------------------------------------------
 // Brick layouts a kernel can read (host-side dispatch).  Every volume has its
 // x-fastest bricks (element type = storage type, order 0).  Copies for views
-// along other axes: float volumes keep plain copies in order 1 or 2 (element
-// type float); 16-bit volumes keep paired copies in any order (element type
+// along other axes: plain copies in order 1 or 2 (element type = storage
+// type); for 16-bit storage also paired copies in any order (element type
 // Pair<S>, as many bytes as float bricks).
 // ---------------------------------------------------------------------------
 template <typename T, int LOG2B_, int L_> struct Layout {
@@ -60,10 +60,9 @@ template <typename S, int LOG2B, typename F, typename R>
 R visit_layout_b(const VolDev &v, F &&f, R none)
 {
     if (!v.paired && v.order == 0) return f(Layout<S, LOG2B, 0>{});
-    if constexpr (std::is_same<S, float>::value) {
-        if (!v.paired && v.order == 1) return f(Layout<S, LOG2B, 1>{});
-        if (!v.paired && v.order == 2) return f(Layout<S, LOG2B, 2>{});
-    } else {
+    if (!v.paired && v.order == 1) return f(Layout<S, LOG2B, 1>{});
+    if (!v.paired && v.order == 2) return f(Layout<S, LOG2B, 2>{});
+    if constexpr (!std::is_same<S, float>::value) {
         if (v.paired && v.order == 0) return f(Layout<Pair<S>, LOG2B, 0>{});
         if (v.paired && v.order == 1) return f(Layout<Pair<S>, LOG2B, 1>{});
         if (v.paired && v.order == 2) return f(Layout<Pair<S>, LOG2B, 2>{});

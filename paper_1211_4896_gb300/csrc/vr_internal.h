@@ -79,10 +79,11 @@ struct vr_volume {
     unsigned *counters = nullptr;      // last slot: device status word (timeouts)
     int counter_slots = 0;
     int next_counter = 0;
-    // copies of the bricks in element order 0 (x), 1 (y), 2 (z fastest), built
-    // on the first software-filter call that prefers them: plain float copies
-    // in order 1 or 2 (bytes each), paired 16-bit copies in any order (2 * bytes)
-    void *copies[3] = {nullptr, nullptr, nullptr};
+    // copies of the bricks, built on the first software-filter call that
+    // prefers them, indexed by copy id: 1, 2 plain copies with y / z fastest
+    // (bytes each); 3, 4, 5 paired 16-bit copies with x / y / z fastest
+    // (2 * bytes each); [0] unused (the bricks themselves are copy -1)
+    void *copies[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
     // backward scratch: one FP32 row of K RGBA gradient bins per warp
     float *wtab = nullptr;
     size_t wtab_cap = 0;         // floats
@@ -115,12 +116,15 @@ cudaError_t launch_forward(const VolDev &v, vr_dtype dt, const CamDev &c, const 
                            uint32_t *nsamples, unsigned *counter, cudaStream_t s);
 cudaError_t launch_forward_texture(const vr_volume *vol, const CamDev &c, const ParamDev &p, float4 *out,
                                    uint32_t *nsamples, unsigned *counter, cudaStream_t s);
-// Brick copy a software-filter view reads: -1 the bricks themselves, o in
-// {0, 1, 2} the copy in element order o (see vr_volume.copies).
+// Brick copy a software-filter view reads: -1 the bricks themselves, else a
+// copy id of vr_volume.copies (element order copy_order, paired if >= 3).
+constexpr int kCopyIds = 6;
+inline bool copy_paired(int copy) { return copy >= 3; }
+inline int copy_order(int copy) { return copy >= 3 ? copy - 3 : copy; }
 VolDev vol_dev_copy(const vr_volume *vol, int copy);
 int preferred_copy(vr_volume *vol, const vr_camera *cam, bool may_build, cudaStream_t s);
-size_t copy_bytes(const vr_volume *vol);
-cudaError_t launch_copy(vr_volume *vol, int order, cudaStream_t s);
+size_t copy_bytes(const vr_volume *vol, int copy);
+cudaError_t launch_copy(vr_volume *vol, int copy, cudaStream_t s);
 cudaError_t launch_backward(const VolDev &v, vr_volume *vol, const CamDev &c, const ParamDev &p, const float4 *rgba,
                             const uint32_t *nsamples, const float4 *grad_rgba, double *grad_tf, float *grad_vox,
                             long long nvox, bool accumulate, unsigned *counter, cudaStream_t s);

@@ -181,8 +181,8 @@ vr_status build_texture(vr_volume *vol, cudaStream_t s)
 // ---------------------------------------------------------------------------
 // Brick copies in element order L (see BrickOrder), built brick by brick from
 // the x-fastest bricks, one CTA per brick; reads are coalesced, writes follow
-// the new order.  Float volumes get plain copies in order 1 or 2.  16-bit
-// volumes get paired copies in any order: element (lx, ly, lz) holds its own
+// the new order.  Plain copies (any storage type) in order 1 or 2; paired
+// copies (16-bit storage) in any order: element (lx, ly, lz) holds its own
 // value and the next one along the order's fastest axis, so that four loads
 // fetch a cell's eight corners.
 // ---------------------------------------------------------------------------
@@ -225,50 +225,53 @@ __global__ void __launch_bounds__(256) pair_kernel(const D *__restrict__ src, ty
     }
 }
 
-template <typename D, int LOG2B, int L>
-static void copy_t(vr_volume *vol, cudaStream_t s)
+template <typename D, int LOG2B, int L, bool PAIRED>
+static void copy_t(vr_volume *vol, void *dst, cudaStream_t s)
 {
     const unsigned nbricks = (unsigned)(vol->nb[0] * vol->nb[1] * vol->nb[2]);
     const D *src = static_cast<const D *>(vol->bricks);
-    if constexpr (std::is_same<D, float>::value) {
-        if constexpr (L != 0)
-            reorder_kernel<D, LOG2B, L><<<nbricks, 256, 0, s>>>(src, static_cast<D *>(vol->copies[L]), vol->stride);
-    } else {
-        pair_kernel<D, LOG2B, L><<<nbricks, 256, 0, s>>>(
-            src, static_cast<typename Pair<D>::V *>(vol->copies[L]), vol->stride);
+    if constexpr (PAIRED) {
+        if constexpr (!std::is_same<D, float>::value)
+            pair_kernel<D, LOG2B, L><<<nbricks, 256, 0, s>>>(src, static_cast<typename Pair<D>::V *>(dst),
+                                                             vol->stride);
+    } else if constexpr (L != 0) {
+        reorder_kernel<D, LOG2B, L><<<nbricks, 256, 0, s>>>(src, static_cast<D *>(dst), vol->stride);
     }
 }
 
 template <typename D, int LOG2B>
-static void copy_b(vr_volume *vol, int order, cudaStream_t s)
+static void copy_b(vr_volume *vol, int copy, cudaStream_t s)
 {
-    switch (order) {
-    case 0: copy_t<D, LOG2B, 0>(vol, s); break;
-    case 1: copy_t<D, LOG2B, 1>(vol, s); break;
-    default: copy_t<D, LOG2B, 2>(vol, s); break;
+    void *dst = vol->copies[copy];
+    switch (copy) {
+    case 1: copy_t<D, LOG2B, 1, false>(vol, dst, s); break;
+    case 2: copy_t<D, LOG2B, 2, false>(vol, dst, s); break;
+    case 3: copy_t<D, LOG2B, 0, true>(vol, dst, s); break;
+    case 4: copy_t<D, LOG2B, 1, true>(vol, dst, s); break;
+    default: copy_t<D, LOG2B, 2, true>(vol, dst, s); break;
     }
 }
 
 template <typename D>
-static void copy_d(vr_volume *vol, int order, cudaStream_t s)
+static void copy_d(vr_volume *vol, int copy, cudaStream_t s)
 {
     switch (vol->log2b) {
-    case 4: copy_b<D, 4>(vol, order, s); break;
-    case 5: copy_b<D, 5>(vol, order, s); break;
-    default: copy_b<D, 6>(vol, order, s); break;
+    case 4: copy_b<D, 4>(vol, copy, s); break;
+    case 5: copy_b<D, 5>(vol, copy, s); break;
+    default: copy_b<D, 6>(vol, copy, s); break;
     }
 }
 
-size_t copy_bytes(const vr_volume *vol) { return vol->store_dtype == VR_F32 ? vol->bytes : 2 * vol->bytes; }
+size_t copy_bytes(const vr_volume *vol, int copy) { return copy_paired(copy) ? 2 * vol->bytes : vol->bytes; }
 
-cudaError_t launch_copy(vr_volume *vol, int order, cudaStream_t s)
+cudaError_t launch_copy(vr_volume *vol, int copy, cudaStream_t s)
 {
-    if (order < 0 || order > 2 || !vol->copies[order]) return cudaErrorInvalidValue;
-    if (vol->store_dtype == VR_F32 && order == 0) return cudaErrorInvalidValue;    // the bricks themselves
+    if (copy < 1 || copy >= kCopyIds || !vol->copies[copy]) return cudaErrorInvalidValue;
+    if (vol->store_dtype == VR_F32 && copy_paired(copy)) return cudaErrorInvalidValue;   // no float pairs
     switch (vol->store_dtype) {
-    case VR_F32: copy_d<float>(vol, order, s); break;
-    case VR_F16: copy_d<__half>(vol, order, s); break;
-    case VR_BF16: copy_d<__nv_bfloat16>(vol, order, s); break;
+    case VR_F32: copy_d<float>(vol, copy, s); break;
+    case VR_F16: copy_d<__half>(vol, copy, s); break;
+    case VR_BF16: copy_d<__nv_bfloat16>(vol, copy, s); break;
     }
     return cudaGetLastError();
 }

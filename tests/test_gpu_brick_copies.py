@@ -35,12 +35,12 @@ def P(torch):
     return P
 
 
-def _cam(forward, up, kind):
+def _cam(forward, up, kind, size=W):
     c = [0.5 * (d - 1) for d in DIMS]
     eye = [c[a] - 180.0 * forward[a] for a in range(3)]
     if kind == "ortho":
-        return synth.camera_ortho(eye, forward, up, 50.0, W, W)
-    return synth.camera_persp(eye, forward, up, 20.0, W, W)
+        return synth.camera_ortho(eye, forward, up, 50.0, size, size)
+    return synth.camera_persp(eye, forward, up, 20.0, size, size)
 
 
 # (camera reading x-fastest bricks, its roll reading order `order`, map from
@@ -90,7 +90,9 @@ def test_rolled_view_reads_a_copy_bit_identically(P, torch, scene, kind, pair, s
     (fa, ua), (fb, ub), order, (rows, cols) = PAIRS[pair]
     vol = _volume(P, torch, cube, store)
     tf = torch.from_numpy(tf_np).cuda()
-    x_copy = 0 if store == "f32" else 0b1          # float views along x read the bricks themselves
+    # copy ids: 1, 2 plain y / z; 3, 4, 5 paired x / y / z (16-bit, dense rays: ~1 voxel per pixel here)
+    x_copy = 0 if store == "f32" else 1 << 3
+    b_copy = 1 << order if store == "f32" else 1 << (3 + order)
     try:
         assert _copies(P, vol) == 0
         camA, camB = _cam(fa, ua, kind), _cam(fb, ub, kind)
@@ -99,7 +101,7 @@ def test_rolled_view_reads_a_copy_bit_identically(P, torch, scene, kind, pair, s
         b, nb = P.render(vol, camB, tf, VMIN, VMAX, STEP)
         torch.cuda.synchronize()
         info = P._lib.vr_volume_info(vol.handle)
-        assert info["copies"] == x_copy | 1 << order
+        assert info["copies"] == x_copy | b_copy
         per_copy = info["bytes"] * (1 if store == "f32" else 2)
         assert info["copy_bytes"] == per_copy * bin(info["copies"]).count("1")
         a, na, b, nb = a.cpu().numpy(), na.cpu().numpy(), b.cpu().numpy(), nb.cpu().numpy()
@@ -174,11 +176,47 @@ def test_half_paired_copies_match_bricks(P, torch, scene, store):
             img, ns = P.render(vol, c, tf, VMIN, VMAX, STEP)
             torch.cuda.synchronize()
             assert torch.equal(img, img0) and torch.equal(ns, ns0)
-        assert _copies(P, vol) == 0b111
+        assert _copies(P, vol) == 0b111000
         (fa, ua), (fb, ub), order, (rows, cols) = PAIRS[0]
         a = plain[0][0].cpu().numpy()
         b = plain[1][0].cpu().numpy()
         assert np.array_equal(b, a[rows, cols])
+    finally:
+        vol.close()
+
+
+@pytest.mark.parametrize("store", ["f16", "bf16"])
+def test_half_sparse_rays_read_plain_copies(P, torch, scene, store):
+    """16-bit storage with rays about 3-4 voxels apart (16x16 image of the
+    40x36x44 cube): the views read plain copies (half the bytes of paired
+    ones), bit for bit the bricks' result, and a rolled view matches."""
+    cube, tf_np = scene
+    vol = _volume(P, torch, cube, store)
+    tf = torch.from_numpy(tf_np).cuda()
+    n = 16
+    i, j = np.arange(n)[None, :], np.arange(n)[:, None]
+    try:
+        cams = [_cam(*PAIRS[0][0], "persp", n), _cam(*PAIRS[0][1], "persp", n), _cam(*PAIRS[1][1], "ortho", n)]
+        plain = []
+        for c in cams:
+            out = torch.full((n, n, 4), -1.0, device="cuda")
+            ns = torch.full((n, n), -1, device="cuda", dtype=torch.int32)
+            from paper_1211_4896_gb300 import _lib as L
+            job = L.vr_job(vol.handle, L.make_camera(c),
+                           L.make_params(tf.data_ptr(), tf.shape[0], VMIN, VMAX, STEP, 2.0), out.data_ptr(),
+                           ns.data_ptr())
+            L.vr_render_batched_noalloc([job], 8, 4, int(torch.cuda.current_stream().cuda_stream))
+            torch.cuda.synchronize()
+            plain.append((out, ns))
+        for c, (img0, ns0) in zip(cams, plain):
+            img, ns = P.render(vol, c, tf, VMIN, VMAX, STEP)
+            torch.cuda.synchronize()
+            assert torch.equal(img, img0) and torch.equal(ns, ns0)
+        assert _copies(P, vol) == 0b110                 # plain y and z copies, no paired ones
+        a = plain[0][0].cpu().numpy()
+        b, _ = P.render(vol, cams[1], tf, VMIN, VMAX, STEP)
+        assert np.array_equal(b.cpu().numpy(), a[n - 1 - i, j])
+        assert a[..., 3].max() > 0.1
     finally:
         vol.close()
 
