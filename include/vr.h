@@ -217,8 +217,10 @@ typedef struct {
 } vr_job;
 
 typedef struct {
-    int use_graph;            /* 1: capture the launch in a CUDA graph on first use and replay it
-                                 while the job list is unchanged (same pointers and parameters) */
+    int use_graph;            /* 1: build a CUDA graph of the call on first use (counter reset, then
+                                 one kernel node per brick layout, the layouts running concurrently)
+                                 and replay it while the job list is unchanged (same pointers and
+                                 parameters); 0: launch the layouts one after another */
     int tile_w, tile_h;       /* ray tile of one warp: tile_w * tile_h == 32; 0 = 8 x 4 */
     int ctas_per_sm;          /* persistent CTAs per SM; 0 = occupancy limit */
 } vr_batch_opts;
@@ -226,8 +228,10 @@ typedef struct {
 /* All volumes of one batch must share store dtype and brick size
  * (UNSUPPORTED otherwise).  A job list is keyed by its bytes: the first call
  * with a new list uploads its descriptors (synchronising cuda_stream); with
- * use_graph the first call also captures the launch.  Later calls with the
- * same list only launch.  Errors: INVALID_ARG, UNSUPPORTED, OOM, CUDA. */
+ * use_graph the first call also builds the graph.  Within a layout the jobs
+ * with the most work (pixels x samples along the box diagonal) are handed out
+ * first.  Later calls with the same list only launch.  Errors: INVALID_ARG,
+ * UNSUPPORTED, OOM, CUDA. */
 vr_status vr_render_batched(const vr_job *jobs, int n, const vr_batch_opts *opts, void *cuda_stream);
 
 /* Times candidate tile shapes and CTA counts for this job list (it renders

@@ -1,12 +1,15 @@
-// vr_batched.cu -- many (volume, camera, transfer function, image) jobs in ONE
-// persistent launch (an extension: the paper's future-work item on many
-// smaller cubes).  Warps pull ray tiles of all jobs from one global atomic
-// queue; a tile index maps to its job by binary search over the per-job tile
-// prefix.  The launch (counter reset + kernel) is captured once in a CUDA
-// graph and replayed while the job list is unchanged.
+// vr_batched.cu -- many (volume, camera, transfer function, image) jobs in one
+// persistent launch per brick layout (an extension: the paper's future-work
+// item on many smaller cubes).  Warps pull ray tiles of all jobs of a layout
+// from one global atomic queue; a tile index maps to its job by binary search
+// over the per-job tile prefix.  The launches (counter reset + one kernel per
+// layout, independent of one another) form a CUDA graph built once and
+// replayed while the job list is unchanged.
 #include "vr_device.cuh"
 
+#include <algorithm>
 #include <chrono>
+#include <cmath>
 #include <cstring>
 #include <map>
 #include <mutex>
@@ -121,10 +124,10 @@ static int log2_of(int x)
 // Builds the descriptors of all jobs into hj[0, n), grouped by the brick copy
 // each view reads (group g = copy + 1: the bricks first, then the paired
 // copies in order 0, 1, 2; call order within a group), and fills seg[] with
-// each group's offset, tile count and kernel.  group_of is host scratch of n
-// ints.  may_build allows building a missing copy.
+// each group's offset, tile count and kernel.  group_of, order and cost are
+// host scratch of n entries.  may_build allows building a missing copy.
 static vr_status prepare_jobs(const vr_job *jobs, int n, int tile_w, bool may_build, cudaStream_t s, JobDev *hj,
-                              int *group_of, Segment seg[kGroups], const char *who)
+                              int *group_of, int *order, double *cost, Segment seg[kGroups], const char *who)
 {
     const int tile_h = 32 / tile_w;
     vr_dtype dt = VR_F32;
@@ -150,7 +153,26 @@ static vr_status prepare_jobs(const vr_job *jobs, int n, int tile_w, bool may_bu
     }
     int fill[kGroups];
     for (int g = 0, first = 0; g < kGroups; first += seg[g].njobs, ++g) fill[g] = seg[g].first = first;
+    // Within a group the most expensive jobs come first (pixels x samples along
+    // the box diagonal), so that the last tiles handed out are cheap ones and
+    // the launch ends with a short tail; ties keep the call order.
     for (int q = 0; q < n; ++q) {
+        const vr_job &J = jobs[q];
+        double d2 = 0.0;
+        for (int a = 0; a < 3; ++a) {
+            const double ext = (double)(J.vol->dims[a] - 1) * J.vol->spacing[a];
+            d2 += ext * ext;
+        }
+        cost[q] = (double)J.cam.width * (double)J.cam.height * std::sqrt(d2) / (double)J.params.step;
+        order[q] = q;
+    }
+    std::sort(order, order + n, [&](int a, int b) {
+        if (group_of[a] != group_of[b]) return group_of[a] < group_of[b];
+        if (cost[a] != cost[b]) return cost[a] > cost[b];
+        return a < b;
+    });
+    for (int k = 0; k < n; ++k) {
+        const int q = order[k];
         const vr_job &J = jobs[q];
         Segment &g = seg[group_of[q]];
         JobDev &d = hj[fill[group_of[q]]++];
@@ -191,6 +213,44 @@ static void size_grids(Segment seg[kGroups], int ctas)
         const unsigned useful = (g.total_tiles + kBatThreads / 32 - 1) / (kBatThreads / 32);
         g.grid = grid < useful ? grid : (useful ? useful : 1);
     }
+}
+
+// Graph of one batched call: the counter reset, then one kernel node per
+// non-empty group, the groups independent of one another so that the tail of
+// one group's launch overlaps the work of the others.
+static cudaError_t build_graph(BatchPlan *plan)
+{
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaGraphCreate(&graph, 0);
+    if (e != cudaSuccess) return e;
+    cudaGraphNode_t reset = nullptr;
+    cudaMemsetParams mp = {};
+    mp.dst = plan->counter;
+    mp.value = 0;
+    mp.elementSize = sizeof(unsigned);
+    mp.width = kGroups;
+    mp.height = 1;
+    e = cudaGraphAddMemsetNode(&reset, graph, nullptr, 0, &mp);
+    for (int g = 0; g < kGroups && e == cudaSuccess; ++g) {
+        const Segment &sg = plan->seg[g];
+        if (!sg.njobs) continue;
+        const JobDev *djobs = plan->djobs + sg.first;
+        int njobs = sg.njobs, log2_tw = plan->log2_tw;
+        unsigned total = sg.total_tiles;
+        unsigned *ctr = plan->counter + g;
+        void *args[] = {&djobs, &njobs, &total, &ctr, &log2_tw};
+        cudaKernelNodeParams kp = {};
+        kp.func = (void *)sg.fn;
+        kp.gridDim = dim3(sg.grid);
+        kp.blockDim = dim3(kBatThreads);
+        kp.sharedMemBytes = 0;
+        kp.kernelParams = args;
+        cudaGraphNode_t node = nullptr;
+        e = cudaGraphAddKernelNode(&node, graph, &reset, 1, &kp);
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&plan->exec, graph, 0);
+    cudaGraphDestroy(graph);
+    return e;
 }
 
 // Counter reset and one launch per non-empty group, in order on stream s.
@@ -281,9 +341,11 @@ extern "C" vr_status vr_render_batched(const vr_job *jobs, int n, const vr_batch
     if (it != g_plans.end()) plan = it->second;
     if (!plan) {
         std::vector<JobDev> hj((size_t)n);
-        std::vector<int> group_of((size_t)n);
+        std::vector<int> group_of((size_t)n), order((size_t)n);
+        std::vector<double> cost((size_t)n);
         Segment seg[kGroups];
-        st = prepare_jobs(jobs, n, tile_w, true, s, hj.data(), group_of.data(), seg, "vr_render_batched");
+        st = prepare_jobs(jobs, n, tile_w, true, s, hj.data(), group_of.data(), order.data(), cost.data(), seg,
+                          "vr_render_batched");
         if (st != VR_OK) return st;
         size_grids(seg, ctas);
         plan = new BatchPlan();
@@ -311,22 +373,10 @@ extern "C" vr_status vr_render_batched(const vr_job *jobs, int n, const vr_batch
     cudaError_t e;
     if (use_graph) {
         if (!plan->exec) {
-            cudaStream_t cap;
-            e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
-            if (e != cudaSuccess) return cuda_fail(e, "cudaStreamCreate");
-            cudaGraph_t graph = nullptr;
-            e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
-            if (e == cudaSuccess) {
-                const cudaError_t le = launch_segments(plan->seg, plan->djobs, plan->counter, plan->log2_tw, cap);
-                e = cudaStreamEndCapture(cap, &graph);
-                if (e == cudaSuccess) e = le;
-            }
-            if (e == cudaSuccess) e = cudaGraphInstantiate(&plan->exec, graph, 0);
-            if (graph) cudaGraphDestroy(graph);
-            cudaStreamDestroy(cap);
+            e = build_graph(plan);
             if (e != cudaSuccess) {
                 plan->exec = nullptr;
-                return cuda_fail(e, "vr_render_batched: graph capture");
+                return cuda_fail(e, "vr_render_batched: graph build");
             }
         }
         e = cudaGraphLaunch(plan->exec, s);
@@ -454,11 +504,13 @@ extern "C" vr_status vr_render_batched_noalloc(const vr_job *jobs, int n, int ti
     }
     // descriptors, built in fixed host buffers (no host allocation either)
     static thread_local JobDev hj[kNoAllocMaxJobs];
-    static thread_local int group_of[kNoAllocMaxJobs];
+    static thread_local int group_of[kNoAllocMaxJobs], order[kNoAllocMaxJobs];
+    static thread_local double cost[kNoAllocMaxJobs];
     Segment seg[kGroups];
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
     // only brick copies that exist already are used (building one allocates)
-    vr_status st = prepare_jobs(jobs, n, tile_w, false, s, hj, group_of, seg, "vr_render_batched_noalloc");
+    vr_status st = prepare_jobs(jobs, n, tile_w, false, s, hj, group_of, order, cost, seg,
+                                  "vr_render_batched_noalloc");
     if (st != VR_OK) return st;
     size_grids(seg, 0);
     NoAllocScratch *scratch = noalloc_scratch_ptr(st);
