@@ -74,6 +74,19 @@ def lib():
             L.orc_ray.argtypes = [P(Volume), P(Camera), P(Params), C.c_int, C.c_int,
                                   P(C.c_double * 3), P(C.c_double * 3), P(C.c_double)]
             L.orc_ray.restype = C.c_int64
+            L.orc_profile.argtypes = [P(Volume), P(Camera), P(Params), C.c_int, C.c_int, C.c_void_p, C.c_int64]
+            L.orc_profile.restype = C.c_int64
+            L.orc_render_mip.argtypes = [P(Volume), P(Camera), P(Params), C.c_int, C.c_int, C.c_void_p,
+                                         C.c_void_p, C.c_void_p, C.c_int]
+            L.orc_render_mip.restype = C.c_int
+            L.orc_minimap.argtypes = [P(Volume), P(C.c_int * 3), C.c_void_p, P(C.c_int64 * 3)]
+            L.orc_minimap.restype = C.c_int
+            L.orc_minimap_sample.argtypes = [C.c_void_p, P(C.c_int64 * 3), P(C.c_int * 3), P(C.c_double * 3),
+                                             P(C.c_double * 2)]
+            L.orc_minimap_sample.restype = None
+            L.orc_render_sigma.argtypes = [P(Volume), P(Camera), P(Params), C.c_void_p, P(C.c_int64 * 3),
+                                           P(C.c_int * 3), C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_int]
+            L.orc_render_sigma.restype = C.c_int
             _lib = L
     return _lib
 
@@ -177,3 +190,78 @@ def ray(cube_shape, cam, step, i, j, origin=(0.0, 0.0, 0.0), spacing=(1.0, 1.0, 
     n = lib().orc_ray(C.byref(c.vol), C.byref(c.cam), C.byref(c.par), int(i), int(j), C.byref(ov),
                       C.byref(dv), C.byref(tin))
     return int(n), np.array(list(ov)), np.array(list(dv)), tin.value
+
+
+def profile(cube, cam, step, i, j, origin=(0.0, 0.0, 0.0), spacing=(1.0, 1.0, 1.0), bits=None):
+    """3D spectrum tool (Section 4.4): trilinear values of the samples along
+    pixel (i, j)'s clipped ray, at the renderer's sample positions."""
+    c = _Call(cube, cam, [[0, 0, 0, 0], [0, 0, 0, 0]], 0.0, 1.0, step, 2.0, (0, 0, 0, 0), origin, spacing, bits)
+    n = lib().orc_profile(C.byref(c.vol), C.byref(c.cam), C.byref(c.par), int(i), int(j), None, 0)
+    if n < 0:
+        raise ValueError("orc_profile failed")
+    out = np.zeros(max(int(n), 1), dtype=np.float64)
+    lib().orc_profile(C.byref(c.vol), C.byref(c.cam), C.byref(c.par), int(i), int(j), out.ctypes.data, int(n))
+    return out[:int(n)]
+
+
+def render_mip(cube, cam, tf, vmin, vmax, step, bg=(0.0, 0.0, 0.0, 0.0), origin=(0.0, 0.0, 0.0),
+               spacing=(1.0, 1.0, 1.0), rows=None, nthreads=None, bits=None):
+    """Maximum intensity projection (Section 3.3.1).  Returns dict(rgba, n_used,
+    vmax (H,W) f64 -- each ray's largest value, NaN on a miss)."""
+    c = _Call(cube, cam, tf, vmin, vmax, step, 2.0, bg, origin, spacing, bits)
+    H, W = c.cam.height, c.cam.width
+    rgba = np.zeros((H, W, 4), dtype=np.float64)
+    n_used = np.zeros((H, W), dtype=np.int32)
+    vm = np.full((H, W), np.nan)
+    r0, r1 = rows if rows is not None else (0, H)
+    rc = lib().orc_render_mip(C.byref(c.vol), C.byref(c.cam), C.byref(c.par), int(r0), int(r1), rgba.ctypes.data,
+                              n_used.ctypes.data, vm.ctypes.data, int(nthreads or os.cpu_count() or 1))
+    if rc != 0:
+        raise ValueError("orc_render_mip failed (%d)" % rc)
+    return dict(rgba=rgba, n_used=n_used, vmax=vm)
+
+
+def minimap(cube, region, bits=None):
+    """Statistical mini-map (Section 4.5): (mk, mj, mi, 2) array of the mean and
+    population standard deviation of each region of region = (rx, ry, rz)
+    voxels (the last region of an axis keeps the remainder)."""
+    c = _Call(cube, dict(kind=0, eye=(0, 0, 0), forward=(0, 0, 1), up=(0, 1, 0), width=1, height=1),
+              [[0, 0, 0, 0], [0, 0, 0, 0]], 0.0, 1.0, 1.0, 2.0, (0, 0, 0, 0), (0, 0, 0), (1, 1, 1), bits)
+    nz, ny, nx = c.cube.shape
+    m = [-(-n // r) for n, r in zip((nx, ny, nz), region)]
+    out = np.zeros((m[2], m[1], m[0], 2), dtype=np.float64)
+    mm = (C.c_int64 * 3)()
+    rc = lib().orc_minimap(C.byref(c.vol), C.byref((C.c_int * 3)(*region)), out.ctypes.data, C.byref(mm))
+    if rc != 0:
+        raise ValueError("orc_minimap failed (%d)" % rc)
+    return out
+
+
+def minimap_sample(stats, region, p):
+    """(mean, sd) of the mini-map at voxel position p = (x, y, z)."""
+    stats = np.ascontiguousarray(stats, dtype=np.float64)
+    mk, mj, mi = stats.shape[:3]
+    out = (C.c_double * 2)()
+    lib().orc_minimap_sample(stats.ctypes.data, C.byref((C.c_int64 * 3)(mi, mj, mk)),
+                             C.byref((C.c_int * 3)(*region)), C.byref((C.c_double * 3)(*p)), C.byref(out))
+    return out[0], out[1]
+
+
+def render_sigma(cube, cam, tf, vmin, vmax, step, stats, region, ert=2.0, bg=(0.0, 0.0, 0.0, 0.0),
+                 origin=(0.0, 0.0, 0.0), spacing=(1.0, 1.0, 1.0), rows=None, nthreads=None, bits=None):
+    """Sigma-clipping render (Section 4.5): each sample value becomes
+    (v - mean)/sd of the mini-map `stats` at its position before the table
+    lookup; [vmin, vmax] are in units of sd.  Returns dict(rgba, n_used)."""
+    c = _Call(cube, cam, tf, vmin, vmax, step, ert, bg, origin, spacing, bits)
+    st = np.ascontiguousarray(stats, dtype=np.float64)
+    mk, mj, mi = st.shape[:3]
+    H, W = c.cam.height, c.cam.width
+    rgba = np.zeros((H, W, 4), dtype=np.float64)
+    n_used = np.zeros((H, W), dtype=np.int32)
+    r0, r1 = rows if rows is not None else (0, H)
+    rc = lib().orc_render_sigma(C.byref(c.vol), C.byref(c.cam), C.byref(c.par), st.ctypes.data,
+                                C.byref((C.c_int64 * 3)(mi, mj, mk)), C.byref((C.c_int * 3)(*region)), int(r0),
+                                int(r1), rgba.ctypes.data, n_used.ctypes.data, int(nthreads or os.cpu_count() or 1))
+    if rc != 0:
+        raise ValueError("orc_render_sigma failed (%d)" % rc)
+    return dict(rgba=rgba, n_used=n_used)

@@ -40,6 +40,12 @@
  * front with suffix accumulators (no division by transmittance), followed by
  * the chain rule through the transfer-function blend and the trilinear
  * weights.
+ *
+ * The same ray also serves the paper's other tools (end of this file): the
+ * 3D spectrum tool of Section 4.4 (the values along one pixel's line of
+ * sight), maximum intensity projection (Section 3.3.1) and the
+ * sigma-clipping transfer function of Section 4.5 (sample values scaled by
+ * the statistics of a mini-map of region means and standard deviations).
  */
 #include <math.h>
 #include <pthread.h>
@@ -562,4 +568,286 @@ int64_t orc_ray(const orc_volume *v, const orc_camera *c, const orc_params *P, i
     for (int a = 0; a < 3; ++a) { ov[a] = rs.ov[a]; dv[a] = rs.dv[a]; }
     *t_in = rs.t_in;
     return rs.n;
+}
+
+/* ======================================================================== */
+/* Further uses of the same ray (Sections 3.3.1, 4.4 and 4.5)                */
+/* ======================================================================== */
+
+/* ------------------------------------------------------------------------ */
+/* 3D spectrum tool (Section 4.4): the data profile along one pixel's line   */
+/* of sight, sampled at the renderer's positions with trilinear values.      */
+/* ------------------------------------------------------------------------ */
+
+/* Values of the first `max` samples of pixel (i, j)'s clipped ray (no table,
+ * no early termination).  Returns the ray's sample count (0 on a miss). */
+int64_t orc_profile(const orc_volume *v, const orc_camera *c, const orc_params *P, int i, int j, double *values,
+                    int64_t max)
+{
+    if (check_args(v, c, P)) return -1;
+    basis b = camera_basis(c);
+    ray_setup rs;
+    setup_ray(v, c, &b, P, i, j, &rs);
+    for (int64_t k = 0; k < rs.n && k < max; ++k) {
+        double p[3];
+        sample_pos(&rs, P, k, p);
+        values[k] = trilinear(v, p, NULL);
+    }
+    return rs.n;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Maximum intensity projection (Section 3.3.1): only the largest value on   */
+/* each ray is shown, through the colour map.                                */
+/* ------------------------------------------------------------------------ */
+
+/* Reading: the pixel is the table entry of the ray's largest sample value,
+ * composited once over the background, (a c + (1 - a) bg.rgb, a + (1 - a)
+ * bg.a) -- a one-sample front-to-back composite; a ray that misses the box
+ * shows the background.  Every sample of the ray is visited (no early
+ * termination). */
+static void mip_pixel(const orc_volume *v, const orc_camera *c, const basis *b, const orc_params *P, int i, int j,
+                      double out[4], int32_t *n_used, double *vmax)
+{
+    ray_setup rs;
+    setup_ray(v, c, b, P, i, j, &rs);
+    double m = -INFINITY;
+    for (int64_t k = 0; k < rs.n; ++k) {
+        double p[3];
+        sample_pos(&rs, P, k, p);
+        double val = trilinear(v, p, NULL);
+        if (val > m) m = val;
+    }
+    if (rs.n > 0) {
+        double rgba[4];
+        tf_lookup(P, m, rgba, NULL);
+        double a = rgba[3];
+        for (int ch = 0; ch < 3; ++ch) out[ch] = a * rgba[ch] + (1.0 - a) * P->bg[ch];
+        out[3] = a + (1.0 - a) * P->bg[3];
+    } else {
+        for (int ch = 0; ch < 4; ++ch) out[ch] = P->bg[ch];
+    }
+    if (n_used) *n_used = (int32_t)rs.n;
+    if (vmax) *vmax = rs.n > 0 ? m : NAN;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Sigma-clipping transfer function (Section 4.5): a statistical mini-map    */
+/* summarises regions of the cube; each sample value is scaled by its        */
+/* region statistics (trilinear on the mini-map) before the table lookup.    */
+/* ------------------------------------------------------------------------ */
+
+/* Mini-map: the cube is split into regions of region[a] voxels per axis (the
+ * last region of an axis keeps the remainder); point q = (k*mj + j)*mi + i
+ * holds the mean (stats[2q]) and the population standard deviation
+ * (stats[2q+1]) of region (i, j, k)'s voxels.  m[] receives the point counts
+ * per axis.  Returns 0, or -1 on invalid arguments. */
+int orc_minimap(const orc_volume *v, const int region[3], double *stats, int64_t m[3])
+{
+    if (!v || !v->data || !stats) return -1;
+    for (int a = 0; a < 3; ++a) {
+        if (region[a] < 1) return -1;
+        m[a] = (v->n[a] + region[a] - 1) / region[a];
+    }
+    for (int64_t k = 0; k < m[2]; ++k)
+        for (int64_t j = 0; j < m[1]; ++j)
+            for (int64_t i = 0; i < m[0]; ++i) {
+                int64_t lo[3] = {i * region[0], j * region[1], k * region[2]}, hi[3];
+                for (int a = 0; a < 3; ++a) {
+                    hi[a] = lo[a] + region[a];
+                    if (hi[a] > v->n[a]) hi[a] = v->n[a];
+                }
+                double sum = 0.0, cnt = 0.0;
+                for (int64_t z = lo[2]; z < hi[2]; ++z)
+                    for (int64_t y = lo[1]; y < hi[1]; ++y)
+                        for (int64_t x = lo[0]; x < hi[0]; ++x) {
+                            sum += voxel_at(v, x, y, z);
+                            cnt += 1.0;
+                        }
+                double mean = sum / cnt, ss = 0.0;
+                for (int64_t z = lo[2]; z < hi[2]; ++z)
+                    for (int64_t y = lo[1]; y < hi[1]; ++y)
+                        for (int64_t x = lo[0]; x < hi[0]; ++x) {
+                            double d = voxel_at(v, x, y, z) - mean;
+                            ss += d * d;
+                        }
+                int64_t q = (k * m[1] + j) * m[0] + i;
+                stats[2 * q] = mean;
+                stats[2 * q + 1] = sqrt(ss / cnt);
+            }
+    return 0;
+}
+
+typedef struct {
+    const double *stats;
+    int64_t m[3];
+    int region[3];
+} minimap;
+
+/* Statistics at voxel position p: trilinear over the points, point i of axis
+ * a sitting at (i + 1/2) region[a] - 1/2 (the centre of a full region);
+ * beyond the first and last points the nearest point's value (the weight is
+ * clamped to [0, 1]); an axis with one point is constant. */
+static void minimap_sample(const minimap *mm, const double p[3], double *mean, double *sd)
+{
+    int64_t i0[3];
+    double w[3];
+    for (int a = 0; a < 3; ++a) {
+        if (mm->m[a] < 2) {
+            i0[a] = 0;
+            w[a] = 0.0;
+            continue;
+        }
+        double g = (p[a] + 0.5) / mm->region[a] - 0.5;
+        int64_t f = (int64_t)floor(g);
+        if (f < 0) f = 0;
+        if (f > mm->m[a] - 2) f = mm->m[a] - 2;
+        double t = g - (double)f;
+        if (t < 0.0) t = 0.0;
+        if (t > 1.0) t = 1.0;
+        i0[a] = f;
+        w[a] = t;
+    }
+    double acc[2] = {0.0, 0.0};
+    for (int q = 0; q < 8; ++q) {
+        int64_t ix = i0[0] + (q & 1), iy = i0[1] + ((q >> 1) & 1), iz = i0[2] + ((q >> 2) & 1);
+        double wt = ((q & 1) ? w[0] : 1.0 - w[0]) * (((q >> 1) & 1) ? w[1] : 1.0 - w[1]) *
+                    (((q >> 2) & 1) ? w[2] : 1.0 - w[2]);
+        if (wt == 0.0) continue;
+        int64_t idx = (iz * mm->m[1] + iy) * mm->m[0] + ix;
+        acc[0] += wt * mm->stats[2 * idx];
+        acc[1] += wt * mm->stats[2 * idx + 1];
+    }
+    *mean = acc[0];
+    *sd = acc[1];
+}
+
+/* Probe of the mini-map interpolation (tests). */
+void orc_minimap_sample(const double *stats, const int64_t m[3], const int region[3], const double p[3],
+                        double out[2])
+{
+    minimap mm;
+    mm.stats = stats;
+    for (int a = 0; a < 3; ++a) { mm.m[a] = m[a]; mm.region[a] = region[a]; }
+    minimap_sample(&mm, p, &out[0], &out[1]);
+}
+
+/* The sample value in units of the local standard deviation above the local
+ * mean; a standard deviation below 1e-30 counts as 1e-30. */
+static double sigma_value(const minimap *mm, const double p[3], double val)
+{
+    double mean, sd;
+    minimap_sample(mm, p, &mean, &sd);
+    if (!(sd > 1e-30)) sd = 1e-30;
+    return (val - mean) / sd;
+}
+
+/* The composite render of render_pixel with every sample value replaced by
+ * sigma_value before the table lookup ([vmin, vmax] are in units of sigma). */
+static void sigma_pixel(const orc_volume *v, const orc_camera *c, const basis *b, const orc_params *P,
+                        const minimap *mm, int i, int j, double out[4], int32_t *n_used)
+{
+    ray_setup rs;
+    setup_ray(v, c, b, P, i, j, &rs);
+    double C[3] = {0.0, 0.0, 0.0}, T = 1.0;
+    int64_t used = 0;
+    for (int64_t k = 0; k < rs.n; ++k) {
+        double p[3], rgba[4];
+        sample_pos(&rs, P, k, p);
+        double val = sigma_value(mm, p, trilinear(v, p, NULL));
+        tf_lookup(P, val, rgba, NULL);
+        double a = rgba[3];
+        for (int ch = 0; ch < 3; ++ch) C[ch] += T * a * rgba[ch];
+        T *= (1.0 - a);
+        used = k + 1;
+        if (1.0 - T >= P->ert) break;
+    }
+    for (int ch = 0; ch < 3; ++ch) out[ch] = C[ch] + T * P->bg[ch];
+    out[3] = 1.0 - T + T * P->bg[3];
+    if (n_used) *n_used = (int32_t)used;
+}
+
+typedef struct {
+    job base;
+    int mode;                 /* 1 MIP, 2 sigma clipping */
+    const minimap *mm;
+    double *vmax;             /* MIP: H*W or NULL */
+} mode_job;
+
+static void *mode_worker(void *arg)
+{
+    mode_job *M = (mode_job *)arg;
+    job *J = &M->base;
+    int W = J->c->width;
+    int64_t first = (int64_t)J->row0 * W, last = (int64_t)J->row1 * W;
+    for (int64_t px = first + J->first; px < last; px += J->stride) {
+        int j = (int)(px / W), i = (int)(px % W);
+        int32_t *nu = J->n_used ? J->n_used + px : NULL;
+        if (M->mode == 1)
+            mip_pixel(J->v, J->c, &J->b, J->P, i, j, J->rgba + 4 * px, nu, M->vmax ? M->vmax + px : NULL);
+        else
+            sigma_pixel(J->v, J->c, &J->b, J->P, M->mm, i, j, J->rgba + 4 * px, nu);
+    }
+    return NULL;
+}
+
+static int run_mode(const orc_volume *v, const orc_camera *c, const orc_params *P, int mode, const minimap *mm,
+                    int row0, int row1, double *rgba, int32_t *n_used, double *vmax, int nthreads)
+{
+    if (check_args(v, c, P) || !rgba) return -1;
+    if (row0 < 0) row0 = 0;
+    if (row1 > c->height) row1 = c->height;
+    if (nthreads < 1) nthreads = 1;
+    mode_job *jobs = (mode_job *)calloc((size_t)nthreads, sizeof(mode_job));
+    if (!jobs) return -3;
+    basis b = camera_basis(c);
+    for (int t = 0; t < nthreads; ++t) {
+        job *J = &jobs[t].base;
+        J->v = v; J->c = c; J->P = P; J->b = b;
+        J->row0 = row0; J->row1 = row1; J->stride = nthreads; J->first = t;
+        J->rgba = rgba; J->n_used = n_used;
+        jobs[t].mode = mode; jobs[t].mm = mm; jobs[t].vmax = vmax;
+    }
+    int rc = 0;
+    if (nthreads <= 1) {
+        mode_worker(&jobs[0]);
+    } else {
+        pthread_t *th = (pthread_t *)malloc(sizeof(pthread_t) * (size_t)nthreads);
+        int started = 0;
+        if (!th) rc = -3;
+        for (int t = 0; t < nthreads && th; ++t) {
+            if (pthread_create(&th[t], NULL, mode_worker, &jobs[t]) != 0) break;
+            ++started;
+        }
+        for (int t = 0; t < started; ++t) pthread_join(th[t], NULL);
+        for (int t = started; t < nthreads && th; ++t) mode_worker(&jobs[t]);
+        free(th);
+    }
+    free(jobs);
+    return rc;
+}
+
+/* Maximum intensity projection of rows [row0, row1); vmax (H*W, may be NULL)
+ * receives each ray's largest value (NaN on a miss). */
+int orc_render_mip(const orc_volume *v, const orc_camera *c, const orc_params *P, int row0, int row1, double *rgba,
+                   int32_t *n_used, double *vmax, int nthreads)
+{
+    return run_mode(v, c, P, 1, NULL, row0, row1, rgba, n_used, vmax, nthreads);
+}
+
+/* Sigma-clipping render of rows [row0, row1) with the mini-map `stats` of
+ * orc_minimap (m[] points per axis, regions of region[] voxels). */
+int orc_render_sigma(const orc_volume *v, const orc_camera *c, const orc_params *P, const double *stats,
+                     const int64_t m[3], const int region[3], int row0, int row1, double *rgba, int32_t *n_used,
+                     int nthreads)
+{
+    if (!stats) return -1;
+    minimap mm;
+    mm.stats = stats;
+    for (int a = 0; a < 3; ++a) {
+        if (region[a] < 1 || m[a] < 1) return -1;
+        mm.m[a] = m[a];
+        mm.region[a] = region[a];
+    }
+    return run_mode(v, c, P, 2, &mm, row0, row1, rgba, n_used, NULL, nthreads);
 }
