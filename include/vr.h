@@ -58,6 +58,13 @@ typedef enum { VR_F32 = 0, VR_F16 = 1, VR_BF16 = 2 } vr_dtype;
 enum { VR_CAMERA_ORTHO = 0, VR_CAMERA_PERSPECTIVE = 1 };
 enum { VR_FILTER_SOFTWARE = 0, VR_FILTER_TEXTURE = 1, VR_FILTER_SOFTWARE_STAGED = 2 };
 
+/* What the ray computes (vr_params.mode). */
+enum {
+    VR_MODE_COMPOSITE = 0,    /* generic transfer function, front-to-back composite (Sections 3.3.2, 3.4) */
+    VR_MODE_MIP = 1,          /* maximum intensity projection (Section 3.3.1) */
+    VR_MODE_SIGMA = 2         /* sigma-clipping transfer function (Section 4.5) */
+};
+
 typedef struct vr_volume *vr_volume_t;   /* opaque, library-owned */
 
 /* Camera.  Basis: f = normalize(forward), r = normalize(f x up), u = r x f.
@@ -100,6 +107,17 @@ typedef struct {
                                    results; allocates a dense copy on first use);
                                  VR_FILTER_TEXTURE: hardware filter, 8-bit fractional weights,
                                    float32/float16 storage only, forward only */
+    int mode;                 /* VR_MODE_*; 0 for the composite.  VR_MODE_MIP: the pixel is the table
+                                   entry of the ray's largest sample value composited once over the
+                                   background, (a rgb + (1 - a) bg.rgb, a + (1 - a) bg.a); a miss shows
+                                   the background; no early termination; nsamples = all samples.
+                                 VR_MODE_SIGMA: the composite, with every sample value v replaced
+                                   by (v - mean) / sd of the mini-map (vr_minimap) trilinearly
+                                   interpolated at the sample; [vmin, vmax] are then in units of sd.
+                                 Both: software filter (VR_FILTER_SOFTWARE) and vr_render only. */
+    const float *minimap;     /* VR_MODE_SIGMA: device mini-map of vr_minimap for this volume and
+                                   minimap_region, 8-byte aligned; otherwise ignored */
+    int minimap_region[3];    /* VR_MODE_SIGMA: region size in voxels per axis, each >= 1 */
 } vr_params;
 
 typedef struct {
@@ -266,6 +284,34 @@ vr_status vr_autotune_batched(const vr_job *jobs, int n, vr_batch_opts *best, vo
 #define VR_NOALLOC_MAX_JOBS 256
 
 vr_status vr_render_batched_noalloc(const vr_job *jobs, int n, int tile_w, int tile_h, void *cuda_stream);
+
+/* ------------------------------------------------------------------------
+ * Statistical mini-map for the sigma-clipping transfer function (Section 4.5:
+ * a scaled-down copy of the cube whose points summarise regions of it).
+ *
+ * The cube is split into regions of region[a] voxels per axis (the last
+ * region of an axis keeps the remainder), m[a] = ceil(dims[a] / region[a])
+ * regions per axis.  Writes m0 * m1 * m2 float pairs to dev_minimap (x
+ * fastest; 8-byte aligned, caller-owned): the mean and the population
+ * standard deviation of the region's stored voxel values, summed in FP64
+ * (two passes) and rounded to float32.  Point (i, j, k) sits at voxel
+ * ((i + 1/2) region - 1/2, ...) for the interpolation of VR_MODE_SIGMA.
+ * Asynchronous on cuda_stream.  Errors: INVALID_ARG, CUDA.
+ * ---------------------------------------------------------------------- */
+vr_status vr_minimap(vr_volume_t vol, const int region[3], float *dev_minimap, void *cuda_stream);
+
+/* ------------------------------------------------------------------------
+ * 3D spectrum tool (Section 4.4: the data profile along the line of sight
+ * of a picked screen position).
+ *
+ * Writes the trilinear values of the samples of pixel (i, j)'s clipped ray
+ * (the renderer's sample positions t_in + (k + 1/2) step) to dev_values[k]
+ * for k < min(n, max_values) and n to *dev_count (0 when the ray misses the
+ * box).  dev_values holds max_values floats; both are caller-owned device
+ * memory.  Asynchronous on cuda_stream.  Errors: INVALID_ARG, CUDA.
+ * ---------------------------------------------------------------------- */
+vr_status vr_profile(vr_volume_t vol, const vr_camera *cam, float step, int i, int j, float *dev_values,
+                     uint32_t max_values, uint32_t *dev_count, void *cuda_stream);
 
 /* Synchronises cuda_stream and reports whether a bounded device-side wait of an
  * earlier call on this volume gave up (the staged kernels wait on the copy

@@ -20,6 +20,7 @@ VR_F32, VR_F16, VR_BF16 = 0, 1, 2
 VR_CAMERA_ORTHO, VR_CAMERA_PERSPECTIVE = 0, 1
 VR_FILTER_SOFTWARE, VR_FILTER_TEXTURE, VR_FILTER_SOFTWARE_STAGED = 0, 1, 2
 VR_GRAD_ACCUMULATE = 1
+VR_MODE_COMPOSITE, VR_MODE_MIP, VR_MODE_SIGMA = 0, 1, 2
 
 STATUS_NAMES = {0: "VR_OK", -1: "VR_ERR_INVALID_ARG", -2: "VR_ERR_UNSUPPORTED", -3: "VR_ERR_OOM",
                 -4: "VR_ERR_CUDA", -5: "VR_ERR_TIMEOUT", -6: "VR_ERR_INTERNAL"}
@@ -34,7 +35,7 @@ class vr_camera(C.Structure):
 class vr_params(C.Structure):
     _fields_ = [("tf_rgba", C.c_void_p), ("tf_size", C.c_int), ("vmin", C.c_float), ("vmax", C.c_float),
                 ("step", C.c_float), ("ert_threshold", C.c_float), ("bg_rgba", C.c_float * 4),
-                ("filter", C.c_int)]
+                ("filter", C.c_int), ("mode", C.c_int), ("minimap", C.c_void_p), ("minimap_region", C.c_int * 3)]
 
 
 class vr_volume_info_t(C.Structure):
@@ -55,7 +56,7 @@ class vr_batch_opts(C.Structure):
 # every symbol include/vr.h declares
 EXPORTS = ("vr_volume_create", "vr_volume_update", "vr_volume_destroy", "vr_volume_info", "vr_render",
            "vr_render_backward", "vr_render_batched", "vr_autotune_batched", "vr_render_batched_noalloc",
-           "vr_check", "vr_last_error", "vr_version")
+           "vr_minimap", "vr_profile", "vr_check", "vr_last_error", "vr_version")
 VR_NOALLOC_MAX_JOBS = 256
 
 _lock = threading.Lock()
@@ -91,9 +92,11 @@ def load() -> C.CDLL:
         L.vr_autotune_batched.argtypes = [P(vr_job), C.c_int, P(vr_batch_opts), vp]
         L.vr_render_batched_noalloc.argtypes = [P(vr_job), C.c_int, C.c_int, C.c_int, vp]
         L.vr_check.argtypes = [vp, vp]
+        L.vr_minimap.argtypes = [vp, P(C.c_int * 3), vp, vp]
+        L.vr_profile.argtypes = [vp, P(vr_camera), C.c_float, C.c_int, C.c_int, vp, C.c_uint32, vp, vp]
         for name in ("vr_volume_create", "vr_volume_update", "vr_volume_destroy", "vr_volume_info", "vr_render",
                      "vr_render_backward", "vr_render_batched", "vr_autotune_batched",
-                     "vr_render_batched_noalloc", "vr_check"):
+                     "vr_render_batched_noalloc", "vr_minimap", "vr_profile", "vr_check"):
             getattr(L, name).restype = C.c_int
         L.vr_last_error.argtypes = []
         L.vr_last_error.restype = C.c_char_p
@@ -123,9 +126,10 @@ def make_camera(cam: dict) -> vr_camera:
 
 
 def make_params(tf_ptr: int, K: int, vmin: float, vmax: float, step: float, ert: float = 2.0,
-                bg=(0.0, 0.0, 0.0, 0.0), filter: int = VR_FILTER_SOFTWARE) -> vr_params:
+                bg=(0.0, 0.0, 0.0, 0.0), filter: int = VR_FILTER_SOFTWARE, mode: int = VR_MODE_COMPOSITE,
+                minimap_ptr: int | None = None, region=(1, 1, 1)) -> vr_params:
     return vr_params(tf_ptr, int(K), float(vmin), float(vmax), float(step), float(ert), (C.c_float * 4)(*bg),
-                     int(filter))
+                     int(filter), int(mode), minimap_ptr, (C.c_int * 3)(*[int(r) for r in region]))
 
 
 # ---------------------------------------------------------------------------
@@ -193,6 +197,17 @@ def vr_render_batched_noalloc(jobs, tile_w: int = 0, tile_h: int = 0, stream: in
     arr = (vr_job * len(jobs))(*jobs)
     _check("vr_render_batched_noalloc", load().vr_render_batched_noalloc(arr, len(jobs), int(tile_w), int(tile_h),
                                                                          stream))
+
+
+def vr_minimap(vol: int, region, dev_minimap: int, stream: int = 0):
+    _check("vr_minimap", load().vr_minimap(vol, C.byref((C.c_int * 3)(*[int(r) for r in region])), dev_minimap,
+                                           stream))
+
+
+def vr_profile(vol: int, cam: vr_camera, step: float, i: int, j: int, dev_values: int | None, max_values: int,
+               dev_count: int, stream: int = 0):
+    _check("vr_profile", load().vr_profile(vol, C.byref(cam), float(step), int(i), int(j), dev_values,
+                                           int(max_values), dev_count, stream))
 
 
 def vr_check(vol: int, stream: int = 0):

@@ -3,6 +3,7 @@ PyTorch, the work is done by libvr.so.  Tensors must live on a CUDA device;
 nothing here computes on the CPU."""
 from __future__ import annotations
 
+import numpy as np
 import torch
 
 from . import _lib as L
@@ -62,23 +63,33 @@ class Volume:
             pass
 
 
-def _params(tf: torch.Tensor, vmin, vmax, step, ert, bg, filter):
+def _params(tf: torch.Tensor, vmin, vmax, step, ert, bg, filter, mode=L.VR_MODE_COMPOSITE, minimap=None,
+            region=(1, 1, 1)):
     _need_cuda(tf, "tf")
     if tf.dtype != torch.float32 or tf.dim() != 2 or tf.shape[1] != 4:
         raise ValueError("tf must be a (K, 4) float32 CUDA tensor")
-    return L.make_params(tf.data_ptr(), tf.shape[0], vmin, vmax, step, ert, bg, filter)
+    mm = None
+    if mode == L.VR_MODE_SIGMA:
+        if minimap is None:
+            raise ValueError("mode VR_MODE_SIGMA needs the volume's minimap (see minimap())")
+        _need_cuda(minimap, "minimap")
+        mm = minimap.data_ptr()
+    return L.make_params(tf.data_ptr(), tf.shape[0], vmin, vmax, step, ert, bg, filter, mode, mm, region)
 
 
 def render(vol: Volume, cam: dict, tf: torch.Tensor, vmin: float, vmax: float, step: float, ert: float = 2.0,
            bg=(0.0, 0.0, 0.0, 0.0), filter: int = L.VR_FILTER_SOFTWARE, want_nsamples: bool = True,
-           out: torch.Tensor | None = None, nsamples: torch.Tensor | None = None, stream=None):
-    """Forward render; returns (rgba (H, W, 4) float32, nsamples (H, W) int32 or None)."""
+           out: torch.Tensor | None = None, nsamples: torch.Tensor | None = None, stream=None,
+           mode: int = L.VR_MODE_COMPOSITE, minimap: torch.Tensor | None = None, region=(1, 1, 1)):
+    """Forward render; returns (rgba (H, W, 4) float32, nsamples (H, W) int32 or None).
+    mode: VR_MODE_COMPOSITE, VR_MODE_MIP, or VR_MODE_SIGMA with the volume's
+    `minimap` (from minimap(vol, region)) and its `region`."""
     H, W = int(cam["height"]), int(cam["width"])
     if out is None:
         out = torch.empty((H, W, 4), device=vol.device, dtype=torch.float32)
     if want_nsamples and nsamples is None:
         nsamples = torch.empty((H, W), device=vol.device, dtype=torch.int32)
-    p = _params(tf, vmin, vmax, step, ert, bg, filter)
+    p = _params(tf, vmin, vmax, step, ert, bg, filter, mode, minimap, region)
     L.vr_render(vol.handle, L.make_camera(cam), p, out.data_ptr(),
                 nsamples.data_ptr() if (want_nsamples and nsamples is not None) else None, _stream(stream))
     return out, (nsamples if want_nsamples else None)
@@ -99,6 +110,34 @@ def render_backward(vol: Volume, cam: dict, tf: torch.Tensor, vmin, vmax, step, 
                          grad_rgba.data_ptr(), grad_tf.data_ptr(), grad_vox.data_ptr() if want_vox else None,
                          L.VR_GRAD_ACCUMULATE if accumulate else 0, _stream(stream))
     return grad_tf, (grad_vox if want_vox else None)
+
+
+def minimap(vol: Volume, region, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """Statistical mini-map of the sigma-clipping transfer function: an
+    (mz, my, mx, 2) float32 tensor of each region's mean and standard
+    deviation (regions of region = (rx, ry, rz) voxels)."""
+    nz, ny, nx = vol.shape
+    m = [-(-n // int(r)) for n, r in zip((nx, ny, nz), region)]
+    if out is None:
+        out = torch.empty((m[2], m[1], m[0], 2), device=vol.device, dtype=torch.float32)
+    L.vr_minimap(vol.handle, region, out.data_ptr(), _stream(stream))
+    return out
+
+
+def profile(vol: Volume, cam: dict, step: float, i: int, j: int, max_values: int | None = None, stream=None):
+    """3D spectrum tool: the values of the samples along pixel (i, j)'s ray.
+    Returns a float32 CUDA tensor of the first min(n, max_values) values
+    (max_values defaults to a bound on any ray's sample count)."""
+    if max_values is None:
+        nz, ny, nx = vol.shape
+        diag = float(np.sqrt(sum(((n - 1) * s) ** 2 for n, s in zip((nx, ny, nz), vol.spacing))))
+        max_values = int(diag / step) + 2
+    values = torch.empty(max(1, max_values), device=vol.device, dtype=torch.float32)
+    count = torch.zeros(1, device=vol.device, dtype=torch.int32)
+    L.vr_profile(vol.handle, L.make_camera(cam), step, i, j, values.data_ptr(), max_values, count.data_ptr(),
+                 _stream(stream))
+    n = min(int(count.item()), max_values)
+    return values[:n]
 
 
 class RenderFunction(torch.autograd.Function):

@@ -95,6 +95,22 @@ static vr_status check_params(const vr_params *p)
     if (p->filter != VR_FILTER_SOFTWARE && p->filter != VR_FILTER_TEXTURE && p->filter != VR_FILTER_SOFTWARE_STAGED)
         return invalid("params.filter must be VR_FILTER_SOFTWARE (0), VR_FILTER_TEXTURE (1) or "
                        "VR_FILTER_SOFTWARE_STAGED (2)");
+    if (p->mode != VR_MODE_COMPOSITE && p->mode != VR_MODE_MIP && p->mode != VR_MODE_SIGMA)
+        return invalid("params.mode must be VR_MODE_COMPOSITE (0), VR_MODE_MIP (1) or VR_MODE_SIGMA (2)");
+    if (p->mode == VR_MODE_SIGMA) {
+        if (!p->minimap || (reinterpret_cast<uintptr_t>(p->minimap) & 7u) != 0)
+            return invalid("params.minimap must be non-NULL and 8-byte aligned for VR_MODE_SIGMA");
+        for (int a = 0; a < 3; ++a)
+            if (p->minimap_region[a] < 1) return invalid("params.minimap_region must be >= 1 per axis");
+    }
+    return VR_OK;
+}
+
+// The paths that implement a mode other than the composite.
+static vr_status check_mode_path(const vr_params *p, const char *who)
+{
+    if (p->mode != VR_MODE_COMPOSITE)
+        return (set_error(std::string(who) + ": only VR_MODE_COMPOSITE is supported here"), VR_ERR_UNSUPPORTED);
     return VR_OK;
 }
 
@@ -366,6 +382,7 @@ vr_status validate_job(const vr_job *J, int q)
     if (st == VR_OK) st = check_params(&J->params);
     if (st == VR_OK) st = check_volume(J->vol);
     if (st == VR_OK) st = check_step(J->vol, &J->params);
+    if (st == VR_OK) st = check_mode_path(&J->params, "batched render");
     if (st != VR_OK) set_error(where + g_err);
     return st;
 }
@@ -536,7 +553,16 @@ vr_status vr_render(vr_volume_t vol, const vr_camera *cam, const vr_params *para
     unsigned *ctr;
     next_counter(vol, &ctr);
     cudaError_t e;
-    if (params->filter == VR_FILTER_TEXTURE) {
+    if (params->mode != VR_MODE_COMPOSITE && params->filter != VR_FILTER_SOFTWARE)
+        return (set_error("vr_render: VR_MODE_MIP and VR_MODE_SIGMA need VR_FILTER_SOFTWARE"), VR_ERR_UNSUPPORTED);
+    if (params->mode == VR_MODE_MIP) {
+        e = launch_mip(vol_dev_copy(vol, preferred_copy(vol, cam, true, s)), vol->store_dtype, c, p,
+                       reinterpret_cast<float4 *>(dev_rgba_out), dev_nsamples_out, ctr, s);
+    } else if (params->mode == VR_MODE_SIGMA) {
+        e = launch_sigma(vol_dev_copy(vol, preferred_copy(vol, cam, true, s)), vol->store_dtype, c, p,
+                         params->minimap, params->minimap_region, reinterpret_cast<float4 *>(dev_rgba_out),
+                         dev_nsamples_out, ctr, s);
+    } else if (params->filter == VR_FILTER_TEXTURE) {
         st = build_texture(vol, s);
         if (st != VR_OK) return st;
         e = launch_forward_texture(vol, c, p, reinterpret_cast<float4 *>(dev_rgba_out), dev_nsamples_out, ctr, s);
@@ -561,6 +587,7 @@ vr_status vr_render_backward(vr_volume_t vol, const vr_camera *cam, const vr_par
     g_err.clear();
     vr_status st = check_camera(cam);
     if (st == VR_OK) st = check_params(params);
+    if (st == VR_OK) st = check_mode_path(params, "vr_render_backward");
     if (st != VR_OK) return st;
     if (params->filter == VR_FILTER_TEXTURE)
         return (set_error("vr_render_backward: only the software filters are differentiable"), VR_ERR_UNSUPPORTED);
@@ -606,6 +633,47 @@ vr_status vr_render_backward(vr_volume_t vol, const vr_camera *cam, const vr_par
                             reinterpret_cast<const float4 *>(dev_grad_rgba), dev_grad_tf, dev_grad_vox, nvox, acc, ctr,
                             s);
     if (e != cudaSuccess) return cuda_fail(e, "vr_render_backward launch");
+    return VR_OK;
+}
+
+vr_status vr_minimap(vr_volume_t vol, const int region[3], float *dev_minimap, void *cuda_stream)
+{
+    g_err.clear();
+    vr_status st = check_volume(vol);
+    if (st != VR_OK) return st;
+    if (!region) return invalid("region is NULL");
+    for (int a = 0; a < 3; ++a)
+        if (region[a] < 1) return invalid("region must be >= 1 per axis");
+    if (!dev_minimap || (reinterpret_cast<uintptr_t>(dev_minimap) & 7u) != 0)
+        return invalid("dev_minimap must be non-NULL and 8-byte aligned");
+    cudaError_t e = launch_minimap(vol_dev(vol), vol->store_dtype, region, dev_minimap,
+                                   static_cast<cudaStream_t>(cuda_stream));
+    if (e != cudaSuccess) return cuda_fail(e, "vr_minimap launch");
+    return VR_OK;
+}
+
+vr_status vr_profile(vr_volume_t vol, const vr_camera *cam, float step, int i, int j, float *dev_values,
+                     uint32_t max_values, uint32_t *dev_count, void *cuda_stream)
+{
+    g_err.clear();
+    vr_status st = check_camera(cam);
+    if (st == VR_OK) st = check_volume(vol);
+    if (st != VR_OK) return st;
+    if (!std::isfinite(step) || !(step > 0.0f)) return invalid("step must be finite and > 0");
+    if (i < 0 || j < 0 || i >= cam->width || j >= cam->height) return invalid("pixel (i, j) outside the image");
+    if (!dev_count || (reinterpret_cast<uintptr_t>(dev_count) & 3u) != 0)
+        return invalid("dev_count must be non-NULL and 4-byte aligned");
+    if (max_values > 0 && (!dev_values || (reinterpret_cast<uintptr_t>(dev_values) & 3u) != 0))
+        return invalid("dev_values must be non-NULL and 4-byte aligned when max_values > 0");
+    vr_params tmp{};
+    tmp.step = step;
+    st = check_step(vol, &tmp);
+    if (st != VR_OK) return st;
+    CamDev c;
+    prepare_camera(vol, cam, &c);
+    cudaError_t e = launch_profile(vol_dev(vol), vol->store_dtype, c, step, i, j, dev_values, max_values, dev_count,
+                                   static_cast<cudaStream_t>(cuda_stream));
+    if (e != cudaSuccess) return cuda_fail(e, "vr_profile launch");
     return VR_OK;
 }
 

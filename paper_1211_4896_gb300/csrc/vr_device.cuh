@@ -369,12 +369,19 @@ struct Composite {
 template <typename T> struct Pipeline { static constexpr int depth = 2; };
 template <> struct Pipeline<float> { static constexpr int depth = 1; };
 
+// The value the transfer function sees for a sample: the interpolated value
+// itself (generic transfer function), or a transform of it at the sample's
+// cell (the sigma-clipping transfer function, vr_modes.cu).
+struct IdentityMap {
+    __device__ __forceinline__ float operator()(float v, const Cell &) const { return v; }
+};
+
 // One sample: composites (cur, fc) and, while the ray goes on, issues the
 // gathers of sample k + depth into (nxt, fn).
-template <typename T, int LOG2B, int L>
+template <typename T, int LOG2B, int L, typename Map = IdentityMap>
 __device__ __forceinline__ void march_step(const VolDev &v, const ParamDev &p, const Ray &ray, int &k, bool &active,
                                            Composite &acc, const Cell &cur, const Gathered<T, L> &fc, Cell &nxt,
-                                           Gathered<T, L> &fn)
+                                           Gathered<T, L> &fn, const Map &map = Map())
 {
     constexpr int D = Pipeline<T>::depth;
     const bool more = k + 1 < ray.n;
@@ -382,7 +389,7 @@ __device__ __forceinline__ void march_step(const VolDev &v, const ParamDev &p, c
         nxt = locate<LOG2B, L>(v, sample_pos(ray, k + D, p.step));
         fetch_corners<T, LOG2B, L>(v, nxt, fn);
     }
-    const float val = interp_corners(cur, fc);
+    const float val = map(interp_corners(cur, fc), cur);
     TfPos tp;
     const float4 e = tf_lookup_l1(p, val, tp);
     const float aT = e.w * acc.T;
@@ -396,9 +403,9 @@ __device__ __forceinline__ void march_step(const VolDev &v, const ParamDev &p, c
 
 // The loop body is unrolled over depth + 1 register sets that take turns, so
 // a prefetched sample is never copied.
-template <typename T, int LOG2B, int L>
+template <typename T, int LOG2B, int L, typename Map = IdentityMap>
 __device__ __forceinline__ int march_ray(const VolDev &v, const ParamDev &p, const Ray &ray, bool active,
-                                         Composite &acc)
+                                         Composite &acc, const Map &map = Map())
 {
     constexpr int D = Pipeline<T>::depth;
     static_assert(D == 1 || D == 2, "pipeline depth 1 or 2");
@@ -416,18 +423,18 @@ __device__ __forceinline__ int march_ray(const VolDev &v, const ParamDev &p, con
     if constexpr (D == 1) {
         for (;;) {
             if (!__any_sync(kFull, active)) break;
-            if (active) march_step<T, LOG2B, L>(v, p, ray, k, active, acc, c0, f0, c1, f1);
+            if (active) march_step<T, LOG2B, L, Map>(v, p, ray, k, active, acc, c0, f0, c1, f1, map);
             if (!__any_sync(kFull, active)) break;
-            if (active) march_step<T, LOG2B, L>(v, p, ray, k, active, acc, c1, f1, c0, f0);
+            if (active) march_step<T, LOG2B, L, Map>(v, p, ray, k, active, acc, c1, f1, c0, f0, map);
         }
     } else {
         for (;;) {
             if (!__any_sync(kFull, active)) break;
-            if (active) march_step<T, LOG2B, L>(v, p, ray, k, active, acc, c0, f0, c2, f2);
+            if (active) march_step<T, LOG2B, L, Map>(v, p, ray, k, active, acc, c0, f0, c2, f2, map);
             if (!__any_sync(kFull, active)) break;
-            if (active) march_step<T, LOG2B, L>(v, p, ray, k, active, acc, c1, f1, c0, f0);
+            if (active) march_step<T, LOG2B, L, Map>(v, p, ray, k, active, acc, c1, f1, c0, f0, map);
             if (!__any_sync(kFull, active)) break;
-            if (active) march_step<T, LOG2B, L>(v, p, ray, k, active, acc, c2, f2, c1, f1);
+            if (active) march_step<T, LOG2B, L, Map>(v, p, ray, k, active, acc, c2, f2, c1, f1, map);
         }
     }
     return k;

@@ -140,6 +140,14 @@ cudaError_t launch_backward_staged(const DenseDev &d, vr_dtype dt, const CamDev 
                                    double *grad_tf, float *grad_vox, long long nvox, bool accumulate,
                                    unsigned *counter, unsigned *status, cudaStream_t s);
 int occupancy_blocks(const void *fn, int threads, size_t smem);
+// Other uses of the march (vr_modes.cu).
+cudaError_t launch_mip(const VolDev &v, vr_dtype dt, const CamDev &c, const ParamDev &p, float4 *out,
+                       uint32_t *nsamples, unsigned *counter, cudaStream_t s);
+cudaError_t launch_sigma(const VolDev &v, vr_dtype dt, const CamDev &c, const ParamDev &p, const float *minimap,
+                         const int region[3], float4 *out, uint32_t *nsamples, unsigned *counter, cudaStream_t s);
+cudaError_t launch_minimap(const VolDev &v, vr_dtype dt, const int region[3], float *dev_out, cudaStream_t s);
+cudaError_t launch_profile(const VolDev &v, vr_dtype dt, const CamDev &c, float step, int i, int j, float *values,
+                           unsigned max_values, unsigned *count, cudaStream_t s);
 vr_status validate_job(const vr_job *job, int index);
 void purge_plans(const vr_volume *vol);
 
