@@ -641,8 +641,62 @@ def run_diff_512(args):
     vol.close()
 
 
+def run_modes_1024(args, mode_name):
+    """The 1024^3 float32 cube and the eight 1080p orbit views of the default
+    workload, rendered per view (vr_render) with maximum intensity projection
+    or the sigma-clipping transfer function (mini-map of 32^3 regions, table
+    over [0, 8] sigma); step 1, no early termination for MIP, 0.99 for sigma.
+    Pixel error against the oracle on three sampled rows of view 0."""
+    import torch
+    import oracle
+    import paper_1211_4896_gb300 as P
+    dev = torch.device("cuda")
+    pre = synth.preset_scale_1024()
+    cube = make_cube(pre, dev)
+    vol = P.Volume(cube, "f32")
+    host = cube.cpu().numpy()
+    del cube
+    torch.cuda.empty_cache()
+    tf_np = synth.tf_ramp(256)
+    tf = torch.from_numpy(tf_np).to(dev)
+    cams = pre["cameras"]
+    outs = [torch.empty((1080, 1920, 4), device=dev) for _ in cams]
+    nss = [torch.empty((1080, 1920), device=dev, dtype=torch.int32) for _ in cams]
+    region = (32, 32, 32)
+    res = {"workload": mode_name + "_1024", "views": len(cams), "image": [1920, 1080]}
+    if mode_name == "mip":
+        kw = dict(mode=P.VR_MODE_MIP)
+        vmin, vmax, ert = synth.TF_VMIN, synth.TF_VMAX, 2.0
+    else:
+        mm = P.minimap(vol, region)
+        res["minimap_ms"] = _time_ms(torch, lambda: P.minimap(vol, region, out=mm), 5)
+        res["minimap_region"] = list(region)
+        kw = dict(mode=P.VR_MODE_SIGMA, minimap=mm, region=region)
+        vmin, vmax, ert = 0.0, 8.0, 0.99
+
+    def f():
+        for c, o, n in zip(cams, outs, nss):
+            P.render(vol, c, tf, vmin, vmax, 1.0, ert, out=o, nsamples=n, **kw)
+    ms = _time_ms(torch, f, max(3, args.steps))
+    samples = sum(int(n.sum()) for n in nss)
+    gs = samples / ms / 1e6
+    rows = [440, 540, 640]
+    if mode_name == "mip":
+        ref = oracle.render_mip(host, cams[0], tf_np, vmin, vmax, 1.0, rows=(rows[0], rows[-1] + 1))
+    else:
+        stats = oracle.minimap(host, region)
+        ref = oracle.render_sigma(host, cams[0], tf_np, vmin, vmax, 1.0, stats, region, ert=ert,
+                                  rows=(rows[0], rows[-1] + 1))
+    res.update({"ms_8_views": ms, "samples": samples, "gsamples_per_s": gs,
+                "roofline_frac": gs * 32 / measured_peaks()[0], "roofline_peak_source": measured_peaks()[1],
+                "px_err": _px_err(outs[0].cpu().numpy(), nss[0].cpu().numpy(), ref, rows)})
+    print(json.dumps(res))
+    vol.close()
+
+
 WORKLOADS = {"plain_128": run_plain_128, "precision_4096": run_precision_4096, "batch_64": run_batch_64,
-             "diff_512": run_diff_512}
+             "diff_512": run_diff_512, "mip_1024": lambda a: run_modes_1024(a, "mip"),
+             "sigma_1024": lambda a: run_modes_1024(a, "sigma")}
 
 
 def main():
