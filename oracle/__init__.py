@@ -87,6 +87,12 @@ def lib():
             L.orc_render_sigma.argtypes = [P(Volume), P(Camera), P(Params), C.c_void_p, P(C.c_int64 * 3),
                                            P(C.c_int * 3), C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_int]
             L.orc_render_sigma.restype = C.c_int
+            L.orc_moments.argtypes = [P(Volume), P(C.c_double * 5)]
+            L.orc_moments.restype = C.c_int
+            L.orc_histogram.argtypes = [P(Volume), C.c_double, C.c_double, C.c_int, C.c_void_p]
+            L.orc_histogram.restype = C.c_int
+            L.orc_median.argtypes = [P(Volume), P(C.c_double), P(C.c_int)]
+            L.orc_median.restype = C.c_int
             _lib = L
     return _lib
 
@@ -265,3 +271,39 @@ def render_sigma(cube, cam, tf, vmin, vmax, step, stats, region, ert=2.0, bg=(0.
     if rc != 0:
         raise ValueError("orc_render_sigma failed (%d)" % rc)
     return dict(rgba=rgba, n_used=n_used)
+
+
+def _vol_only(cube, bits=None):
+    return _Call(cube, dict(kind=0, eye=(0, 0, 0), forward=(0, 0, 1), up=(0, 1, 0), width=1, height=1),
+                 [[0, 0, 0, 0], [0, 0, 0, 0]], 0.0, 1.0, 1.0, 2.0, (0, 0, 0, 0), (0, 0, 0), (1, 1, 1), bits)
+
+
+def moments(cube, bits=None):
+    """Global statistics of the non-NaN voxels (Section 4.2): dict(count,
+    mean, sd (population), min, max), FP64."""
+    c = _vol_only(cube, bits)
+    out = (C.c_double * 5)()
+    if lib().orc_moments(C.byref(c.vol), C.byref(out)) != 0:
+        raise ValueError("orc_moments failed")
+    return dict(count=int(out[0]), mean=out[1], sd=out[2], min=out[3], max=out[4])
+
+
+def histogram(cube, lo, hi, nbins, bits=None):
+    """Histogram of the non-NaN voxels over [lo, hi] in nbins equal bins
+    (Section 4.1; the value hi falls in the last bin)."""
+    c = _vol_only(cube, bits)
+    counts = np.zeros(int(nbins), dtype=np.uint64)
+    if lib().orc_histogram(C.byref(c.vol), float(lo), float(hi), int(nbins), counts.ctypes.data) != 0:
+        raise ValueError("orc_histogram failed")
+    return counts
+
+
+def median(cube, bits=None):
+    """Torben's median of the non-NaN voxels (Section 4.3 and the paper's
+    appendix): the value of rank (n + 1) // 2.  Returns (median, passes)."""
+    c = _vol_only(cube, bits)
+    m = C.c_double()
+    it = C.c_int()
+    if lib().orc_median(C.byref(c.vol), C.byref(m), C.byref(it)) != 0:
+        raise ValueError("orc_median failed (no values)")
+    return m.value, it.value

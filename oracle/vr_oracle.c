@@ -45,7 +45,9 @@
  * 3D spectrum tool of Section 4.4 (the values along one pixel's line of
  * sight), maximum intensity projection (Section 3.3.1) and the
  * sigma-clipping transfer function of Section 4.5 (sample values scaled by
- * the statistics of a mini-map of region means and standard deviations).
+ * the statistics of a mini-map of region means and standard deviations), and
+ * the global statistics of Sections 4.1-4.3 (histogram, mean and standard
+ * deviation, Torben's median as the appendix gives it).
  */
 #include <math.h>
 #include <pthread.h>
@@ -850,4 +852,110 @@ int orc_render_sigma(const orc_volume *v, const orc_camera *c, const orc_params 
         mm.region[a] = region[a];
     }
     return run_mode(v, c, P, 2, &mm, row0, row1, rgba, n_used, NULL, nthreads);
+}
+
+/* ======================================================================== */
+/* Global statistics of the cube (Sections 4.1-4.3)                          */
+/* ======================================================================== */
+
+/* NULL (undefined, NaN) voxels are left out of every statistic (Section 4
+ * asks for their special handling).  The stored values are widened exactly. */
+
+/* Count, mean, population standard deviation, minimum and maximum of the
+ * non-NaN voxels (two passes in FP64).  out = {count, mean, sd, min, max}. */
+int orc_moments(const orc_volume *v, double out[5])
+{
+    if (!v || !v->data) return -1;
+    double n = 0.0, sum = 0.0, mn = INFINITY, mx = -INFINITY;
+    for (int64_t z = 0; z < v->n[2]; ++z)
+        for (int64_t y = 0; y < v->n[1]; ++y)
+            for (int64_t x = 0; x < v->n[0]; ++x) {
+                double a = voxel_at(v, x, y, z);
+                if (isnan(a)) continue;
+                n += 1.0;
+                sum += a;
+                if (a < mn) mn = a;
+                if (a > mx) mx = a;
+            }
+    double mean = n > 0 ? sum / n : NAN, ss = 0.0;
+    for (int64_t z = 0; z < v->n[2]; ++z)
+        for (int64_t y = 0; y < v->n[1]; ++y)
+            for (int64_t x = 0; x < v->n[0]; ++x) {
+                double a = voxel_at(v, x, y, z);
+                if (isnan(a)) continue;
+                ss += (a - mean) * (a - mean);
+            }
+    out[0] = n;
+    out[1] = mean;
+    out[2] = n > 0 ? sqrt(ss / n) : NAN;
+    out[3] = mn;
+    out[4] = mx;
+    return 0;
+}
+
+/* Histogram of the non-NaN voxels over [lo, hi] in nbins equal bins (Section
+ * 4.1): value a goes to bin floor((a - lo) / (hi - lo) * nbins), the value hi
+ * to the last bin; values outside [lo, hi] are not counted. */
+int orc_histogram(const orc_volume *v, double lo, double hi, int nbins, uint64_t *counts)
+{
+    if (!v || !v->data || !counts || nbins < 1 || !(hi > lo)) return -1;
+    for (int b = 0; b < nbins; ++b) counts[b] = 0;
+    for (int64_t z = 0; z < v->n[2]; ++z)
+        for (int64_t y = 0; y < v->n[1]; ++y)
+            for (int64_t x = 0; x < v->n[0]; ++x) {
+                double a = voxel_at(v, x, y, z);
+                if (!(a >= lo && a <= hi)) continue;          /* also drops NaN */
+                int64_t b = (int64_t)floor((a - lo) / (hi - lo) * nbins);
+                if (b >= nbins) b = nbins - 1;
+                counts[b] += 1;
+            }
+    return 0;
+}
+
+/* Median of the non-NaN voxels by Torben Mogensen's method as the paper's
+ * appendix states it: repeated passes that count the values below, above and
+ * equal to a guess halfway between the current bounds, and note the largest
+ * value below and the smallest above it, until neither side holds more than
+ * half of the values.  The result is the value of rank (n + 1) / 2 (integer
+ * division, 1-based): the median for odd n, the lower median for even n.
+ * *passes receives the number of passes.  Returns 0, -1 without values. */
+int orc_median(const orc_volume *v, double *median, int *passes)
+{
+    double m5[5];
+    if (orc_moments(v, m5) || !(m5[0] > 0)) return -1;
+    const int64_t n = (int64_t)m5[0], half = (n + 1) / 2;
+    double lo = m5[3], hi = m5[4];
+    int it = 0;
+    int64_t less, greater, equal;
+    double guess, max_lt, min_gt;
+    for (;;) {
+        ++it;
+        guess = 0.5 * (lo + hi);
+        less = greater = equal = 0;
+        max_lt = lo;
+        min_gt = hi;
+        for (int64_t z = 0; z < v->n[2]; ++z)
+            for (int64_t y = 0; y < v->n[1]; ++y)
+                for (int64_t x = 0; x < v->n[0]; ++x) {
+                    double a = voxel_at(v, x, y, z);
+                    if (isnan(a)) continue;
+                    if (a < guess) {
+                        ++less;
+                        if (a > max_lt) max_lt = a;
+                    } else if (a > guess) {
+                        ++greater;
+                        if (a < min_gt) min_gt = a;
+                    } else {
+                        ++equal;
+                    }
+                }
+        if (less <= half && greater <= half) break;
+        if (less > greater) hi = max_lt;
+        else lo = min_gt;
+    }
+    if (less >= half) *median = max_lt;
+    else if (less + equal >= half) *median = guess;
+    else *median = min_gt;
+    if (passes) *passes = it;
+    return 0;
 }
