@@ -694,9 +694,52 @@ def run_modes_1024(args, mode_name):
     vol.close()
 
 
+def run_stats_1024(args):
+    """Global statistics of the 1024^3 float32 cube (Sections 4.1-4.3):
+    moments (one pass), a 256-bin histogram over [min, max] (one pass) and the
+    exact median (three passes), each streamed from the bricks; achieved
+    bandwidth = bricked bytes read / time, against the measured HBM copy
+    bandwidth.  Checked against the oracle."""
+    import torch
+    import oracle
+    import paper_1211_4896_gb300 as P
+    dev = torch.device("cuda")
+    pre = synth.preset_scale_1024()
+    cube = make_cube(pre, dev)
+    vol = P.Volume(cube, "f32")
+    host = cube.cpu().numpy()
+    del cube
+    torch.cuda.empty_cache()
+    bricked = vol.info["bytes"]
+    peak, src = measured_peaks()
+    s = int(torch.cuda.current_stream().cuda_stream)
+    from paper_1211_4896_gb300 import _lib as L
+    mom = torch.empty(5, device=dev, dtype=torch.float64)
+    med = torch.empty(1, device=dev, dtype=torch.float64)
+    m = P.moments(vol)
+    hist = torch.empty(256, device=dev, dtype=torch.int64)
+    reps = max(5, args.steps)
+    t_m = _time_ms(torch, lambda: L.vr_moments(vol.handle, mom.data_ptr(), s), reps)
+    t_h = _time_ms(torch, lambda: L.vr_histogram(vol.handle, m["min"], m["max"], 256, hist.data_ptr(), s), reps)
+    t_q = _time_ms(torch, lambda: L.vr_median(vol.handle, med.data_ptr(), s), reps)
+    r = oracle.moments(host)
+    ok = (m["count"] == r["count"] and abs(m["sd"] - r["sd"]) <= 1e-6 * r["sd"]
+          and np.array_equal(hist.cpu().numpy(), oracle.histogram(host, m["min"], m["max"], 256).astype(np.int64))
+          and float(med.item()) == oracle.median(host)[0])
+    res = {"workload": "stats_1024", "voxels": int(host.size), "bricked_bytes": bricked,
+           "moments": {"ms": t_m, "gb_per_s": bricked / t_m / 1e6, "frac": bricked / t_m / 1e6 / peak},
+           "histogram_256": {"ms": t_h, "gb_per_s": bricked / t_h / 1e6, "frac": bricked / t_h / 1e6 / peak},
+           "median_3_passes": {"ms": t_q, "gb_per_s": 3 * bricked / t_q / 1e6,
+                               "frac": 3 * bricked / t_q / 1e6 / peak},
+           "peak_gb_per_s": peak, "peak_source": src, "matches_oracle": bool(ok),
+           "values": {"mean": m["mean"], "sd": m["sd"], "median": float(med.item())}}
+    print(json.dumps(res))
+    vol.close()
+
+
 WORKLOADS = {"plain_128": run_plain_128, "precision_4096": run_precision_4096, "batch_64": run_batch_64,
              "diff_512": run_diff_512, "mip_1024": lambda a: run_modes_1024(a, "mip"),
-             "sigma_1024": lambda a: run_modes_1024(a, "sigma")}
+             "sigma_1024": lambda a: run_modes_1024(a, "sigma"), "stats_1024": run_stats_1024}
 
 
 def main():

@@ -313,6 +313,31 @@ vr_status vr_minimap(vr_volume_t vol, const int region[3], float *dev_minimap, v
 vr_status vr_profile(vr_volume_t vol, const vr_camera *cam, float step, int i, int j, float *dev_values,
                      uint32_t max_values, uint32_t *dev_count, void *cuda_stream);
 
+/* ------------------------------------------------------------------------
+ * Global statistics of the resident cube (Sections 4.1-4.3 of the paper).
+ * Each is one or a few streaming passes over the bricks, asynchronous on
+ * cuda_stream; every voxel counts once; NULL (NaN) voxels are left out.
+ * Outputs are caller-owned device memory, 8-byte aligned.
+ *
+ * vr_moments writes 5 doubles: the count of non-NaN voxels, their mean,
+ * population standard deviation, minimum and maximum (NaN without values).
+ * Sums as in Section 4.2: runs of 16 values in FP32, the runs in FP64, about
+ * a shift (the first voxel).
+ *
+ * vr_histogram writes nbins (1 .. 16384) uint64 counts of the values in
+ * [lo, hi] (finite, hi > lo) in equal bins, the value hi in the last bin;
+ * values outside are not counted (Section 4.1).
+ *
+ * vr_median writes 1 double: the value of rank (n + 1) / 2 (integer division,
+ * 1-based) among the n non-NaN voxels -- the median for odd n, the lower
+ * median for even n, the rank the paper's Torben method returns (Section
+ * 4.3) -- by a three-pass radix select (NaN without values).
+ * Errors: INVALID_ARG, OOM (first moments/median call), CUDA.
+ * ---------------------------------------------------------------------- */
+vr_status vr_moments(vr_volume_t vol, double *dev_out, void *cuda_stream);
+vr_status vr_histogram(vr_volume_t vol, double lo, double hi, int nbins, uint64_t *dev_counts, void *cuda_stream);
+vr_status vr_median(vr_volume_t vol, double *dev_median, void *cuda_stream);
+
 /* Synchronises cuda_stream and reports whether a bounded device-side wait of an
  * earlier call on this volume gave up (the staged kernels wait on the copy
  * engine with an iteration limit; a timeout leaves that call's results

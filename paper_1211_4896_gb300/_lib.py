@@ -56,7 +56,8 @@ class vr_batch_opts(C.Structure):
 # every symbol include/vr.h declares
 EXPORTS = ("vr_volume_create", "vr_volume_update", "vr_volume_destroy", "vr_volume_info", "vr_render",
            "vr_render_backward", "vr_render_batched", "vr_autotune_batched", "vr_render_batched_noalloc",
-           "vr_minimap", "vr_profile", "vr_check", "vr_last_error", "vr_version")
+           "vr_minimap", "vr_profile", "vr_moments", "vr_histogram", "vr_median", "vr_check", "vr_last_error",
+           "vr_version")
 VR_NOALLOC_MAX_JOBS = 256
 
 _lock = threading.Lock()
@@ -94,9 +95,13 @@ def load() -> C.CDLL:
         L.vr_check.argtypes = [vp, vp]
         L.vr_minimap.argtypes = [vp, P(C.c_int * 3), vp, vp]
         L.vr_profile.argtypes = [vp, P(vr_camera), C.c_float, C.c_int, C.c_int, vp, C.c_uint32, vp, vp]
+        L.vr_moments.argtypes = [vp, vp, vp]
+        L.vr_histogram.argtypes = [vp, C.c_double, C.c_double, C.c_int, vp, vp]
+        L.vr_median.argtypes = [vp, vp, vp]
         for name in ("vr_volume_create", "vr_volume_update", "vr_volume_destroy", "vr_volume_info", "vr_render",
                      "vr_render_backward", "vr_render_batched", "vr_autotune_batched",
-                     "vr_render_batched_noalloc", "vr_minimap", "vr_profile", "vr_check"):
+                     "vr_render_batched_noalloc", "vr_minimap", "vr_profile", "vr_moments", "vr_histogram",
+                     "vr_median", "vr_check"):
             getattr(L, name).restype = C.c_int
         L.vr_last_error.argtypes = []
         L.vr_last_error.restype = C.c_char_p
@@ -208,6 +213,18 @@ def vr_profile(vol: int, cam: vr_camera, step: float, i: int, j: int, dev_values
                dev_count: int, stream: int = 0):
     _check("vr_profile", load().vr_profile(vol, C.byref(cam), float(step), int(i), int(j), dev_values,
                                            int(max_values), dev_count, stream))
+
+
+def vr_moments(vol: int, dev_out: int, stream: int = 0):
+    _check("vr_moments", load().vr_moments(vol, dev_out, stream))
+
+
+def vr_histogram(vol: int, lo: float, hi: float, nbins: int, dev_counts: int, stream: int = 0):
+    _check("vr_histogram", load().vr_histogram(vol, float(lo), float(hi), int(nbins), dev_counts, stream))
+
+
+def vr_median(vol: int, dev_median: int, stream: int = 0):
+    _check("vr_median", load().vr_median(vol, dev_median, stream))
 
 
 def vr_check(vol: int, stream: int = 0):

@@ -140,6 +140,29 @@ def profile(vol: Volume, cam: dict, step: float, i: int, j: int, max_values: int
     return values[:n]
 
 
+def moments(vol: Volume, stream=None) -> dict:
+    """Count, mean, population standard deviation, minimum and maximum of the
+    non-NaN voxels (Section 4.2)."""
+    out = torch.empty(5, device=vol.device, dtype=torch.float64)
+    L.vr_moments(vol.handle, out.data_ptr(), _stream(stream))
+    v = out.cpu().tolist()
+    return dict(count=int(v[0]), mean=v[1], sd=v[2], min=v[3], max=v[4])
+
+
+def histogram(vol: Volume, lo: float, hi: float, nbins: int, stream=None) -> torch.Tensor:
+    """Counts of the voxel values in [lo, hi] in nbins equal bins (Section 4.1)."""
+    counts = torch.empty(int(nbins), device=vol.device, dtype=torch.int64)
+    L.vr_histogram(vol.handle, lo, hi, nbins, counts.data_ptr(), _stream(stream))
+    return counts
+
+
+def median(vol: Volume, stream=None) -> float:
+    """The value of rank (n + 1) // 2 among the n non-NaN voxels (Section 4.3)."""
+    out = torch.empty(1, device=vol.device, dtype=torch.float64)
+    L.vr_median(vol.handle, out.data_ptr(), _stream(stream))
+    return float(out.item())
+
+
 class RenderFunction(torch.autograd.Function):
     """Differentiable render: inputs (cube, tf), output the RGBA image.  The
     volume handle must hold the bricked copy of ``cube`` (call vol.update

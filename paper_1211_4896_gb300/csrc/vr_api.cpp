@@ -396,6 +396,7 @@ static void free_volume(vr_volume *vol)
     if (vol->bricks) cudaFree(vol->bricks);
     if (vol->dense) cudaFree(vol->dense);
     if (vol->wtab) cudaFree(vol->wtab);
+    if (vol->stats) cudaFree(vol->stats);
     for (void *o : vol->copies)
         if (o) cudaFree(o);
     if (vol->counters) cudaFree(vol->counters);
@@ -452,6 +453,10 @@ vr_status vr_volume_create(const void *dev_cube, vr_dtype src_dtype, vr_dtype st
     const long long b1 = brick + 1;
     vol->stride = (b1 * b1 * b1 + 63) / 64 * 64;                // 64-element (>=128 B) aligned bricks
     const long long nbricks = vol->nb[0] * vol->nb[1] * vol->nb[2];
+    if (nbricks >= (1LL << 31)) {
+        free_volume(vol);
+        return invalid("the volume needs 2^31 or more bricks");
+    }
     vol->bytes = (size_t)nbricks * (size_t)vol->stride * dtype_size(store_dtype);
     cudaError_t e = cudaGetDevice(&vol->device);
     if (e != cudaSuccess) { free_volume(vol); return cuda_fail(e, "cudaGetDevice"); }
@@ -674,6 +679,63 @@ vr_status vr_profile(vr_volume_t vol, const vr_camera *cam, float step, int i, i
     cudaError_t e = launch_profile(vol_dev(vol), vol->store_dtype, c, step, i, j, dev_values, max_values, dev_count,
                                    static_cast<cudaStream_t>(cuda_stream));
     if (e != cudaSuccess) return cuda_fail(e, "vr_profile launch");
+    return VR_OK;
+}
+
+static vr_status ensure_stats(vr_volume *vol)
+{
+    if (vol->stats) return VR_OK;
+    cudaError_t e = cudaMalloc(&vol->stats, stats_scratch_bytes());
+    if (e != cudaSuccess) {
+        vol->stats = nullptr;
+        return cuda_fail(e, "statistics scratch");
+    }
+    return VR_OK;
+}
+
+vr_status vr_moments(vr_volume_t vol, double *dev_out, void *cuda_stream)
+{
+    g_err.clear();
+    vr_status st = check_volume(vol);
+    if (st != VR_OK) return st;
+    if (!dev_out || (reinterpret_cast<uintptr_t>(dev_out) & 7u) != 0)
+        return invalid("dev_out must be non-NULL and 8-byte aligned");
+    st = ensure_stats(vol);
+    if (st != VR_OK) return st;
+    cudaError_t e = launch_moments(vol_dev(vol), vol->store_dtype, vol->stats, dev_out,
+                                   static_cast<cudaStream_t>(cuda_stream));
+    if (e != cudaSuccess) return cuda_fail(e, "vr_moments launch");
+    return VR_OK;
+}
+
+vr_status vr_histogram(vr_volume_t vol, double lo, double hi, int nbins, uint64_t *dev_counts, void *cuda_stream)
+{
+    g_err.clear();
+    vr_status st = check_volume(vol);
+    if (st != VR_OK) return st;
+    if (!std::isfinite(lo) || !std::isfinite(hi) || !(hi > lo)) return invalid("lo/hi must be finite with hi > lo");
+    if (nbins < 1 || nbins > 16384) return invalid("nbins must be in [1, 16384]");
+    if (!dev_counts || (reinterpret_cast<uintptr_t>(dev_counts) & 7u) != 0)
+        return invalid("dev_counts must be non-NULL and 8-byte aligned");
+    cudaError_t e = launch_histogram(vol_dev(vol), vol->store_dtype, lo, hi, nbins,
+                                     reinterpret_cast<unsigned long long *>(dev_counts),
+                                     static_cast<cudaStream_t>(cuda_stream));
+    if (e != cudaSuccess) return cuda_fail(e, "vr_histogram launch");
+    return VR_OK;
+}
+
+vr_status vr_median(vr_volume_t vol, double *dev_median, void *cuda_stream)
+{
+    g_err.clear();
+    vr_status st = check_volume(vol);
+    if (st != VR_OK) return st;
+    if (!dev_median || (reinterpret_cast<uintptr_t>(dev_median) & 7u) != 0)
+        return invalid("dev_median must be non-NULL and 8-byte aligned");
+    st = ensure_stats(vol);
+    if (st != VR_OK) return st;
+    cudaError_t e = launch_median(vol_dev(vol), vol->store_dtype, vol->stats, dev_median,
+                                  static_cast<cudaStream_t>(cuda_stream));
+    if (e != cudaSuccess) return cuda_fail(e, "vr_median launch");
     return VR_OK;
 }
 

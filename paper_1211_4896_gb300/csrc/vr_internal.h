@@ -91,6 +91,8 @@ struct vr_volume {
     void *dense = nullptr;
     int dense_px = 0;
     size_t dense_bytes = 0;
+    // scratch of the statistics passes (created on first use)
+    void *stats = nullptr;
     // hardware-filter copy (created on first texture-filter render)
     cudaArray_t tex_array = nullptr;
     cudaTextureObject_t tex = 0;
@@ -148,6 +150,12 @@ cudaError_t launch_sigma(const VolDev &v, vr_dtype dt, const CamDev &c, const Pa
 cudaError_t launch_minimap(const VolDev &v, vr_dtype dt, const int region[3], float *dev_out, cudaStream_t s);
 cudaError_t launch_profile(const VolDev &v, vr_dtype dt, const CamDev &c, float step, int i, int j, float *values,
                            unsigned max_values, unsigned *count, cudaStream_t s);
+// Global statistics (vr_stats.cu).
+size_t stats_scratch_bytes();
+cudaError_t launch_moments(const VolDev &v, vr_dtype dt, void *scratch, double *out, cudaStream_t s);
+cudaError_t launch_histogram(const VolDev &v, vr_dtype dt, double lo, double hi, int nbins,
+                             unsigned long long *counts, cudaStream_t s);
+cudaError_t launch_median(const VolDev &v, vr_dtype dt, void *scratch, double *median, cudaStream_t s);
 vr_status validate_job(const vr_job *job, int index);
 void purge_plans(const vr_volume *vol);
 

@@ -5,6 +5,7 @@
   python -m paper_1211_4896_gb300.profile_cases fwd16  # the same views of the cube stored as f16
   python -m paper_1211_4896_gb300.profile_cases bat    # the same 4 views in one batched call, f32
   python -m paper_1211_4896_gb300.profile_cases bwd    # 256^3 f32, 2 views at 512^2, step 0.5, table = ramp + 5% noise
+  python -m paper_1211_4896_gb300.profile_cases stats  # 512^3 f32: moments, 256-bin histogram, median (twice)
 
 The fwd/fwd16/bwd cases render each view forward then backward on cuda:0,
 so capture the kernel of interest with -k and -c.
@@ -70,8 +71,22 @@ def case_bwd():
     print("ok", int(ns.sum()))
 
 
+def case_stats():
+    import torch
+    import synth
+    import paper_1211_4896_gb300 as P
+    dev = torch.device("cuda")
+    vol = P.Volume(synth.hi_cube((512, 512, 512), 250, 25, 9, device=dev), "f32")
+    for _ in range(2):
+        m = P.moments(vol)
+        h = P.histogram(vol, m["min"], m["max"], 256)
+        med = P.median(vol)
+    torch.cuda.synchronize()
+    print("ok", m["count"], int(h.sum()), med)
+
+
 if __name__ == "__main__":
     from paper_1211_4896_gb300 import build
     build.build()
-    {"fwd": case_fwd, "fwd16": lambda: case_fwd("f16"), "bat": case_bat,
-     "bwd": case_bwd}[sys.argv[1] if len(sys.argv) > 1 else "fwd"]()
+    {"fwd": case_fwd, "fwd16": lambda: case_fwd("f16"), "bat": case_bat, "bwd": case_bwd,
+     "stats": case_stats}[sys.argv[1] if len(sys.argv) > 1 else "fwd"]()
