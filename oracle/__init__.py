@@ -87,6 +87,11 @@ def lib():
             L.orc_render_sigma.argtypes = [P(Volume), P(Camera), P(Params), C.c_void_p, P(C.c_int64 * 3),
                                            P(C.c_int * 3), C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_int]
             L.orc_render_sigma.restype = C.c_int
+            L.orc_render_subbox.argtypes = [P(Volume), P(Camera), P(Params), P(C.c_int64 * 3), P(C.c_int64 * 3),
+                                            C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]
+            L.orc_render_subbox.restype = C.c_int
+            L.orc_composite.argtypes = [C.c_int, C.c_void_p, C.c_void_p, C.c_int64, P(C.c_double * 4), C.c_void_p]
+            L.orc_composite.restype = None
             L.orc_moments.argtypes = [P(Volume), P(C.c_double * 5)]
             L.orc_moments.restype = C.c_int
             L.orc_histogram.argtypes = [P(Volume), C.c_double, C.c_double, C.c_int, C.c_void_p]
@@ -307,3 +312,37 @@ def median(cube, bits=None):
     if lib().orc_median(C.byref(c.vol), C.byref(m), C.byref(it)) != 0:
         raise ValueError("orc_median failed (no values)")
     return m.value, it.value
+
+
+def render_subbox(cube, cam, tf, vmin, vmax, step, lo, hi, rows=None, origin=(0.0, 0.0, 0.0),
+                  spacing=(1.0, 1.0, 1.0), bits=None):
+    """Sort-last partial render (Sections 3.2, 3.4) of the samples whose cell
+    lies in [lo, hi) (per axis x, y, z), at the whole volume's sample
+    positions: dict(partial (H,W,4) = premultiplied C and T, depth (H,W) =
+    ray parameter of the first sample or inf, count (H,W))."""
+    c = _Call(cube, cam, tf, vmin, vmax, step, 2.0, (0, 0, 0, 0), origin, spacing, bits)
+    H, W = c.cam.height, c.cam.width
+    part = np.zeros((H, W, 4))
+    part[..., 3] = 1.0
+    depth = np.full((H, W), np.inf)
+    count = np.zeros((H, W), np.int32)
+    r0, r1 = rows if rows is not None else (0, H)
+    rc = lib().orc_render_subbox(C.byref(c.vol), C.byref(c.cam), C.byref(c.par), C.byref((C.c_int64 * 3)(*lo)),
+                                 C.byref((C.c_int64 * 3)(*hi)), int(r0), int(r1), part.ctypes.data,
+                                 depth.ctypes.data, count.ctypes.data)
+    if rc != 0:
+        raise ValueError("orc_render_subbox failed")
+    return dict(partial=part, depth=depth, count=count)
+
+
+def composite(partials, depths, bg=(0.0, 0.0, 0.0, 0.0)):
+    """Over-composite of partial images in per-pixel depth order."""
+    ps = [np.ascontiguousarray(p, dtype=np.float64) for p in partials]
+    ds = [np.ascontiguousarray(d, dtype=np.float64) for d in depths]
+    k = len(ps)
+    H, W = ds[0].shape
+    out = np.zeros((H, W, 4))
+    pp = (C.c_void_p * k)(*[p.ctypes.data for p in ps])
+    dd = (C.c_void_p * k)(*[d.ctypes.data for d in ds])
+    lib().orc_composite(k, pp, dd, H * W, C.byref((C.c_double * 4)(*bg)), out.ctypes.data)
+    return out

@@ -959,3 +959,94 @@ int orc_median(const orc_volume *v, double *median, int *passes)
     if (passes) *passes = it;
     return 0;
 }
+
+/* ======================================================================== */
+/* Sort-last rendering of sub-boxes (Sections 3.2 and 3.4)                   */
+/* ======================================================================== */
+
+/* The paper splits the cube into sub-cubes, renders each on its own GPU and
+ * merges the sub-images in visibility order with the over operator.  Here a
+ * sub-box is a range of cells [lo, hi) per axis; a sample belongs to the
+ * sub-box holding its cell (the cell origin of the trilinear interpolation,
+ * clamp(floor(p), 0, n-2)), so every sample of a ray belongs to exactly one
+ * sub-box of a partition.  Samples sit at the positions of the whole volume's
+ * ray (the same t_in), so the sub-images composite to the whole render.
+ *
+ * Per pixel: the premultiplied partial colour C and transmittance T of the
+ * sub-box's samples (front to back, no early termination, no background),
+ * the ray parameter of its first sample (depth; +inf if none) and the count. */
+static void subbox_pixel(const orc_volume *v, const orc_camera *c, const basis *b, const orc_params *P,
+                         const int64_t lo[3], const int64_t hi[3], int i, int j, double out[4], double *depth,
+                         int32_t *count)
+{
+    ray_setup rs;
+    setup_ray(v, c, b, P, i, j, &rs);
+    double C[3] = {0.0, 0.0, 0.0}, T = 1.0, first = INFINITY;
+    int32_t used = 0;
+    for (int64_t k = 0; k < rs.n; ++k) {
+        double p[3];
+        sample_pos(&rs, P, k, p);
+        int inside = 1;
+        for (int a = 0; a < 3; ++a) {
+            int64_t x0 = (int64_t)floor(p[a]);
+            if (x0 < 0) x0 = 0;
+            if (x0 > v->n[a] - 2) x0 = v->n[a] - 2;
+            if (x0 < lo[a] || x0 >= hi[a]) inside = 0;
+        }
+        if (!inside) continue;
+        double rgba[4];
+        tf_lookup(P, trilinear(v, p, NULL), rgba, NULL);
+        double a = rgba[3];
+        for (int ch = 0; ch < 3; ++ch) C[ch] += T * a * rgba[ch];
+        T *= (1.0 - a);
+        if (used == 0) first = rs.t_in + ((double)k + 0.5) * P->step;
+        ++used;
+    }
+    out[0] = C[0]; out[1] = C[1]; out[2] = C[2]; out[3] = T;
+    if (depth) *depth = first;
+    if (count) *count = used;
+}
+
+/* Sub-box render of rows [row0, row1) (single thread; test sizes). */
+int orc_render_subbox(const orc_volume *v, const orc_camera *c, const orc_params *P, const int64_t lo[3],
+                      const int64_t hi[3], int row0, int row1, double *partial, double *depth, int32_t *count)
+{
+    if (check_args(v, c, P) || !partial) return -1;
+    basis b = camera_basis(c);
+    int W = c->width;
+    if (row0 < 0) row0 = 0;
+    if (row1 > c->height) row1 = c->height;
+    for (int j = row0; j < row1; ++j)
+        for (int i = 0; i < W; ++i) {
+            int64_t px = (int64_t)j * W + i;
+            subbox_pixel(v, c, &b, P, lo, hi, i, j, partial + 4 * px, depth ? depth + px : NULL,
+                         count ? count + px : NULL);
+        }
+    return 0;
+}
+
+/* Over-composite of k partial images per pixel in order of their depth
+ * (front first): C = C1 + T1 C2 + T1 T2 C3 + ..., T = T1 T2 ...; the pixel is
+ * (C + T bg.rgb, 1 - T + T bg.a).  partials[q] / depths[q] index pixel px at
+ * 4 px / px. */
+void orc_composite(int k, const double *const *partials, const double *const *depths, int64_t npx,
+                   const double bg[4], double *rgba)
+{
+    int *ord = (int *)malloc(sizeof(int) * (size_t)(k > 0 ? k : 1));
+    for (int64_t px = 0; px < npx; ++px) {
+        for (int q = 0; q < k; ++q) ord[q] = q;
+        for (int q = 1; q < k; ++q)                 /* insertion sort by depth */
+            for (int r = q; r > 0 && depths[ord[r]][px] < depths[ord[r - 1]][px]; --r) {
+                int t = ord[r]; ord[r] = ord[r - 1]; ord[r - 1] = t;
+            }
+        double C[3] = {0.0, 0.0, 0.0}, T = 1.0;
+        for (int q = 0; q < k; ++q) {
+            const double *s = partials[ord[q]] + 4 * px;
+            for (int ch = 0; ch < 3; ++ch) C[ch] += T * s[ch];
+            T *= s[3];
+        }
+        for (int ch = 0; ch < 3; ++ch) rgba[4 * px + ch] = C[ch] + T * bg[ch];
+        rgba[4 * px + 3] = 1.0 - T + T * bg[3];
+    }
+    free(ord);
+}
