@@ -737,9 +737,67 @@ def run_stats_1024(args):
     vol.close()
 
 
+def run_sortlast_1024(args):
+    """Sort-last rendering of the 1024^3 float32 cube split into 2x2x2
+    sub-boxes of cells (the paper's sub-cubes), eight 1080p orbit views, step 1,
+    no early termination: 8 sub-box renders + one depth-ordered composite per
+    view, against the whole render of the same views; pixel error of the
+    composite against the oracle on three rows of view 0."""
+    import torch
+    import oracle
+    import paper_1211_4896_gb300 as P
+    dev = torch.device("cuda")
+    pre = synth.preset_scale_1024()
+    cube = make_cube(pre, dev)
+    vol = P.Volume(cube, "f32")
+    host = cube.cpu().numpy()
+    del cube
+    torch.cuda.empty_cache()
+    tf_np = synth.tf_ramp(256)
+    tf = torch.from_numpy(tf_np).to(dev)
+    cams = pre["cameras"]
+    boxes = [((x, y, z), (x + 512, y + 512, z + 512)) for z in (0, 511) for y in (0, 511) for x in (0, 511)]
+    boxes = [(lo, tuple(min(h, 1023) for h in hi)) for lo, hi in boxes]
+    whole = [torch.empty((1080, 1920, 4), device=dev) for _ in cams]
+    nss = [torch.empty((1080, 1920), device=dev, dtype=torch.int32) for _ in cams]
+    outs = [torch.empty((1080, 1920, 4), device=dev) for _ in cams]
+    from paper_1211_4896_gb300 import _lib as L
+    s = int(torch.cuda.current_stream().cuda_stream)
+    parts = [[torch.empty((1080, 1920, 4), device=dev) for _ in boxes] for _ in cams]
+    depths = [[torch.empty((1080, 1920), device=dev) for _ in boxes] for _ in cams]
+    par = L.make_params(tf.data_ptr(), 256, synth.TF_VMIN, synth.TF_VMAX, 1.0, 2.0)
+
+    def f_whole():
+        for c, o, n in zip(cams, whole, nss):
+            P.render(vol, c, tf, synth.TF_VMIN, synth.TF_VMAX, 1.0, 2.0, out=o, nsamples=n)
+
+    def f_sort_last():
+        for v, c in enumerate(cams):
+            cc = L.make_camera(c)
+            for b, (lo, hi) in enumerate(boxes):
+                L.vr_render_subbox(vol.handle, cc, par, lo, hi, parts[v][b].data_ptr(), depths[v][b].data_ptr(),
+                                   None, s)
+            L.vr_composite([p.data_ptr() for p in parts[v]], [d.data_ptr() for d in depths[v]], 1920, 1080,
+                           (0, 0, 0, 0), outs[v].data_ptr(), s)
+    reps = max(3, args.steps)
+    t_whole = _time_ms(torch, f_whole, reps)
+    t_sl = _time_ms(torch, f_sort_last, reps)
+    samples = sum(int(n.sum()) for n in nss)
+    rows = [440, 540, 640]
+    ref = oracle.render(host, cams[0], tf_np, synth.TF_VMIN, synth.TF_VMAX, 1.0, 2.0, rows=(rows[0], rows[-1] + 1))
+    err = _px_err(outs[0].cpu().numpy(), nss[0].cpu().numpy(), ref, rows)
+    print(json.dumps({"workload": "sortlast_1024", "subboxes": len(boxes), "views": len(cams),
+                      "whole_ms_8_views": t_whole, "sort_last_ms_8_views": t_sl, "overhead": t_sl / t_whole,
+                      "samples": samples, "sort_last_gsamples_per_s": samples / t_sl / 1e6,
+                      "max_diff_vs_whole": float(max((o - w).abs().max().item() for o, w in zip(outs, whole))),
+                      "px_err": err}))
+    vol.close()
+
+
 WORKLOADS = {"plain_128": run_plain_128, "precision_4096": run_precision_4096, "batch_64": run_batch_64,
              "diff_512": run_diff_512, "mip_1024": lambda a: run_modes_1024(a, "mip"),
-             "sigma_1024": lambda a: run_modes_1024(a, "sigma"), "stats_1024": run_stats_1024}
+             "sigma_1024": lambda a: run_modes_1024(a, "sigma"), "stats_1024": run_stats_1024,
+             "sortlast_1024": run_sortlast_1024}
 
 
 def main():

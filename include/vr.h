@@ -314,6 +314,35 @@ vr_status vr_profile(vr_volume_t vol, const vr_camera *cam, float step, int i, i
                      uint32_t max_values, uint32_t *dev_count, void *cuda_stream);
 
 /* ------------------------------------------------------------------------
+ * Sort-last rendering (Sections 3.2 and 3.4: each GPU renders its sub-cube,
+ * the sub-images are merged in visibility order with the over operator).
+ *
+ * vr_render_subbox renders only the samples whose cell (the cell origin of
+ * the trilinear interpolation, clamp(floor(p), 0, n-2) per axis) lies in
+ * [cell_lo, cell_hi) -- cells, 0 <= cell_lo < cell_hi <= dims - 1 per axis --
+ * at the sample positions of the whole volume's ray, so that the sub-images
+ * of a partition of the cells composite to the whole render.  Per pixel it
+ * writes the partial composite to dev_partial (float4: premultiplied colour
+ * C.rgb and the transmittance T of these samples; (0, 0, 0, 1) when there are
+ * none), the distance of the first such sample from the eye (perspective) or
+ * the image plane (orthographic) to dev_depth (+inf when none) and, if
+ * dev_count is not NULL, their number.  No early termination,
+ * no background; composite mode, software filter.  Reads the brick copy the
+ * view prefers, like vr_render.
+ *
+ * vr_composite merges k (1 .. 64) such partial images of one view (host array
+ * of device pointers; width x height pixels each): per pixel in order of
+ * depth, front first, C = C1 + T1 C2 + T1 T2 C3 + ..., T = T1 T2 ...; writes
+ * (C + T bg.rgb, 1 - T + T bg.a) to dev_rgba_out.  All buffers caller-owned,
+ * float4 arrays 16-byte aligned.  Errors: INVALID_ARG, UNSUPPORTED, CUDA.
+ * ---------------------------------------------------------------------- */
+vr_status vr_render_subbox(vr_volume_t vol, const vr_camera *cam, const vr_params *params, const int cell_lo[3],
+                           const int cell_hi[3], float *dev_partial, float *dev_depth, uint32_t *dev_count,
+                           void *cuda_stream);
+vr_status vr_composite(int k, const float *const *dev_partials, const float *const *dev_depths, int width,
+                       int height, const float bg_rgba[4], float *dev_rgba_out, void *cuda_stream);
+
+/* ------------------------------------------------------------------------
  * Global statistics of the resident cube (Sections 4.1-4.3 of the paper).
  * Each is one or a few streaming passes over the bricks, asynchronous on
  * cuda_stream; every voxel counts once; NULL (NaN) voxels are left out.

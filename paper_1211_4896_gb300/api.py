@@ -140,6 +140,30 @@ def profile(vol: Volume, cam: dict, step: float, i: int, j: int, max_values: int
     return values[:n]
 
 
+def render_subbox(vol: Volume, cam: dict, tf: torch.Tensor, vmin: float, vmax: float, step: float, cell_lo, cell_hi,
+                  stream=None):
+    """Sort-last partial render of the cells [cell_lo, cell_hi) (x, y, z):
+    returns (partial (H, W, 4): premultiplied colour and transmittance,
+    depth (H, W): ray parameter of the first sample or inf, count (H, W))."""
+    H, W = int(cam["height"]), int(cam["width"])
+    partial = torch.empty((H, W, 4), device=vol.device, dtype=torch.float32)
+    depth = torch.empty((H, W), device=vol.device, dtype=torch.float32)
+    count = torch.empty((H, W), device=vol.device, dtype=torch.int32)
+    p = _params(tf, vmin, vmax, step, 2.0, (0.0, 0.0, 0.0, 0.0), L.VR_FILTER_SOFTWARE)
+    L.vr_render_subbox(vol.handle, L.make_camera(cam), p, cell_lo, cell_hi, partial.data_ptr(), depth.data_ptr(),
+                       count.data_ptr(), _stream(stream))
+    return partial, depth, count
+
+
+def composite(partials, depths, bg=(0.0, 0.0, 0.0, 0.0), stream=None) -> torch.Tensor:
+    """Over-composite of partial images (from render_subbox) in per-pixel depth order."""
+    H, W = depths[0].shape
+    out = torch.empty((H, W, 4), device=depths[0].device, dtype=torch.float32)
+    L.vr_composite([p.data_ptr() for p in partials], [d.data_ptr() for d in depths], W, H, bg, out.data_ptr(),
+                   _stream(stream))
+    return out
+
+
 def moments(vol: Volume, stream=None) -> dict:
     """Count, mean, population standard deviation, minimum and maximum of the
     non-NaN voxels (Section 4.2)."""

@@ -682,6 +682,64 @@ vr_status vr_profile(vr_volume_t vol, const vr_camera *cam, float step, int i, i
     return VR_OK;
 }
 
+vr_status vr_render_subbox(vr_volume_t vol, const vr_camera *cam, const vr_params *params, const int cell_lo[3],
+                           const int cell_hi[3], float *dev_partial, float *dev_depth, uint32_t *dev_count,
+                           void *cuda_stream)
+{
+    g_err.clear();
+    vr_status st = check_camera(cam);
+    if (st == VR_OK) st = check_params(params);
+    if (st == VR_OK) st = check_mode_path(params, "vr_render_subbox");
+    if (st != VR_OK) return st;
+    if (params->filter != VR_FILTER_SOFTWARE)
+        return (set_error("vr_render_subbox: software filter only"), VR_ERR_UNSUPPORTED);
+    st = check_volume(vol);
+    if (st == VR_OK) st = check_step(vol, params);
+    if (st != VR_OK) return st;
+    if (!cell_lo || !cell_hi) return invalid("cell_lo and cell_hi must not be NULL");
+    for (int a = 0; a < 3; ++a)
+        if (cell_lo[a] < 0 || cell_hi[a] > vol->dims[a] - 1 || cell_lo[a] >= cell_hi[a])
+            return invalid("need 0 <= cell_lo < cell_hi <= dims - 1 (cells) per axis");
+    if (!dev_partial || !is_aligned16(dev_partial)) return invalid("dev_partial must be non-NULL and 16-byte aligned");
+    if (!dev_depth || (reinterpret_cast<uintptr_t>(dev_depth) & 3u) != 0)
+        return invalid("dev_depth must be non-NULL and 4-byte aligned");
+    if ((reinterpret_cast<uintptr_t>(dev_count) & 3u) != 0) return invalid("dev_count must be 4-byte aligned");
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    CamDev c;
+    ParamDev p;
+    prepare_camera(vol, cam, &c);
+    prepare_params(params, &p);
+    unsigned *ctr;
+    next_counter(vol, &ctr);
+    cudaError_t e = launch_subbox(vol_dev_copy(vol, preferred_copy(vol, cam, true, s)), vol->store_dtype, c, p,
+                                  cell_lo, cell_hi, reinterpret_cast<float4 *>(dev_partial), dev_depth, dev_count,
+                                  ctr, s);
+    if (e != cudaSuccess) return cuda_fail(e, "vr_render_subbox launch");
+    return VR_OK;
+}
+
+vr_status vr_composite(int k, const float *const *dev_partials, const float *const *dev_depths, int width,
+                       int height, const float bg_rgba[4], float *dev_rgba_out, void *cuda_stream)
+{
+    g_err.clear();
+    if (k < 1 || k > kMaxPartials) return invalid("k must be in [1, " + std::to_string(kMaxPartials) + "]");
+    if (!dev_partials || !dev_depths) return invalid("dev_partials and dev_depths must not be NULL");
+    if (width < 1 || height < 1 || width > 32768 || height > 32768)
+        return invalid("width and height must be in [1, 32768]");
+    if (!bg_rgba) return invalid("bg_rgba is NULL");
+    for (int q = 0; q < k; ++q) {
+        if (!dev_partials[q] || !is_aligned16(dev_partials[q]))
+            return invalid("dev_partials[" + std::to_string(q) + "] must be non-NULL and 16-byte aligned");
+        if (!dev_depths[q] || (reinterpret_cast<uintptr_t>(dev_depths[q]) & 3u) != 0)
+            return invalid("dev_depths[" + std::to_string(q) + "] must be non-NULL and 4-byte aligned");
+    }
+    if (!dev_rgba_out || !is_aligned16(dev_rgba_out)) return invalid("dev_rgba_out must be non-NULL and 16-byte aligned");
+    cudaError_t e = launch_composite(k, dev_partials, dev_depths, (long long)width * height, bg_rgba, dev_rgba_out,
+                                     static_cast<cudaStream_t>(cuda_stream));
+    if (e != cudaSuccess) return cuda_fail(e, "vr_composite launch");
+    return VR_OK;
+}
+
 static vr_status ensure_stats(vr_volume *vol)
 {
     if (vol->stats) return VR_OK;

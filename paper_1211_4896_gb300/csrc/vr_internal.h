@@ -150,6 +150,13 @@ cudaError_t launch_sigma(const VolDev &v, vr_dtype dt, const CamDev &c, const Pa
 cudaError_t launch_minimap(const VolDev &v, vr_dtype dt, const int region[3], float *dev_out, cudaStream_t s);
 cudaError_t launch_profile(const VolDev &v, vr_dtype dt, const CamDev &c, float step, int i, int j, float *values,
                            unsigned max_values, unsigned *count, cudaStream_t s);
+// Sort-last sub-box render and depth-ordered composite (vr_modes.cu).
+constexpr int kMaxPartials = 64;
+cudaError_t launch_subbox(const VolDev &v, vr_dtype dt, const CamDev &c, const ParamDev &p, const int lo[3],
+                          const int hi[3], float4 *partial, float *depth, uint32_t *count, unsigned *counter,
+                          cudaStream_t s);
+cudaError_t launch_composite(int k, const float *const *partials, const float *const *depths, long long npx,
+                             const float bg[4], float *out, cudaStream_t s);
 // Global statistics (vr_stats.cu).
 size_t stats_scratch_bytes();
 cudaError_t launch_moments(const VolDev &v, vr_dtype dt, void *scratch, double *out, cudaStream_t s);

@@ -6,11 +6,14 @@
 //     and each sample value is scaled by the statistics interpolated at its
 //     position before the table lookup;
 //   - the 3D spectrum tool (Section 4.4): the data profile along one pixel's
-//     line of sight, at the renderer's sample positions.
+//     line of sight, at the renderer's sample positions;
+//   - sort-last rendering (Sections 3.2, 3.4): partial images of sub-boxes of
+//     cells, composited over one another in depth order.
 // Same camera, clipping, sampling, brick layouts and work queue as
 // vr_forward.cu.
 #include "vr_device.cuh"
 
+#include <algorithm>
 #include <cmath>
 
 namespace vr {
@@ -217,6 +220,189 @@ cudaError_t launch_sigma(const VolDev &v, vr_dtype dt, const CamDev &c, const Pa
             return cudaGetLastError();
         },
         cudaErrorInvalidValue);
+}
+
+// ---------------------------------------------------------------------------
+// Sort-last rendering (Sections 3.2 and 3.4): the samples of the whole
+// volume's ray whose cell lies in a sub-box [lo, hi) of cells, composited
+// into a partial image (premultiplied C, transmittance T, depth of the first
+// sample); partial images composite over one another in depth order.
+// ---------------------------------------------------------------------------
+
+// Ray parameters where the ray is inside [a, b] along one axis (intersected
+// into [s0, s1]); false when it misses.
+__device__ __forceinline__ bool slab_range(float q, float d, float a, float b, float &s0, float &s1)
+{
+    if (d == 0.0f) return q >= a && q <= b;
+    const float inv = 1.0f / d;
+    float t0 = (a - q) * inv, t1 = (b - q) * inv;
+    if (t0 > t1) {
+        const float t = t0;
+        t0 = t1;
+        t1 = t;
+    }
+    s0 = fmaxf(s0, t0);
+    s1 = fminf(s1, t1);
+    return s0 <= s1;
+}
+
+// Ray parameter of the eye (perspective) or of the image plane (orthographic)
+// in the units of Ray: depths are reported from there, like the oracle's t.
+__device__ __forceinline__ float eye_param(const CamDev &c, int i, int j)
+{
+    if (!c.persp) return -c.dist;
+    const float hi = (float)i - 0.5f * (float)(c.W - 1);
+    const float hj = (float)j - 0.5f * (float)(c.H - 1);
+    const float wx = fmaf(hi, c.wa.x, fmaf(hj, c.wb.x, c.wf.x));
+    const float wy = fmaf(hi, c.wa.y, fmaf(hj, c.wb.y, c.wf.y));
+    const float wz = fmaf(hi, c.wa.z, fmaf(hj, c.wb.z, c.wf.z));
+    return -c.dist * sqrtf(wx * wx + wy * wy + wz * wz);
+}
+
+template <typename T, int LOG2B, int L>
+__global__ void __launch_bounds__(kModeThreads) subbox_kernel(VolDev v, CamDev c, ParamDev p, int3 lo, int3 hi,
+                                                               float4 *partial, float *depth, uint32_t *count,
+                                                               unsigned *counter, int tiles_x, unsigned ntiles)
+{
+    const int lane = threadIdx.x & 31;
+    for (;;) {
+        unsigned tile = 0;
+        if (lane == 0) tile = atomicAdd(counter, 1u);
+        tile = __shfl_sync(kFull, tile, 0);
+        if (tile >= ntiles) break;
+        const int i = (int)(tile % tiles_x) * 8 + (lane & 7);
+        const int j = (int)(tile / tiles_x) * 4 + (lane >> 3);
+        const bool inside_img = i < c.W && j < c.H;
+        Ray ray;
+        bool active = inside_img && setup_ray(c, v.nx, v.ny, v.nz, p.step, i, j, ray);
+        // samples whose position lies in the sub-box widened by one voxel: the
+        // exact cell test below decides each of them
+        int k = 0, k_end = 0;
+        if (active) {
+            float s0 = -INFINITY, s1 = INFINITY;
+            active = slab_range(ray.q.x, ray.d.x, (float)lo.x - 1.0f, (float)hi.x + 1.0f, s0, s1) &&
+                     slab_range(ray.q.y, ray.d.y, (float)lo.y - 1.0f, (float)hi.y + 1.0f, s0, s1) &&
+                     slab_range(ray.q.z, ray.d.z, (float)lo.z - 1.0f, (float)hi.z + 1.0f, s0, s1);
+            if (active) {
+                const float k0 = floorf((s0 - ray.s_in) / p.step - 0.5f) - 1.0f;
+                const float k1 = ceilf((s1 - ray.s_in) / p.step - 0.5f) + 2.0f;
+                k = (int)fmaxf(k0, 0.0f);
+                k_end = (int)fminf(k1, (float)ray.n);
+                active = k < k_end;
+            }
+        }
+        float Cr = 0.0f, Cg = 0.0f, Cb = 0.0f, Tt = 1.0f;
+        int first = -1, used = 0;
+        Cell c0, c1;
+        Gathered<T, L> f0, f1;
+        if (active) {
+            c0 = locate<LOG2B, L>(v, sample_pos(ray, k, p.step));
+            fetch_corners<T, LOG2B, L>(v, c0, f0);
+        }
+        auto step = [&](const Cell &cur, const Gathered<T, L> &fc, Cell &nxt, Gathered<T, L> &fn) {
+            const bool more = k + 1 < k_end;
+            if (more) {
+                nxt = locate<LOG2B, L>(v, sample_pos(ray, k + 1, p.step));
+                fetch_corners<T, LOG2B, L>(v, nxt, fn);
+            }
+            if (cur.x0 >= lo.x && cur.x0 < hi.x && cur.y0 >= lo.y && cur.y0 < hi.y && cur.z0 >= lo.z &&
+                cur.z0 < hi.z) {
+                TfPos tp;
+                const float4 e = tf_lookup_l1(p, interp_corners(cur, fc), tp);
+                const float aT = e.w * Tt;
+                Cr = fmaf(aT, e.x, Cr);
+                Cg = fmaf(aT, e.y, Cg);
+                Cb = fmaf(aT, e.z, Cb);
+                Tt = fmaf(-e.w, Tt, Tt);
+                if (first < 0) first = k;
+                ++used;
+            }
+            ++k;
+            if (!more) active = false;
+        };
+        for (;;) {
+            if (!__any_sync(kFull, active)) break;
+            if (active) step(c0, f0, c1, f1);
+            if (!__any_sync(kFull, active)) break;
+            if (active) step(c1, f1, c0, f0);
+        }
+        if (!inside_img) continue;
+        const long long px = (long long)j * c.W + i;
+        partial[px] = make_float4(Cr, Cg, Cb, Tt);
+        depth[px] = first >= 0 ? fmaf((float)first + 0.5f, p.step, ray.s_in) - eye_param(c, i, j) : INFINITY;
+        if (count) count[px] = (uint32_t)used;
+    }
+}
+
+cudaError_t launch_subbox(const VolDev &v, vr_dtype dt, const CamDev &c, const ParamDev &p, const int lo[3],
+                          const int hi[3], float4 *partial, float *depth, uint32_t *count, unsigned *counter,
+                          cudaStream_t s)
+{
+    const int tiles_x = (c.W + 7) / 8, tiles_y = (c.H + 3) / 4;
+    const unsigned ntiles = (unsigned)tiles_x * (unsigned)tiles_y;
+    cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(unsigned), s);
+    if (e != cudaSuccess) return e;
+    const int3 l3 = make_int3(lo[0], lo[1], lo[2]), h3 = make_int3(hi[0], hi[1], hi[2]);
+    return visit_layout(
+        v, dt,
+        [&](auto lay) {
+            using Y = decltype(lay);
+            auto fn = subbox_kernel<typename Y::type, Y::log2b, Y::order>;
+            fn<<<persistent_grid(fn, ntiles), kModeThreads, 0, s>>>(v, c, p, l3, h3, partial, depth, count, counter,
+                                                                    tiles_x, ntiles);
+            return cudaGetLastError();
+        },
+        cudaErrorInvalidValue);
+}
+
+// Over-composite of k partial images per pixel, ordered by depth (front
+// first); the pixel is (C + T bg.rgb, 1 - T + T bg.a).
+struct PartialList {
+    const float4 *img[kMaxPartials];
+    const float *depth[kMaxPartials];
+};
+
+__global__ void __launch_bounds__(256) composite_kernel(PartialList pl, int k, long long npx, float4 bg,
+                                                         float4 *out)
+{
+    for (long long px = (long long)blockIdx.x * blockDim.x + threadIdx.x; px < npx;
+         px += (long long)gridDim.x * blockDim.x) {
+        float d[kMaxPartials];
+        unsigned char ord[kMaxPartials];
+        for (int q = 0; q < k; ++q) {
+            d[q] = pl.depth[q][px];
+            ord[q] = (unsigned char)q;
+        }
+        for (int q = 1; q < k; ++q)               // insertion sort by depth (stable)
+            for (int r = q; r > 0 && d[ord[r]] < d[ord[r - 1]]; --r) {
+                const unsigned char t = ord[r];
+                ord[r] = ord[r - 1];
+                ord[r - 1] = t;
+            }
+        float Cr = 0.0f, Cg = 0.0f, Cb = 0.0f, T = 1.0f;
+        for (int q = 0; q < k; ++q) {
+            const float4 s = pl.img[ord[q]][px];
+            Cr = fmaf(T, s.x, Cr);
+            Cg = fmaf(T, s.y, Cg);
+            Cb = fmaf(T, s.z, Cb);
+            T *= s.w;
+        }
+        out[px] = make_float4(fmaf(T, bg.x, Cr), fmaf(T, bg.y, Cg), fmaf(T, bg.z, Cb), fmaf(T, bg.w, 1.0f - T));
+    }
+}
+
+cudaError_t launch_composite(int k, const float *const *partials, const float *const *depths, long long npx,
+                             const float bg[4], float *out, cudaStream_t s)
+{
+    PartialList pl;
+    for (int q = 0; q < k; ++q) {
+        pl.img[q] = reinterpret_cast<const float4 *>(partials[q]);
+        pl.depth[q] = depths[q];
+    }
+    const long long blocks = std::min<long long>((npx + 255) / 256, (long long)sm_count() * 16);
+    composite_kernel<<<(unsigned)std::max<long long>(blocks, 1), 256, 0, s>>>(
+        pl, k, npx, make_float4(bg[0], bg[1], bg[2], bg[3]), reinterpret_cast<float4 *>(out));
+    return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------
