@@ -756,8 +756,8 @@ def run_sortlast_1024(args):
     tf_np = synth.tf_ramp(256)
     tf = torch.from_numpy(tf_np).to(dev)
     cams = pre["cameras"]
-    boxes = [((x, y, z), (x + 512, y + 512, z + 512)) for z in (0, 511) for y in (0, 511) for x in (0, 511)]
-    boxes = [(lo, tuple(min(h, 1023) for h in hi)) for lo, hi in boxes]
+    e = (0, 511, 1023)                        # 1023 cells per axis, split in two
+    boxes = [((e[x], e[y], e[z]), (e[x + 1], e[y + 1], e[z + 1])) for z in (0, 1) for y in (0, 1) for x in (0, 1)]
     whole = [torch.empty((1080, 1920, 4), device=dev) for _ in cams]
     nss = [torch.empty((1080, 1920), device=dev, dtype=torch.int32) for _ in cams]
     outs = [torch.empty((1080, 1920, 4), device=dev) for _ in cams]
