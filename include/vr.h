@@ -118,6 +118,12 @@ typedef struct {
     const float *minimap;     /* VR_MODE_SIGMA: device mini-map of vr_minimap for this volume and
                                    minimap_region, 8-byte aligned; otherwise ignored */
     int minimap_region[3];    /* VR_MODE_SIGMA: region size in voxels per axis, each >= 1 */
+    int skip_empty;           /* 1: skip the samples of bricks whose whole value range maps to
+                                   table entries of zero opacity (exact: such samples add nothing
+                                   and do not change T; images and sample counts are bit-identical
+                                   to skip_empty = 0).  Composite mode, VR_FILTER_SOFTWARE, vr_render
+                                   only; the first such call builds a per-brick value range
+                                   (8 bytes per brick) and synchronises cuda_stream. */
 } vr_params;
 
 typedef struct {

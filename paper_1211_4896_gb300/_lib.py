@@ -35,7 +35,8 @@ class vr_camera(C.Structure):
 class vr_params(C.Structure):
     _fields_ = [("tf_rgba", C.c_void_p), ("tf_size", C.c_int), ("vmin", C.c_float), ("vmax", C.c_float),
                 ("step", C.c_float), ("ert_threshold", C.c_float), ("bg_rgba", C.c_float * 4),
-                ("filter", C.c_int), ("mode", C.c_int), ("minimap", C.c_void_p), ("minimap_region", C.c_int * 3)]
+                ("filter", C.c_int), ("mode", C.c_int), ("minimap", C.c_void_p), ("minimap_region", C.c_int * 3),
+                ("skip_empty", C.c_int)]
 
 
 class vr_volume_info_t(C.Structure):
@@ -135,9 +136,10 @@ def make_camera(cam: dict) -> vr_camera:
 
 def make_params(tf_ptr: int, K: int, vmin: float, vmax: float, step: float, ert: float = 2.0,
                 bg=(0.0, 0.0, 0.0, 0.0), filter: int = VR_FILTER_SOFTWARE, mode: int = VR_MODE_COMPOSITE,
-                minimap_ptr: int | None = None, region=(1, 1, 1)) -> vr_params:
+                minimap_ptr: int | None = None, region=(1, 1, 1), skip_empty: bool = False) -> vr_params:
     return vr_params(tf_ptr, int(K), float(vmin), float(vmax), float(step), float(ert), (C.c_float * 4)(*bg),
-                     int(filter), int(mode), minimap_ptr, (C.c_int * 3)(*[int(r) for r in region]))
+                     int(filter), int(mode), minimap_ptr, (C.c_int * 3)(*[int(r) for r in region]),
+                     int(bool(skip_empty)))
 
 
 # ---------------------------------------------------------------------------

@@ -64,7 +64,7 @@ class Volume:
 
 
 def _params(tf: torch.Tensor, vmin, vmax, step, ert, bg, filter, mode=L.VR_MODE_COMPOSITE, minimap=None,
-            region=(1, 1, 1)):
+            region=(1, 1, 1), skip_empty=False):
     _need_cuda(tf, "tf")
     if tf.dtype != torch.float32 or tf.dim() != 2 or tf.shape[1] != 4:
         raise ValueError("tf must be a (K, 4) float32 CUDA tensor")
@@ -74,22 +74,25 @@ def _params(tf: torch.Tensor, vmin, vmax, step, ert, bg, filter, mode=L.VR_MODE_
             raise ValueError("mode VR_MODE_SIGMA needs the volume's minimap (see minimap())")
         _need_cuda(minimap, "minimap")
         mm = minimap.data_ptr()
-    return L.make_params(tf.data_ptr(), tf.shape[0], vmin, vmax, step, ert, bg, filter, mode, mm, region)
+    return L.make_params(tf.data_ptr(), tf.shape[0], vmin, vmax, step, ert, bg, filter, mode, mm, region,
+                         skip_empty)
 
 
 def render(vol: Volume, cam: dict, tf: torch.Tensor, vmin: float, vmax: float, step: float, ert: float = 2.0,
            bg=(0.0, 0.0, 0.0, 0.0), filter: int = L.VR_FILTER_SOFTWARE, want_nsamples: bool = True,
            out: torch.Tensor | None = None, nsamples: torch.Tensor | None = None, stream=None,
-           mode: int = L.VR_MODE_COMPOSITE, minimap: torch.Tensor | None = None, region=(1, 1, 1)):
+           mode: int = L.VR_MODE_COMPOSITE, minimap: torch.Tensor | None = None, region=(1, 1, 1),
+           skip_empty: bool = False):
     """Forward render; returns (rgba (H, W, 4) float32, nsamples (H, W) int32 or None).
     mode: VR_MODE_COMPOSITE, VR_MODE_MIP, or VR_MODE_SIGMA with the volume's
-    `minimap` (from minimap(vol, region)) and its `region`."""
+    `minimap` (from minimap(vol, region)) and its `region`.  skip_empty: skip
+    bricks that the table makes fully transparent (same result)."""
     H, W = int(cam["height"]), int(cam["width"])
     if out is None:
         out = torch.empty((H, W, 4), device=vol.device, dtype=torch.float32)
     if want_nsamples and nsamples is None:
         nsamples = torch.empty((H, W), device=vol.device, dtype=torch.int32)
-    p = _params(tf, vmin, vmax, step, ert, bg, filter, mode, minimap, region)
+    p = _params(tf, vmin, vmax, step, ert, bg, filter, mode, minimap, region, skip_empty)
     L.vr_render(vol.handle, L.make_camera(cam), p, out.data_ptr(),
                 nsamples.data_ptr() if (want_nsamples and nsamples is not None) else None, _stream(stream))
     return out, (nsamples if want_nsamples else None)

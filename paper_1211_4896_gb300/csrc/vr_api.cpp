@@ -397,6 +397,7 @@ static void free_volume(vr_volume *vol)
     if (vol->dense) cudaFree(vol->dense);
     if (vol->wtab) cudaFree(vol->wtab);
     if (vol->stats) cudaFree(vol->stats);
+    if (vol->brick_range) cudaFree(vol->brick_range);
     for (void *o : vol->copies)
         if (o) cudaFree(o);
     if (vol->counters) cudaFree(vol->counters);
@@ -499,6 +500,7 @@ vr_status vr_volume_update(vr_volume_t vol, const void *dev_cube, vr_dtype src_d
     cudaError_t e = launch_brick(dev_cube, src_dtype, vol, s);
     for (int c = 1; c < kCopyIds && e == cudaSuccess; ++c)
         if (vol->copies[c]) e = launch_copy(vol, c, s);
+    if (e == cudaSuccess && vol->brick_range) e = launch_brick_range(vol_dev(vol), vol->store_dtype, vol->brick_range, s);
     if (e == cudaSuccess && vol->dense) e = launch_densify(dev_cube, src_dtype, vol, s);
     if (e != cudaSuccess) return cuda_fail(e, "vr_volume_update");
     return VR_OK;
@@ -560,7 +562,28 @@ vr_status vr_render(vr_volume_t vol, const vr_camera *cam, const vr_params *para
     cudaError_t e;
     if (params->mode != VR_MODE_COMPOSITE && params->filter != VR_FILTER_SOFTWARE)
         return (set_error("vr_render: VR_MODE_MIP and VR_MODE_SIGMA need VR_FILTER_SOFTWARE"), VR_ERR_UNSUPPORTED);
-    if (params->mode == VR_MODE_MIP) {
+    if (params->skip_empty && (params->mode != VR_MODE_COMPOSITE || params->filter != VR_FILTER_SOFTWARE))
+        return (set_error("vr_render: skip_empty needs VR_MODE_COMPOSITE and VR_FILTER_SOFTWARE"),
+                VR_ERR_UNSUPPORTED);
+    if (params->skip_empty) {
+        if (!vol->brick_range) {
+            const size_t n = (size_t)(vol->nb[0] * vol->nb[1] * vol->nb[2]);
+            e = cudaMalloc(&vol->brick_range, n * sizeof(float2));
+            if (e != cudaSuccess) {
+                vol->brick_range = nullptr;
+                return cuda_fail(e, "vr_render: brick ranges");
+            }
+            e = launch_brick_range(vol_dev(vol), vol->store_dtype, vol->brick_range, s);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+            if (e != cudaSuccess) {
+                cudaFree(vol->brick_range);
+                vol->brick_range = nullptr;
+                return cuda_fail(e, "vr_render: brick ranges");
+            }
+        }
+        e = launch_forward_skip(vol_dev_copy(vol, preferred_copy(vol, cam, true, s)), vol->store_dtype, c, p,
+                                vol->brick_range, reinterpret_cast<float4 *>(dev_rgba_out), dev_nsamples_out, ctr, s);
+    } else if (params->mode == VR_MODE_MIP) {
         e = launch_mip(vol_dev_copy(vol, preferred_copy(vol, cam, true, s)), vol->store_dtype, c, p,
                        reinterpret_cast<float4 *>(dev_rgba_out), dev_nsamples_out, ctr, s);
     } else if (params->mode == VR_MODE_SIGMA) {

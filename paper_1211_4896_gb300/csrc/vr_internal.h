@@ -93,6 +93,8 @@ struct vr_volume {
     size_t dense_bytes = 0;
     // scratch of the statistics passes (created on first use)
     void *stats = nullptr;
+    // per-brick value range (min, max) for empty-space skipping (first use)
+    float2 *brick_range = nullptr;
     // hardware-filter copy (created on first texture-filter render)
     cudaArray_t tex_array = nullptr;
     cudaTextureObject_t tex = 0;
@@ -157,6 +159,11 @@ cudaError_t launch_subbox(const VolDev &v, vr_dtype dt, const CamDev &c, const P
                           cudaStream_t s);
 cudaError_t launch_composite(int k, const float *const *partials, const float *const *depths, long long npx,
                              const float bg[4], float *out, cudaStream_t s);
+// Empty-space skipping (vr_skip.cu).
+cudaError_t launch_brick_range(const VolDev &v, vr_dtype dt, float2 *range, cudaStream_t s);
+cudaError_t launch_forward_skip(const VolDev &v, vr_dtype dt, const CamDev &c, const ParamDev &p,
+                                const float2 *range, float4 *out, uint32_t *nsamples, unsigned *counter,
+                                cudaStream_t s);
 // Global statistics (vr_stats.cu).
 size_t stats_scratch_bytes();
 cudaError_t launch_moments(const VolDev &v, vr_dtype dt, void *scratch, double *out, cudaStream_t s);

@@ -6,6 +6,8 @@
   python -m paper_1211_4896_gb300.profile_cases bat    # the same 4 views in one batched call, f32
   python -m paper_1211_4896_gb300.profile_cases bwd    # 256^3 f32, 2 views at 512^2, step 0.5, table = ramp + 5% noise
   python -m paper_1211_4896_gb300.profile_cases stats  # 512^3 f32: moments, 256-bin histogram, median (twice)
+  python -m paper_1211_4896_gb300.profile_cases skip   # the fwd views with a table transparent below v = 6,
+                                                       # plain then with empty-space skipping
 
 The fwd/fwd16/bwd cases render each view forward then backward on cuda:0,
 so capture the kernel of interest with -k and -c.
@@ -71,6 +73,25 @@ def case_bwd():
     print("ok", int(ns.sum()))
 
 
+def case_skip():
+    import numpy as np
+    import torch
+    import synth
+    import paper_1211_4896_gb300 as P
+    dev = torch.device("cuda")
+    dims = (512, 512, 512)
+    vol = P.Volume(synth.hi_cube(dims, 250, 25, 9, device=dev), "f32")
+    v = -3.0 + 53.0 * np.arange(256) / 255
+    t = (v + 3.0) / 53.0
+    a = np.where(v < 6.0, 0.0, 0.02 + 0.2 * (v - 6.0) / 44.0)
+    tf = torch.from_numpy(np.stack([t, t * t, 1 - t, a], 1).astype(np.float32)).to(dev)
+    for flag in (False, True):
+        for c in synth.orbit_cameras(dims, 4, 40.0, 960, 540, start_deg=20.0):
+            img, ns = P.render(vol, c, tf, -3.0, 50.0, 1.0, 0.99, skip_empty=flag)
+    torch.cuda.synchronize()
+    print("ok", int(ns.sum()))
+
+
 def case_stats():
     import torch
     import synth
@@ -89,4 +110,4 @@ if __name__ == "__main__":
     from paper_1211_4896_gb300 import build
     build.build()
     {"fwd": case_fwd, "fwd16": lambda: case_fwd("f16"), "bat": case_bat, "bwd": case_bwd,
-     "stats": case_stats}[sys.argv[1] if len(sys.argv) > 1 else "fwd"]()
+     "stats": case_stats, "skip": case_skip}[sys.argv[1] if len(sys.argv) > 1 else "fwd"]()
