@@ -287,7 +287,7 @@ static cudaError_t launch_bwd_t(const VolDev &v, vr_volume *vol, const CamDev &c
 
 // Largest table the backward supports (the staged kernel keeps eight warps of
 // bins in shared memory).
-int backward_max_tf_size() { return (int)(200 * 1024 / (sizeof(float) * 4 * kBwdWarps)); }
+int backward_max_tf_size() { return (int)(200 * 1024 / (sizeof(float) * 4 * 8)); }
 
 cudaError_t launch_backward(const VolDev &v, vr_volume *vol, const CamDev &c, const ParamDev &p, const float4 *rgba,
                             const uint32_t *nsamples, const float4 *grad_rgba, double *grad_tf, float *grad_vox,
