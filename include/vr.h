@@ -381,6 +381,14 @@ vr_status vr_median(vr_volume_t vol, double *dev_median, void *cuda_stream);
  * failure detection. */
 vr_status vr_check(vr_volume_t vol, void *cuda_stream);
 
+/* Failure-detection self-test (no counterpart in the paper): enqueues on
+ * cuda_stream one wait, with the staged kernels' bounded mbarrier wait, on a
+ * barrier that nothing completes.  The wait gives up after 256 polls and
+ * records the timeout in the volume's status word, so the next vr_check
+ * returns VR_ERR_TIMEOUT (and clears it).  Nothing faults or hangs; the
+ * device stays usable.  Errors: INVALID_ARG, CUDA. */
+vr_status vr_selftest_timeout(vr_volume_t vol, void *cuda_stream);
+
 /* Human-readable message of the last failed call on this thread ("" if none). */
 const char *vr_last_error(void);
 

@@ -58,7 +58,7 @@ class vr_batch_opts(C.Structure):
 EXPORTS = ("vr_volume_create", "vr_volume_update", "vr_volume_destroy", "vr_volume_info", "vr_render",
            "vr_render_backward", "vr_render_batched", "vr_autotune_batched", "vr_render_batched_noalloc",
            "vr_minimap", "vr_profile", "vr_render_subbox", "vr_composite", "vr_moments", "vr_histogram",
-           "vr_median", "vr_check", "vr_last_error", "vr_version")
+           "vr_median", "vr_check", "vr_selftest_timeout", "vr_last_error", "vr_version")
 VR_NOALLOC_MAX_JOBS = 256
 
 _lock = threading.Lock()
@@ -94,6 +94,7 @@ def load() -> C.CDLL:
         L.vr_autotune_batched.argtypes = [P(vr_job), C.c_int, P(vr_batch_opts), vp]
         L.vr_render_batched_noalloc.argtypes = [P(vr_job), C.c_int, C.c_int, C.c_int, vp]
         L.vr_check.argtypes = [vp, vp]
+        L.vr_selftest_timeout.argtypes = [vp, vp]
         L.vr_minimap.argtypes = [vp, P(C.c_int * 3), vp, vp]
         L.vr_profile.argtypes = [vp, P(vr_camera), C.c_float, C.c_int, C.c_int, vp, C.c_uint32, vp, vp]
         L.vr_render_subbox.argtypes = [vp, P(vr_camera), P(vr_params), P(C.c_int * 3), P(C.c_int * 3), vp, vp, vp,
@@ -105,7 +106,7 @@ def load() -> C.CDLL:
         for name in ("vr_volume_create", "vr_volume_update", "vr_volume_destroy", "vr_volume_info", "vr_render",
                      "vr_render_backward", "vr_render_batched", "vr_autotune_batched",
                      "vr_render_batched_noalloc", "vr_minimap", "vr_profile", "vr_render_subbox", "vr_composite",
-                     "vr_moments", "vr_histogram", "vr_median", "vr_check"):
+                     "vr_moments", "vr_histogram", "vr_median", "vr_check", "vr_selftest_timeout"):
             getattr(L, name).restype = C.c_int
         L.vr_last_error.argtypes = []
         L.vr_last_error.restype = C.c_char_p
@@ -245,6 +246,10 @@ def vr_histogram(vol: int, lo: float, hi: float, nbins: int, dev_counts: int, st
 
 def vr_median(vol: int, dev_median: int, stream: int = 0):
     _check("vr_median", load().vr_median(vol, dev_median, stream))
+
+
+def vr_selftest_timeout(vol: int, stream: int = 0):
+    _check("vr_selftest_timeout", load().vr_selftest_timeout(vol, stream))
 
 
 def vr_check(vol: int, stream: int = 0):

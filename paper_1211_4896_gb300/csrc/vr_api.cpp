@@ -820,6 +820,16 @@ vr_status vr_median(vr_volume_t vol, double *dev_median, void *cuda_stream)
     return VR_OK;
 }
 
+vr_status vr_selftest_timeout(vr_volume_t vol, void *cuda_stream)
+{
+    g_err.clear();
+    vr_status st = check_volume(vol);
+    if (st != VR_OK) return st;
+    cudaError_t e = launch_wait_selftest(status_word(vol), static_cast<cudaStream_t>(cuda_stream));
+    if (e != cudaSuccess) return cuda_fail(e, "vr_selftest_timeout launch");
+    return VR_OK;
+}
+
 vr_status vr_check(vr_volume_t vol, void *cuda_stream)
 {
     g_err.clear();

@@ -144,6 +144,7 @@ cudaError_t launch_backward_staged(const DenseDev &d, vr_dtype dt, const CamDev 
                                    double *grad_tf, float *grad_vox, long long nvox, bool accumulate,
                                    unsigned *counter, unsigned *status, cudaStream_t s);
 int occupancy_blocks(const void *fn, int threads, size_t smem);
+cudaError_t launch_wait_selftest(unsigned *status, cudaStream_t s);
 // Other uses of the march (vr_modes.cu).
 cudaError_t launch_mip(const VolDev &v, vr_dtype dt, const CamDev &c, const ParamDev &p, float4 *out,
                        uint32_t *nsamples, unsigned *counter, cudaStream_t s);

@@ -69,17 +69,39 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, unsigned bytes)
 }
 
 // Waits for the phase of `bar` with the given parity; gives up after
-// kWaitSpins polls and records the timeout in *status.
-__device__ __forceinline__ void mbar_wait(uint64_t *bar, unsigned parity, unsigned *status)
+// `spins` polls and records the timeout in *status.
+__device__ __forceinline__ void mbar_wait(uint64_t *bar, unsigned parity, unsigned *status,
+                                          unsigned spins = kWaitSpins)
 {
     const unsigned a = smem_u32(bar);
-    for (unsigned spin = 0; spin < kWaitSpins; ++spin) {
+    for (unsigned spin = 0; spin < spins; ++spin) {
         unsigned done;
         asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
                      : "=r"(done) : "r"(a), "r"(parity) : "memory");
         if (done) return;
     }
     atomicOr(status, 1u);
+}
+
+// Failure-detection self-test: one thread waits, with the bounded wait of the
+// staged kernels, on a barrier that expects one arrival that never comes; the
+// wait gives up after `spins` polls and sets the status word.  Nothing faults
+// and no copy is in flight.
+__global__ void wait_selftest_kernel(unsigned *status, unsigned spins)
+{
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) mbar_init(&bar, 1);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        mbar_wait(&bar, 0u, status, spins);
+        asm volatile("mbarrier.inval.shared::cta.b64 [%0];\n" ::"r"(smem_u32(&bar)) : "memory");
+    }
+}
+
+cudaError_t launch_wait_selftest(unsigned *status, cudaStream_t s)
+{
+    wait_selftest_kernel<<<1, 32, 0, s>>>(status, 256u);
+    return cudaGetLastError();
 }
 
 __device__ __forceinline__ void bulk_copy(void *smem_dst, const void *gmem_src, unsigned bytes, uint64_t *bar)
