@@ -603,8 +603,9 @@ def run_batch_64(args):
 
 def run_diff_512(args):
     """512^3 f32, four 1024^2 views, step 0.5, no early termination: L2 loss
-    against targets rendered with a hidden table; forward and backward (table
-    and voxel gradients) per view, and their time ratio."""
+    against targets rendered with a hidden table; forward (one call per view)
+    and backward (table and voxel gradients; one call for the four views, and
+    one call per view), and their time ratio."""
     import torch
     import paper_1211_4896_gb300 as P
     dev = torch.device("cuda")
@@ -627,16 +628,24 @@ def run_diff_512(args):
         for c, o, n in zip(cams, outs, nss):
             P.render(vol, c, tf, synth.TF_VMIN, synth.TF_VMAX, pre["step"], 2.0, out=o, nsamples=n)
 
-    def bwd():
+    def bwd():              # the loss summed over the four views: one multi-view backward call
+        for o, g, t in zip(outs, grads, tgts):
+            torch.sub(o, t, out=g).mul_(2.0)
+        P.render_backward_views(vol, cams, tf, synth.TF_VMIN, synth.TF_VMAX, pre["step"], outs, nss, grads, 2.0,
+                                grad_tf=gtf, grad_vox=gvox)
+
+    def bwd_per_view():     # the same as one vr_render_backward call per view
         for v, (c, o, n, g, t) in enumerate(zip(cams, outs, nss, grads, tgts)):
             torch.sub(o, t, out=g).mul_(2.0)
             P.render_backward(vol, c, tf, synth.TF_VMIN, synth.TF_VMAX, pre["step"], o, n, g, 2.0, grad_tf=gtf,
                               grad_vox=gvox, accumulate=v > 0)
     t_f = _time_ms(torch, fwd, max(5, args.steps))
     t_b = _time_ms(torch, bwd, max(5, args.steps))
+    t_bv = _time_ms(torch, bwd_per_view, max(5, args.steps))
     samples = sum(int(n.sum()) for n in nss)
     print(json.dumps({"workload": "diff_512", "samples": samples, "fwd_ms_4_views": t_f, "bwd_ms_4_views": t_b,
-                      "bwd_over_fwd": t_b / t_f, "fwd_gsamples_per_s": samples / t_f / 1e6,
+                      "bwd_over_fwd": t_b / t_f, "bwd_ms_per_view_calls": t_bv, "bwd_per_view_calls_over_fwd":
+                      t_bv / t_f, "fwd_gsamples_per_s": samples / t_f / 1e6,
                       "fwd_bwd_gsamples_per_s": samples / (t_f + t_b) / 1e6}))
     vol.close()
 

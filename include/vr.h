@@ -206,23 +206,59 @@ vr_status vr_render(vr_volume_t vol, const vr_camera *cam, const vr_params *para
  * transmittance behind sample k is recovered from the final colour and
  * transmittance, T_final = (1 - alpha_out)/(1 - bg.a), so bg.a must be < 1.
  * Early-termination decisions of the forward are kept (dev_nsamples).
- *   dev_grad_tf  (K*4 float64): each warp sums one 32-ray tile in FP32
- *                shared-memory bins, then adds them to the output with FP64
- *                atomics (the final cross-block sum is the only FP64 step;
- *                its order is not deterministic).
- *   dev_grad_vox (nx*ny*nz float32 dense, x fastest) or NULL: float atomics
- *                (summation order is not deterministic).
+ *   dev_grad_tf  (K*4 float64): each warp accumulates its rays' terms in a
+ *                private FP32 row of K RGBA bins (16-byte vector reductions,
+ *                L2-resident); one final kernel sums the rows in FP64 (the
+ *                only FP64 step; the order of its atomics is not
+ *                deterministic).
+ *   dev_grad_vox (nx*ny*nz float32 dense, x fastest) or NULL: float
+ *                reductions (summation order is not deterministic), either
+ *                straight into dev_grad_vox or, where the view puts at least
+ *                one sample per voxel (ray pitch and step at the volume
+ *                centre), into a library-owned scratch of one float4 per
+ *                voxel (two 16-byte reductions per cell instead of four to
+ *                eight) that a gather pass then adds into dev_grad_vox.  The
+ *                scratch (16 bytes per voxel) is allocated on first use when
+ *                the stream is not being captured and an eighth of the
+ *                device memory stays free besides it; otherwise the direct
+ *                form runs.  VR_GRAD_DIRECT forces the direct form,
+ *                VR_GRAD_SCRATCH the scratch form (memory permitting); the
+ *                staged filter's backward always scatters directly.
  * Both are overwritten, or added to when flags has VR_GRAD_ACCUMULATE (a
  * loss summed over several views: call once per view).
- * Only software filtering is differentiable.  Errors: INVALID_ARG,
- * UNSUPPORTED (texture filter, bg.a >= 1, tf_size > 1600), CUDA.
+ * Only software filtering is differentiable.  Errors: INVALID_ARG (also
+ * VR_GRAD_DIRECT with VR_GRAD_SCRATCH), UNSUPPORTED (texture filter,
+ * bg.a >= 1, tf_size > 1600), CUDA.
  * ---------------------------------------------------------------------- */
-enum { VR_GRAD_ACCUMULATE = 1 };
+enum { VR_GRAD_ACCUMULATE = 1, VR_GRAD_DIRECT = 2, VR_GRAD_SCRATCH = 4 };
 
 vr_status vr_render_backward(vr_volume_t vol, const vr_camera *cam, const vr_params *params,
                              const float *dev_rgba, const uint32_t *dev_nsamples,
                              const float *dev_grad_rgba, double *dev_grad_tf, float *dev_grad_vox,
                              unsigned flags, void *cuda_stream);
+
+/* ------------------------------------------------------------------------
+ * Adjoint over several views at once: the gradients of L = sum over the n
+ * views of their losses (a table or volume fitted to several target
+ * renderings), equal to n vr_render_backward calls with VR_GRAD_ACCUMULATE
+ * after the first.  One call clears the outputs (unless VR_GRAD_ACCUMULATE),
+ * launches one backward kernel per view into the same per-warp table rows
+ * and voxel gradient, then runs the FP64 row sum and, with the quad scratch,
+ * its gather once for all views; the scratch is chosen from the views'
+ * summed sample density, with one quad orientation (the carry axis most
+ * views share).  views is a host array of n (1..4096) entries; each view's
+ * image, sample counts and dL/d(image) follow the rules of
+ * vr_render_backward.  Errors as vr_render_backward.
+ * ---------------------------------------------------------------------- */
+typedef struct {
+    vr_camera cam;
+    const float *rgba;            /* this view's forward image (W*H*4 float32, 16-byte aligned) */
+    const uint32_t *nsamples;     /* its sample counts (W*H, 4-byte aligned) */
+    const float *grad_rgba;       /* dL/d(image) for this view (W*H*4 float32, 16-byte aligned) */
+} vr_grad_view;
+
+vr_status vr_render_backward_views(vr_volume_t vol, const vr_grad_view *views, int n, const vr_params *params,
+                                   double *dev_grad_tf, float *dev_grad_vox, unsigned flags, void *cuda_stream);
 
 /* ------------------------------------------------------------------------
  * Batched render (not in the paper; its "many smaller cubes" future-work

@@ -19,7 +19,7 @@ VR_OK, VR_ERR_INVALID_ARG, VR_ERR_UNSUPPORTED, VR_ERR_OOM, VR_ERR_CUDA, VR_ERR_T
 VR_F32, VR_F16, VR_BF16 = 0, 1, 2
 VR_CAMERA_ORTHO, VR_CAMERA_PERSPECTIVE = 0, 1
 VR_FILTER_SOFTWARE, VR_FILTER_TEXTURE, VR_FILTER_SOFTWARE_STAGED = 0, 1, 2
-VR_GRAD_ACCUMULATE = 1
+VR_GRAD_ACCUMULATE, VR_GRAD_DIRECT, VR_GRAD_SCRATCH = 1, 2, 4
 VR_MODE_COMPOSITE, VR_MODE_MIP, VR_MODE_SIGMA = 0, 1, 2
 
 STATUS_NAMES = {0: "VR_OK", -1: "VR_ERR_INVALID_ARG", -2: "VR_ERR_UNSUPPORTED", -3: "VR_ERR_OOM",
@@ -50,13 +50,17 @@ class vr_job(C.Structure):
                 ("dev_rgba_out", C.c_void_p), ("dev_nsamples_out", C.c_void_p)]
 
 
+class vr_grad_view(C.Structure):
+    _fields_ = [("cam", vr_camera), ("rgba", C.c_void_p), ("nsamples", C.c_void_p), ("grad_rgba", C.c_void_p)]
+
+
 class vr_batch_opts(C.Structure):
     _fields_ = [("use_graph", C.c_int), ("tile_w", C.c_int), ("tile_h", C.c_int), ("ctas_per_sm", C.c_int)]
 
 
 # every symbol include/vr.h declares
 EXPORTS = ("vr_volume_create", "vr_volume_update", "vr_volume_destroy", "vr_volume_info", "vr_render",
-           "vr_render_backward", "vr_render_batched", "vr_autotune_batched", "vr_render_batched_noalloc",
+           "vr_render_backward", "vr_render_backward_views", "vr_render_batched", "vr_autotune_batched", "vr_render_batched_noalloc",
            "vr_minimap", "vr_profile", "vr_render_subbox", "vr_composite", "vr_moments", "vr_histogram",
            "vr_median", "vr_check", "vr_selftest_timeout", "vr_last_error", "vr_version")
 VR_NOALLOC_MAX_JOBS = 256
@@ -90,6 +94,7 @@ def load() -> C.CDLL:
         L.vr_volume_info.argtypes = [vp, P(vr_volume_info_t)]
         L.vr_render.argtypes = [vp, P(vr_camera), P(vr_params), vp, vp, vp]
         L.vr_render_backward.argtypes = [vp, P(vr_camera), P(vr_params), vp, vp, vp, vp, vp, C.c_uint, vp]
+        L.vr_render_backward_views.argtypes = [vp, P(vr_grad_view), C.c_int, P(vr_params), vp, vp, C.c_uint, vp]
         L.vr_render_batched.argtypes = [P(vr_job), C.c_int, P(vr_batch_opts), vp]
         L.vr_autotune_batched.argtypes = [P(vr_job), C.c_int, P(vr_batch_opts), vp]
         L.vr_render_batched_noalloc.argtypes = [P(vr_job), C.c_int, C.c_int, C.c_int, vp]
@@ -104,7 +109,7 @@ def load() -> C.CDLL:
         L.vr_histogram.argtypes = [vp, C.c_double, C.c_double, C.c_int, vp, vp]
         L.vr_median.argtypes = [vp, vp, vp]
         for name in ("vr_volume_create", "vr_volume_update", "vr_volume_destroy", "vr_volume_info", "vr_render",
-                     "vr_render_backward", "vr_render_batched", "vr_autotune_batched",
+                     "vr_render_backward", "vr_render_backward_views", "vr_render_batched", "vr_autotune_batched",
                      "vr_render_batched_noalloc", "vr_minimap", "vr_profile", "vr_render_subbox", "vr_composite",
                      "vr_moments", "vr_histogram", "vr_median", "vr_check", "vr_selftest_timeout"):
             getattr(L, name).restype = C.c_int
@@ -188,6 +193,16 @@ def vr_render_backward(vol: int, cam: vr_camera, params: vr_params, dev_rgba: in
     _check("vr_render_backward", load().vr_render_backward(vol, C.byref(cam), C.byref(params), dev_rgba,
                                                            dev_nsamples, dev_grad_rgba, dev_grad_tf,
                                                            dev_grad_vox, int(flags), stream))
+
+
+def vr_render_backward_views(vol: int, views, params: vr_params, dev_grad_tf: int, dev_grad_vox: int | None,
+                             flags: int = 0, stream: int = 0):
+    """views: a sequence of vr_grad_view (camera, image, sample counts and
+    dL/d(image) pointers of each view)."""
+    arr = (vr_grad_view * len(views))(*views)
+    _check("vr_render_backward_views", load().vr_render_backward_views(vol, arr, len(views), C.byref(params),
+                                                                       dev_grad_tf, dev_grad_vox, int(flags),
+                                                                       stream))
 
 
 def vr_render_batched(jobs, opts: vr_batch_opts | None = None, stream: int = 0):

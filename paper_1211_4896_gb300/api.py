@@ -100,8 +100,11 @@ def render(vol: Volume, cam: dict, tf: torch.Tensor, vmin: float, vmax: float, s
 
 def render_backward(vol: Volume, cam: dict, tf: torch.Tensor, vmin, vmax, step, rgba, nsamples, grad_rgba,
                     ert: float = 2.0, bg=(0.0, 0.0, 0.0, 0.0), want_vox: bool = True, grad_tf=None, grad_vox=None,
-                    accumulate: bool = False, filter: int = L.VR_FILTER_SOFTWARE, stream=None):
-    """Adjoint: returns (grad_tf (K, 4) float64, grad_vox (nz, ny, nx) float32 or None)."""
+                    accumulate: bool = False, filter: int = L.VR_FILTER_SOFTWARE, stream=None,
+                    vox_reduce: str | None = None):
+    """Adjoint: returns (grad_tf (K, 4) float64, grad_vox (nz, ny, nx) float32 or None).
+    vox_reduce: None (the library picks), "direct" (reductions straight into
+    grad_vox) or "scratch" (through the 16-byte-per-voxel quad scratch)."""
     for t, n in ((rgba, "rgba"), (nsamples, "nsamples"), (grad_rgba, "grad_rgba")):
         _need_cuda(t, n)
     if grad_tf is None:
@@ -111,7 +114,35 @@ def render_backward(vol: Volume, cam: dict, tf: torch.Tensor, vmin, vmax, step, 
     p = _params(tf, vmin, vmax, step, ert, bg, filter)
     L.vr_render_backward(vol.handle, L.make_camera(cam), p, rgba.data_ptr(), nsamples.data_ptr(),
                          grad_rgba.data_ptr(), grad_tf.data_ptr(), grad_vox.data_ptr() if want_vox else None,
-                         L.VR_GRAD_ACCUMULATE if accumulate else 0, _stream(stream))
+                         (L.VR_GRAD_ACCUMULATE if accumulate else 0) | _VOX_REDUCE[vox_reduce], _stream(stream))
+    return grad_tf, (grad_vox if want_vox else None)
+
+
+_VOX_REDUCE = {None: 0, "direct": L.VR_GRAD_DIRECT, "scratch": L.VR_GRAD_SCRATCH}
+
+
+def render_backward_views(vol: Volume, cams, tf: torch.Tensor, vmin, vmax, step, rgbas, nsamples, grad_rgbas,
+                          ert: float = 2.0, bg=(0.0, 0.0, 0.0, 0.0), want_vox: bool = True, grad_tf=None,
+                          grad_vox=None, accumulate: bool = False, filter: int = L.VR_FILTER_SOFTWARE, stream=None,
+                          vox_reduce: str | None = None):
+    """Adjoint of a loss summed over several views in one call: returns
+    (grad_tf (K, 4) float64, grad_vox (nz, ny, nx) float32 or None), equal to
+    render_backward per view with accumulate after the first."""
+    if not (len(cams) == len(rgbas) == len(nsamples) == len(grad_rgbas)) or not cams:
+        raise ValueError("cams, rgbas, nsamples and grad_rgbas must be non-empty and of equal length")
+    for q in range(len(cams)):
+        for t, n in ((rgbas[q], "rgbas"), (nsamples[q], "nsamples"), (grad_rgbas[q], "grad_rgbas")):
+            _need_cuda(t, n)
+    if grad_tf is None:
+        grad_tf = torch.empty(tuple(tf.shape), device=vol.device, dtype=torch.float64)
+    if want_vox and grad_vox is None:
+        grad_vox = torch.empty(vol.shape, device=vol.device, dtype=torch.float32)
+    views = [L.vr_grad_view(L.make_camera(c), r.data_ptr(), n.data_ptr(), g.data_ptr())
+             for c, r, n, g in zip(cams, rgbas, nsamples, grad_rgbas)]
+    p = _params(tf, vmin, vmax, step, ert, bg, filter)
+    L.vr_render_backward_views(vol.handle, views, p, grad_tf.data_ptr(), grad_vox.data_ptr() if want_vox else None,
+                               (L.VR_GRAD_ACCUMULATE if accumulate else 0) | _VOX_REDUCE[vox_reduce],
+                               _stream(stream))
     return grad_tf, (grad_vox if want_vox else None)
 
 

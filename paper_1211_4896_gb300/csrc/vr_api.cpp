@@ -6,6 +6,7 @@
 #include <mutex>
 #include <new>
 #include <string>
+#include <vector>
 
 #include "vr_internal.h"
 
@@ -324,6 +325,65 @@ int preferred_copy(vr_volume *vol, const vr_camera *cam, bool may_build, cudaStr
     return copy;
 }
 
+// Voxel-gradient scratch for a backward pass.  One 16-byte quad reduction per
+// plane of four corners replaces two to four scalar or pair reductions into
+// the dense gradient, at the cost of clearing and gathering 16 bytes per
+// voxel once per call; it pays where each voxel takes many samples: by
+// default where the call's views together put at least one sample per voxel,
+// estimated from the ray pitch and the step at the volume centre
+// (VR_GRAD_DIRECT / VR_GRAD_SCRATCH override it).  Created
+// on first use when the stream is not being captured and the device keeps an
+// eighth of its memory free besides it.
+static float4 *grad_quad_for(vr_volume *vol, const vr_grad_view *views, int n, const vr_params *params,
+                             unsigned flags, cudaStream_t s)
+{
+    if (flags & VR_GRAD_DIRECT) return nullptr;
+    if (!(flags & VR_GRAD_SCRATCH)) {
+        const double sp = (vol->spacing[0] + vol->spacing[1] + vol->spacing[2]) / 3.0;
+        const double unit[3] = {1.0, 0.0, 0.0};
+        const double step = params->step / sp;                                  // in voxels
+        double density = 0.0;                                                   // samples per voxel, all views
+        for (int q = 0; q < n; ++q) {
+            const double pitch = ray_pitch_voxels(vol, &views[q].cam, unit) * vol->spacing[0] / sp;   // in voxels
+            if (pitch > 0.0) density += 1.0 / (pitch * pitch * step);
+        }
+        if (!(density >= 1.0)) return nullptr;
+    }
+    if (vol->gquad) return vol->gquad;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    const size_t bytes = sizeof(float4) * (size_t)vol->dims[0] * (size_t)vol->dims[1] * (size_t)vol->dims[2];
+    size_t free_b = 0, total_b = 0;
+    if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess || free_b < bytes + total_b / 8) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    void *p = nullptr;
+    if (cudaMalloc(&p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    vol->gquad = static_cast<float4 *>(p);
+    return vol->gquad;
+}
+
+// Carry axis of the backward's voxel-gradient sums: the axis along which the
+// view direction (in voxel units) is longest, so that most of a ray's cell
+// steps move along it.
+static int carry_axis(const vr_volume *vol, const vr_camera *cam)
+{
+    int a = 0;
+    double best = -1.0;
+    for (int q = 0; q < 3; ++q) {
+        const double m = std::fabs(cam->forward[q] / vol->spacing[q]);
+        if (m > best) best = m, a = q;
+    }
+    return a;
+}
+
 // The last slot of the ring is the volume's device status word.
 vr_status next_counter(vr_volume *vol, unsigned **ctr)
 {
@@ -396,6 +456,7 @@ static void free_volume(vr_volume *vol)
     if (vol->bricks) cudaFree(vol->bricks);
     if (vol->dense) cudaFree(vol->dense);
     if (vol->wtab) cudaFree(vol->wtab);
+    if (vol->gquad) cudaFree(vol->gquad);
     if (vol->stats) cudaFree(vol->stats);
     if (vol->brick_range) cudaFree(vol->brick_range);
     for (void *o : vol->copies)
@@ -608,60 +669,106 @@ vr_status vr_render(vr_volume_t vol, const vr_camera *cam, const vr_params *para
     return VR_OK;
 }
 
-vr_status vr_render_backward(vr_volume_t vol, const vr_camera *cam, const vr_params *params, const float *dev_rgba,
-                             const uint32_t *dev_nsamples, const float *dev_grad_rgba, double *dev_grad_tf,
-                             float *dev_grad_vox, unsigned flags, void *cuda_stream)
+static vr_status backward_views(vr_volume_t vol, const vr_grad_view *views, int n, const vr_params *params,
+                                double *dev_grad_tf, float *dev_grad_vox, unsigned flags, void *cuda_stream,
+                                const char *who)
 {
     g_err.clear();
-    vr_status st = check_camera(cam);
-    if (st == VR_OK) st = check_params(params);
-    if (st == VR_OK) st = check_mode_path(params, "vr_render_backward");
+    if (n < 1 || !views) return invalid(std::string(who) + ": at least one view is required");
+    if (n > 4096) return invalid(std::string(who) + ": at most 4096 views per call");
+    vr_status st = check_params(params);
+    if (st == VR_OK) st = check_mode_path(params, who);
     if (st != VR_OK) return st;
+    for (int q = 0; q < n; ++q) {
+        st = check_camera(&views[q].cam);
+        if (st != VR_OK) return (n > 1 ? set_error("views[" + std::to_string(q) + "]: " + g_err) : void()), st;
+    }
     if (params->filter == VR_FILTER_TEXTURE)
-        return (set_error("vr_render_backward: only the software filters are differentiable"), VR_ERR_UNSUPPORTED);
+        return (set_error(std::string(who) + ": only the software filters are differentiable"), VR_ERR_UNSUPPORTED);
     if (!(params->bg_rgba[3] < 1.0f))
-        return (set_error("vr_render_backward: bg alpha must be < 1 (T_final is recovered from the output alpha)"),
+        return (set_error(std::string(who) + ": bg alpha must be < 1 (T_final is recovered from the output alpha)"),
                 VR_ERR_UNSUPPORTED);
-    if (!dev_rgba || !dev_nsamples || !dev_grad_rgba || !dev_grad_tf)
-        return invalid("dev_rgba, dev_nsamples, dev_grad_rgba and dev_grad_tf must not be NULL");
-    if (!is_aligned16(dev_rgba) || !is_aligned16(dev_grad_rgba))
-        return invalid("dev_rgba and dev_grad_rgba must be 16-byte aligned");
+    for (int q = 0; q < n; ++q) {
+        const vr_grad_view &w = views[q];
+        if (!w.rgba || !w.nsamples || !w.grad_rgba)
+            return invalid("dev_rgba, dev_nsamples and dev_grad_rgba must not be NULL");
+        if (!is_aligned16(w.rgba) || !is_aligned16(w.grad_rgba))
+            return invalid("dev_rgba and dev_grad_rgba must be 16-byte aligned");
+        if ((reinterpret_cast<uintptr_t>(w.nsamples) & 3u) != 0) return invalid("dev_nsamples must be 4-byte aligned");
+    }
+    if (!dev_grad_tf) return invalid("dev_grad_tf must not be NULL");
     if ((reinterpret_cast<uintptr_t>(dev_grad_tf) & 7u) != 0) return invalid("dev_grad_tf must be 8-byte aligned");
-    if (flags & ~(unsigned)VR_GRAD_ACCUMULATE) return invalid("flags: unknown bits");
+    if (flags & ~(unsigned)(VR_GRAD_ACCUMULATE | VR_GRAD_DIRECT | VR_GRAD_SCRATCH))
+        return invalid("flags: unknown bits");
+    if ((flags & VR_GRAD_DIRECT) && (flags & VR_GRAD_SCRATCH))
+        return invalid("flags: VR_GRAD_DIRECT and VR_GRAD_SCRATCH exclude each other");
     if (params->tf_size > backward_max_tf_size())
-        return (set_error("vr_render_backward: tf_size above " + std::to_string(backward_max_tf_size()) +
+        return (set_error(std::string(who) + ": tf_size above " + std::to_string(backward_max_tf_size()) +
                           " (per-warp gradient bins must fit in shared memory)"), VR_ERR_UNSUPPORTED);
-    if ((reinterpret_cast<uintptr_t>(dev_nsamples) & 3u) != 0 || (reinterpret_cast<uintptr_t>(dev_grad_vox) & 3u) != 0)
-        return invalid("dev_nsamples and dev_grad_vox must be 4-byte aligned");
+    if ((reinterpret_cast<uintptr_t>(dev_grad_vox) & 3u) != 0) return invalid("dev_grad_vox must be 4-byte aligned");
     st = check_volume(vol);
     if (st == VR_OK) st = check_step(vol, params);
     if (st != VR_OK) return st;
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
-    CamDev c;
     ParamDev p;
-    prepare_camera(vol, cam, &c);
     prepare_params(params, &p);
     const long long nvox = (long long)vol->dims[0] * vol->dims[1] * vol->dims[2];
     unsigned *ctr;
     next_counter(vol, &ctr);
     const bool acc = (flags & VR_GRAD_ACCUMULATE) != 0;
-    cudaError_t e;
+    cudaError_t e = cudaSuccess;
     if (params->filter == VR_FILTER_SOFTWARE_STAGED) {
         st = ensure_dense(vol, s);
         if (st != VR_OK) return st;
+        for (int q = 0; q < n && e == cudaSuccess; ++q) {
+            CamDev c;
+            prepare_camera(vol, &views[q].cam, &c);
+            e = launch_backward_staged(dense_dev(vol), vol->store_dtype, c, p,
+                                       reinterpret_cast<const float4 *>(views[q].rgba), views[q].nsamples,
+                                       reinterpret_cast<const float4 *>(views[q].grad_rgba), dev_grad_tf,
+                                       dev_grad_vox, nvox, acc || q > 0, ctr, status_word(vol), s);
+        }
+    } else {
+        std::vector<BwdView> bv((size_t)n);
+        int votes[3] = {0, 0, 0};
+        for (int q = 0; q < n; ++q) {
+            prepare_camera(vol, &views[q].cam, &bv[q].c);
+            bv[q].v = vol_dev_copy(vol, preferred_copy(vol, &views[q].cam, true, s));
+            bv[q].rgba = reinterpret_cast<const float4 *>(views[q].rgba);
+            bv[q].grad_rgba = reinterpret_cast<const float4 *>(views[q].grad_rgba);
+            bv[q].nsamples = views[q].nsamples;
+            bv[q].carry_axis = carry_axis(vol, &views[q].cam);
+            ++votes[bv[q].carry_axis];
+        }
+        const int quad_axis = votes[2] >= votes[0] && votes[2] >= votes[1] ? 2 : (votes[0] >= votes[1] ? 0 : 1);
+        float4 *quad = dev_grad_vox ? grad_quad_for(vol, views, n, params, flags, s) : nullptr;
+        e = launch_backward(vol, bv.data(), n, p, dev_grad_tf, dev_grad_vox, quad, quad_axis, nvox, acc, ctr, s);
     }
-    if (params->filter == VR_FILTER_SOFTWARE_STAGED)
-        e = launch_backward_staged(dense_dev(vol), vol->store_dtype, c, p, reinterpret_cast<const float4 *>(dev_rgba),
-                                   dev_nsamples, reinterpret_cast<const float4 *>(dev_grad_rgba), dev_grad_tf,
-                                   dev_grad_vox, nvox, acc, ctr, status_word(vol), s);
-    else
-        e = launch_backward(vol_dev_copy(vol, preferred_copy(vol, cam, true, s)), vol, c, p,
-                            reinterpret_cast<const float4 *>(dev_rgba),
-                            dev_nsamples,
-                            reinterpret_cast<const float4 *>(dev_grad_rgba), dev_grad_tf, dev_grad_vox, nvox, acc, ctr,
-                            s);
-    if (e != cudaSuccess) return cuda_fail(e, "vr_render_backward launch");
+    if (e != cudaSuccess) return cuda_fail(e, who);
     return VR_OK;
+}
+
+vr_status vr_render_backward(vr_volume_t vol, const vr_camera *cam, const vr_params *params, const float *dev_rgba,
+                             const uint32_t *dev_nsamples, const float *dev_grad_rgba, double *dev_grad_tf,
+                             float *dev_grad_vox, unsigned flags, void *cuda_stream)
+{
+    if (!cam) {
+        g_err.clear();
+        return invalid("camera is NULL");
+    }
+    vr_grad_view w;
+    w.cam = *cam;
+    w.rgba = dev_rgba;
+    w.nsamples = dev_nsamples;
+    w.grad_rgba = dev_grad_rgba;
+    return backward_views(vol, &w, 1, params, dev_grad_tf, dev_grad_vox, flags, cuda_stream, "vr_render_backward");
+}
+
+vr_status vr_render_backward_views(vr_volume_t vol, const vr_grad_view *views, int n, const vr_params *params,
+                                   double *dev_grad_tf, float *dev_grad_vox, unsigned flags, void *cuda_stream)
+{
+    return backward_views(vol, views, n, params, dev_grad_tf, dev_grad_vox, flags, cuda_stream,
+                          "vr_render_backward_views");
 }
 
 vr_status vr_minimap(vr_volume_t vol, const int region[3], float *dev_minimap, void *cuda_stream)

@@ -17,8 +17,16 @@
 // global memory (L2-resident); a sample adds its two weighted contributions
 // with two fire-and-forget 16-byte vector reductions.  One final kernel sums
 // the warps' rows in FP64 (the only FP64 arithmetic: the cross-block sum).
-// The voxel gradient is scattered into the dense layout with reductions, the
-// two x-neighbours of a corner pair as one 8-byte reduction when aligned.
+// The voxel gradient is scattered with reductions.  A ray's pending sums for
+// the eight corners of its current cell are kept as two planes of four
+// corners across the carry axis (the view's dominant axis); when the ray
+// steps to the next cell along that axis the shared plane is carried in
+// registers instead of being written, so a straight run writes one plane per
+// cell.  A plane goes either into the dense gradient (x-neighbour pairs as
+// 8-byte reductions when aligned) or, where many samples fall in each voxel,
+// into a quad scratch holding per voxel position the plane's four corners as
+// one float4 (one 16-byte reduction per plane); a gather pass then adds the
+// four quads that hold each voxel into the dense gradient.
 #include "vr_device.cuh"
 
 namespace vr {
@@ -40,24 +48,6 @@ __device__ __forceinline__ void red_add_v2(float *a, float x, float y)
 __device__ __forceinline__ void red_add_f32(float *a, float x)
 {
     asm volatile("red.global.add.f32 [%0], %1;\n" ::"l"(a), "f"(x) : "memory");
-}
-
-// dv distributed to the 8 corners of the cell whose (x0, y0, z0) corner is at gv.
-__device__ __forceinline__ void scatter_corners(float *gv, long long nx, long long nyx, float fx, float fy, float fz,
-                                                float dv)
-{
-    const float wx0 = 1.0f - fx, wy0 = 1.0f - fy, wz0 = 1.0f - fz;
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        const float a = ((q & 1) ? fy : wy0) * ((q & 2) ? fz : wz0) * dv;
-        float *b = gv + ((q & 1) ? nx : 0) + ((q & 2) ? nyx : 0);
-        if ((reinterpret_cast<uintptr_t>(b) & 7u) == 0) {
-            red_add_v2(b, wx0 * a, fx * a);
-        } else {
-            red_add_f32(b, wx0 * a);
-            red_add_f32(b + 1, fx * a);
-        }
-    }
 }
 
 __device__ __forceinline__ float4 f4_axpy(float a, float4 x, float4 y)
@@ -104,41 +94,78 @@ struct BinRun {
     }
 };
 
-// A ray's pending voxel-gradient contributions to the 8 corners of one cell.
+// Where the voxel gradient goes.  Axes u, v, w: w is the carry axis, u and
+// v the other two in x, y, z order; su, sv, sw their strides in the dense
+// layout.  quad (or NULL): the scratch, quad[i] = the corners i, i + su,
+// i + sv, i + su + sv of one plane.
+struct GradDev {
+    float *vox;
+    float4 *quad;
+    long long su, sv, sw;
+    int axis;
+};
+
+// A ray's pending voxel-gradient sums for the cell whose corner (x0, y0, z0)
+// has dense index idx: plane p0 at w0 and p1 at w0 + 1, each in corner order
+// (u, v) = (0, 0), (1, 0), (0, 1), (1, 1).
 struct CellRun {
-    float *base = nullptr;             // corner (x0, y0, z0) in the dense gradient
-    float acc[8];
-    __device__ __forceinline__ void add(float *gv, float fx, float fy, float fz, float dv, long long nx,
-                                        long long nyx)
+    long long idx = -1;
+    float p0[4], p1[4];
+    __device__ __forceinline__ void add(const GradDev &g, long long cell, float fu, float fv, float fw, float dv)
     {
-        if (gv != base) {
-            flush(nx, nyx);
-            base = gv;
+        if (cell != idx) {
+            if (idx >= 0 && cell == idx + g.sw) {            // step +1 along w: p1 becomes the new p0
+                plane(g, idx, p0);
 #pragma unroll
-            for (int q = 0; q < 8; ++q) acc[q] = 0.0f;
+                for (int q = 0; q < 4; ++q) p0[q] = p1[q], p1[q] = 0.0f;
+            } else if (idx >= 0 && cell == idx - g.sw) {     // step -1 along w: p0 becomes the new p1
+                plane(g, idx + g.sw, p1);
+#pragma unroll
+                for (int q = 0; q < 4; ++q) p1[q] = p0[q], p0[q] = 0.0f;
+            } else {
+                flush(g);
+#pragma unroll
+                for (int q = 0; q < 4; ++q) p0[q] = 0.0f, p1[q] = 0.0f;
+            }
+            idx = cell;
         }
-        const float wx0 = 1.0f - fx, wy0 = 1.0f - fy, wz0 = 1.0f - fz;
+        const float wu0 = 1.0f - fu, wv0 = 1.0f - fv;
+        const float d0 = (1.0f - fw) * dv, d1 = fw * dv;
+        const float c[4] = {wu0 * wv0, fu * wv0, wu0 * fv, fu * fv};
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-            const float a = ((q & 1) ? fy : wy0) * ((q & 2) ? fz : wz0) * dv;
-            acc[2 * q] = fmaf(wx0, a, acc[2 * q]);
-            acc[2 * q + 1] = fmaf(fx, a, acc[2 * q + 1]);
+            p0[q] = fmaf(c[q], d0, p0[q]);
+            p1[q] = fmaf(c[q], d1, p1[q]);
         }
     }
-    __device__ __forceinline__ void flush(long long nx, long long nyx)
+    __device__ __forceinline__ static void plane(const GradDev &g, long long base, const float (&p)[4])
     {
-        if (!base) return;
+        if (g.quad) {
+            red_add_v4(g.quad + base, make_float4(p[0], p[1], p[2], p[3]));
+        } else if (g.su == 1) {                               // (0,0)-(1,0) and (0,1)-(1,1) are x-neighbours
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            float *b = base + ((q & 1) ? nx : 0) + ((q & 2) ? nyx : 0);
-            if ((reinterpret_cast<uintptr_t>(b) & 7u) == 0) {
-                red_add_v2(b, acc[2 * q], acc[2 * q + 1]);
-            } else {
-                red_add_f32(b, acc[2 * q]);
-                red_add_f32(b + 1, acc[2 * q + 1]);
+            for (int h = 0; h < 2; ++h) {
+                float *b = g.vox + base + (h ? g.sv : 0);
+                if ((reinterpret_cast<uintptr_t>(b) & 7u) == 0) {
+                    red_add_v2(b, p[2 * h], p[2 * h + 1]);
+                } else {
+                    red_add_f32(b, p[2 * h]);
+                    red_add_f32(b + 1, p[2 * h + 1]);
+                }
             }
+        } else {
+            red_add_f32(g.vox + base, p[0]);
+            red_add_f32(g.vox + base + g.su, p[1]);
+            red_add_f32(g.vox + base + g.sv, p[2]);
+            red_add_f32(g.vox + base + g.su + g.sv, p[3]);
         }
-        base = nullptr;
+    }
+    __device__ __forceinline__ void flush(const GradDev &g)
+    {
+        if (idx < 0) return;
+        plane(g, idx, p0);
+        plane(g, idx + g.sw, p1);
+        idx = -1;
     }
 };
 
@@ -147,7 +174,7 @@ __global__ void __launch_bounds__(kBwdThreads) bwd_kernel(VolDev v, CamDev c, Pa
                                                            const float4 *__restrict__ rgba,
                                                            const uint32_t *__restrict__ nsamples,
                                                            const float4 *__restrict__ grad_rgba, float4 *wtab,
-                                                           float *grad_vox, unsigned *counter, int tiles_x,
+                                                           GradDev gd, unsigned *counter, int tiles_x,
                                                            unsigned ntiles)
 {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -209,11 +236,14 @@ __global__ void __launch_bounds__(kBwdThreads) bwd_kernel(VolDev v, CamDev c, Pa
             if (aT != 0.0f || da != 0.0f) {
                 const float4 dr = make_float4(aT * g.x, aT * g.y, aT * g.z, da);
                 bins.add(row, tp.i0, 1.0f - tp.w, tp.w, dr);
-                if (grad_vox && tp.interior) {
+                if (gd.vox && tp.interior) {
                     const float dv = (dr.x * de.x + dr.y * de.y + dr.z * de.z + dr.w * de.w) * vscale;
-                    if (dv != 0.0f)
-                        cells.add(grad_vox + ((long long)cell.z0 * nyx + (long long)cell.y0 * v.nx + cell.x0),
-                                  cell.fx, cell.fy, cell.fz, dv, v.nx, nyx);
+                    if (dv != 0.0f) {
+                        const float fu = gd.axis == 0 ? cell.fy : cell.fx;
+                        const float fv = gd.axis == 2 ? cell.fy : cell.fz;
+                        const float fw = gd.axis == 0 ? cell.fx : (gd.axis == 1 ? cell.fy : cell.fz);
+                        cells.add(gd, (long long)cell.z0 * nyx + (long long)cell.y0 * v.nx + cell.x0, fu, fv, fw, dv);
+                    }
                 }
             }
             T = fmaf(-a, T, T);
@@ -233,7 +263,32 @@ __global__ void __launch_bounds__(kBwdThreads) bwd_kernel(VolDev v, CamDev c, Pa
             if (active) step(c1, f1, c0, f0);
         }
         bins.flush(row);
-        cells.flush(v.nx, nyx);
+        cells.flush(gd);
+    }
+}
+
+// Dense voxel gradient from the quad scratch: the voxel at (u, v) of its
+// plane is corner (0, 0) of quad (u, v), (1, 0) of (u-1, v), (0, 1) of
+// (u, v-1) and (1, 1) of (u-1, v-1).  Quads at u = nu-1 or v = nv-1 are never
+// written and stay zero.  One CTA per (y, z) row.
+__global__ void __launch_bounds__(256) quad_gather(const float4 *__restrict__ quad, float *grad_vox, int nx, int ny,
+                                                    int axis, int accumulate)
+{
+    const unsigned row = blockIdx.x;                       // z * ny + y
+    const int y = (int)(row % (unsigned)ny);
+    const int z = (int)(row / (unsigned)ny);
+    const long long base = (long long)row * nx, nyx = (long long)nx * ny;
+    const long long su = axis == 0 ? nx : 1, sv = axis == 2 ? nx : nyx;
+    for (int x = threadIdx.x; x < nx; x += blockDim.x) {
+        const long long q = base + x;
+        const bool u1 = (axis == 0 ? y : x) > 0, v1 = (axis == 2 ? y : z) > 0;
+        float s = __ldg(&quad[q].x);
+        if (u1) s += __ldg(&quad[q - su].y);
+        if (v1) {
+            s += __ldg(&quad[q - sv].z);
+            if (u1) s += __ldg(&quad[q - su - sv].w);
+        }
+        grad_vox[q] = accumulate ? grad_vox[q] + s : s;
     }
 }
 
@@ -249,59 +304,112 @@ __global__ void __launch_bounds__(256) reduce_rows(const float *__restrict__ row
     atomicAdd(out + q, acc);
 }
 
-template <typename T, int LOG2B, int L>
-static cudaError_t launch_bwd_t(const VolDev &v, vr_volume *vol, const CamDev &c, const ParamDev &p, const float4 *rgba,
-                                const uint32_t *nsamples, const float4 *grad_rgba, double *grad_tf, float *grad_vox,
-                                long long nvox, bool accumulate, unsigned *counter, cudaStream_t s)
+static GradDev grad_dev(const VolDev &v, float *grad_vox, float4 *grad_quad, int axis)
 {
-    auto fn = bwd_kernel<T, LOG2B, L>;
-    const int tiles_x = (c.W + 7) / 8, tiles_y = (c.H + 3) / 4;
-    const unsigned ntiles = (unsigned)tiles_x * (unsigned)tiles_y;
-    const int per_sm = occupancy_blocks((const void *)fn, kBwdThreads, 0);
-    unsigned grid = (unsigned)(per_sm * sm_count());
+    const long long nx = v.nx, nyx = (long long)v.nx * v.ny;
+    GradDev gd;
+    gd.vox = grad_vox;
+    gd.quad = grad_quad;
+    gd.axis = axis;
+    gd.su = axis == 0 ? nx : 1;
+    gd.sv = axis == 2 ? nx : nyx;
+    gd.sw = axis == 0 ? 1 : (axis == 1 ? nx : nyx);
+    return gd;
+}
+
+// Persistent grid of one view's backward kernel: the resident CTAs, but no
+// more than its tiles need.
+static unsigned view_grid(const void *fn, const CamDev &c)
+{
+    const unsigned ntiles = (unsigned)((c.W + 7) / 8) * (unsigned)((c.H + 3) / 4);
+    unsigned grid = (unsigned)(occupancy_blocks(fn, kBwdThreads, 0) * sm_count());
     const unsigned max_useful = (ntiles + kBwdWarps - 1) / kBwdWarps;
     if (grid > max_useful) grid = max_useful;
-    if (grid < 1) grid = 1;
-    const int nrows = (int)grid * kBwdWarps;
+    return grid < 1 ? 1 : grid;
+}
+
+static cudaError_t view_kernel(const BwdView &bv, vr_dtype dt, const void **fn_out)
+{
+    return visit_layout(
+        bv.v, dt,
+        [&](auto lay) {
+            using Y = decltype(lay);
+            *fn_out = (const void *)bwd_kernel<typename Y::type, Y::log2b, Y::order>;
+            return cudaSuccess;
+        },
+        cudaErrorInvalidValue);
+}
+
+// The backward of a loss summed over n views: every view's kernel adds into
+// the same per-warp table rows and voxel gradient, then one FP64 row sum and
+// (with the quad scratch) one gather finish all of them.
+cudaError_t launch_backward(vr_volume *vol, const BwdView *views, int n, const ParamDev &p, double *grad_tf,
+                            float *grad_vox, float4 *grad_quad, int quad_axis, long long nvox, bool accumulate,
+                            unsigned *counter, cudaStream_t s)
+{
+    const vr_dtype dt = vol->store_dtype;
+    unsigned max_grid = 1;
+    for (int q = 0; q < n; ++q) {
+        const void *fn = nullptr;
+        cudaError_t e = view_kernel(views[q], dt, &fn);
+        if (e != cudaSuccess) return e;
+        const unsigned g = view_grid(fn, views[q].c);
+        if (g > max_grid) max_grid = g;
+    }
+    const int nrows = (int)max_grid * kBwdWarps;
     const size_t need = (size_t)nrows * 4 * (size_t)p.K;          // floats
     cudaError_t e = ensure_wtab(vol, need, s);
     if (e != cudaSuccess) return e;
     e = cudaMemsetAsync(vol->wtab, 0, need * sizeof(float), s);
     if (e != cudaSuccess) return e;
+    if (!grad_vox) grad_quad = nullptr;
     if (!accumulate) {
         e = cudaMemsetAsync(grad_tf, 0, sizeof(double) * 4 * (size_t)p.K, s);
-        if (e == cudaSuccess && grad_vox) e = cudaMemsetAsync(grad_vox, 0, sizeof(float) * (size_t)nvox, s);
+        if (e == cudaSuccess && grad_vox && !grad_quad)
+            e = cudaMemsetAsync(grad_vox, 0, sizeof(float) * (size_t)nvox, s);
         if (e != cudaSuccess) return e;
     }
-    e = cudaMemsetAsync(counter, 0, sizeof(unsigned), s);
-    if (e != cudaSuccess) return e;
-    fn<<<grid, kBwdThreads, 0, s>>>(v, c, p, rgba, nsamples, grad_rgba,
-                                    reinterpret_cast<float4 *>(vol->wtab), grad_vox, counter, tiles_x, ntiles);
+    if (grad_quad) {
+        e = cudaMemsetAsync(grad_quad, 0, sizeof(float4) * (size_t)nvox, s);
+        if (e != cudaSuccess) return e;
+    }
+    float4 *wtab = reinterpret_cast<float4 *>(vol->wtab);
+    for (int q = 0; q < n; ++q) {
+        const BwdView &bv = views[q];
+        // direct reductions carry along each view's own axis; the quads have one
+        // orientation for the whole call
+        const GradDev gd = grad_dev(bv.v, grad_vox, grad_quad, grad_quad ? quad_axis : bv.carry_axis);
+        const int tiles_x = (bv.c.W + 7) / 8;
+        const unsigned ntiles = (unsigned)tiles_x * (unsigned)((bv.c.H + 3) / 4);
+        e = cudaMemsetAsync(counter, 0, sizeof(unsigned), s);
+        if (e != cudaSuccess) return e;
+        e = visit_layout(
+            bv.v, dt,
+            [&](auto lay) {
+                using Y = decltype(lay);
+                auto fn = bwd_kernel<typename Y::type, Y::log2b, Y::order>;
+                fn<<<view_grid((const void *)fn, bv.c), kBwdThreads, 0, s>>>(bv.v, bv.c, p, bv.rgba, bv.nsamples,
+                                                                            bv.grad_rgba, wtab, gd, counter,
+                                                                            tiles_x, ntiles);
+                return cudaGetLastError();
+            },
+            cudaErrorInvalidValue);
+        if (e != cudaSuccess) return e;
+    }
+    const int nb = 4 * p.K, chunk = 64;
+    dim3 rgrid((unsigned)((nb + 255) / 256), (unsigned)((nrows + chunk - 1) / chunk));
+    reduce_rows<<<rgrid, 256, 0, s>>>(vol->wtab, nrows, nb, grad_tf, chunk);
     e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    const int n = 4 * p.K, chunk = 64;
-    dim3 rgrid((unsigned)((n + 255) / 256), (unsigned)((nrows + chunk - 1) / chunk));
-    reduce_rows<<<rgrid, 256, 0, s>>>(vol->wtab, nrows, n, grad_tf, chunk);
+    if (e != cudaSuccess || !grad_quad) return e;
+    const VolDev &v = views[0].v;
+    const unsigned rows = (unsigned)((long long)v.ny * v.nz);
+    const unsigned threads = v.nx >= 256 ? 256u : (unsigned)((v.nx + 31) / 32 * 32);
+    quad_gather<<<rows, threads, 0, s>>>(grad_quad, grad_vox, v.nx, v.ny, quad_axis, accumulate ? 1 : 0);
     return cudaGetLastError();
 }
 
 // Largest table the backward supports (the staged kernel keeps eight warps of
 // bins in shared memory).
 int backward_max_tf_size() { return (int)(200 * 1024 / (sizeof(float) * 4 * 8)); }
-
-cudaError_t launch_backward(const VolDev &v, vr_volume *vol, const CamDev &c, const ParamDev &p, const float4 *rgba,
-                            const uint32_t *nsamples, const float4 *grad_rgba, double *grad_tf, float *grad_vox,
-                            long long nvox, bool accumulate, unsigned *counter, cudaStream_t s)
-{
-    return visit_layout(
-        v, vol->store_dtype,
-        [&](auto lay) {
-            using Y = decltype(lay);
-            return launch_bwd_t<typename Y::type, Y::log2b, Y::order>(v, vol, c, p, rgba, nsamples, grad_rgba,
-                                                                       grad_tf, grad_vox, nvox, accumulate, counter,
-                                                                       s);
-        },
-        cudaErrorInvalidValue);
-}
 
 }  // namespace vr

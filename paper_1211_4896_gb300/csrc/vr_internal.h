@@ -87,6 +87,9 @@ struct vr_volume {
     // backward scratch: one FP32 row of K RGBA gradient bins per warp
     float *wtab = nullptr;
     size_t wtab_cap = 0;         // floats
+    // backward scratch: the voxel-gradient quads (one float4 per voxel),
+    // created on the first backward whose rays are dense enough to use it
+    float4 *gquad = nullptr;
     // dense padded copy used by the shared-memory staged kernels
     void *dense = nullptr;
     int dense_px = 0;
@@ -129,9 +132,19 @@ VolDev vol_dev_copy(const vr_volume *vol, int copy);
 int preferred_copy(vr_volume *vol, const vr_camera *cam, bool may_build, cudaStream_t s);
 size_t copy_bytes(const vr_volume *vol, int copy);
 cudaError_t launch_copy(vr_volume *vol, int copy, cudaStream_t s);
-cudaError_t launch_backward(const VolDev &v, vr_volume *vol, const CamDev &c, const ParamDev &p, const float4 *rgba,
-                            const uint32_t *nsamples, const float4 *grad_rgba, double *grad_tf, float *grad_vox,
-                            long long nvox, bool accumulate, unsigned *counter, cudaStream_t s);
+// One view of a backward call: the layout it reads (a brick copy or the
+// bricks), its camera, the forward's image and sample counts, dL/d(image),
+// and the axis along which its direct voxel-gradient sums are carried.
+struct BwdView {
+    VolDev v;
+    CamDev c;
+    const float4 *rgba, *grad_rgba;
+    const uint32_t *nsamples;
+    int carry_axis;
+};
+cudaError_t launch_backward(vr_volume *vol, const BwdView *views, int n, const ParamDev &p, double *grad_tf,
+                            float *grad_vox, float4 *grad_quad, int quad_axis, long long nvox, bool accumulate,
+                            unsigned *counter, cudaStream_t s);
 cudaError_t ensure_wtab(vr_volume *vol, size_t floats, cudaStream_t s);
 int backward_max_tf_size();
 DenseDev dense_dev(const vr_volume *vol);

@@ -94,12 +94,25 @@ def test_output_and_volume_validation(L):
     with pytest.raises(L.VRError, match="texture|differentiable"):
         L.vr_render_backward(None, cam, L.make_params(4096, 256, -3, 50, 0.5, filter=1), 4096, 4096, 4096, 4096,
                              None)
-    with pytest.raises(L.VRError, match="flags"):
-        L.vr_render_backward(None, cam, L.make_params(4096, 256, -3, 50, 0.5), 4096, 4096, 4096, 4096, None, 6)
+    with pytest.raises(L.VRError, match="flags: unknown"):
+        L.vr_render_backward(None, cam, L.make_params(4096, 256, -3, 50, 0.5), 4096, 4096, 4096, 4096, None, 8)
+    with pytest.raises(L.VRError, match="exclude each other"):
+        L.vr_render_backward(None, cam, L.make_params(4096, 256, -3, 50, 0.5), 4096, 4096, 4096, 4096, None,
+                             L.VR_GRAD_DIRECT | L.VR_GRAD_SCRATCH)
     with pytest.raises(L.VRError) as ei:
         L.vr_render_backward(None, cam, L.make_params(4096, 256, -3, 50, 0.5, bg=(0, 0, 0, 1)), 4096, 4096, 4096,
                              4096, None)
     assert ei.value.status == L.VR_ERR_UNSUPPORTED
+    p = L.make_params(4096, 256, -3, 50, 0.5)
+    with pytest.raises(L.VRError, match="at least one view"):
+        L.vr_render_backward_views(None, [], p, 4096, None)
+    with pytest.raises(L.VRError, match="must not be NULL"):
+        L.vr_render_backward_views(None, [L.vr_grad_view(cam, 4096, 4096, 4096), L.vr_grad_view(cam, 4096, None,
+                                                                                                4096)], p, 4096, None)
+    with pytest.raises(L.VRError, match="16-byte aligned"):
+        L.vr_render_backward_views(None, [L.vr_grad_view(cam, 4104, 4096, 4096)], p, 4096, None)
+    with pytest.raises(L.VRError, match="volume handle is NULL"):
+        L.vr_render_backward_views(None, [L.vr_grad_view(cam, 4096, 4096, 4096)] * 3, p, 4096, None)
 
 
 def test_volume_create_validation(L):

@@ -71,6 +71,68 @@ def test_backward_matches_fp64_reverse_sweep(P, torch, ert, bg, filt):
     vol.close()
 
 
+@pytest.mark.parametrize("dims,brick,store,W,H,step", [((36, 30, 40), 16, "f32", 48, 40, 0.5),
+                                                       ((41, 27, 33), 32, "f16", 64, 56, 0.35),
+                                                       ((30, 34, 26), 16, "bf16", 40, 30, 1.0)])
+def test_voxel_gradient_direct_and_scratch_reductions_agree(P, torch, dims, brick, store, W, H, step):
+    """Both voxel-gradient reductions (straight into the dense gradient, and
+    through the quad scratch plus its gather) against the FP64 reverse sweep,
+    overwriting and accumulating over three views (carried along x, y and z),
+    per view and in one multi-view call; odd and even nx, table and voxel
+    gradients alike."""
+    dev = torch.device("cuda")
+    cube = synth.hi_cube(dims, n_blobs=5, n_disks=1, seed=sum(dims))
+    t = cube.to(dev)
+    vol = P.Volume(t, store, brick=brick)
+    ref_cube = (cube.numpy() if store == "f32" else
+                (t.half() if store == "f16" else t.bfloat16()).float().cpu().numpy()).astype(np.float64)
+    tf_np = synth.tf_random_pwl(seed=W, alpha_max=0.3)
+    tf = torch.from_numpy(tf_np).to(dev)
+    cams = [synth.camera_random_persp(dims, seed=7 * q + H, width=W, height=H) for q in range(2)]
+    # and one view mostly along y (the random ones carry along x or z)
+    ext = [d - 1.0 for d in dims]
+    fwd = np.array([0.25, -0.93, 0.27]) / np.linalg.norm([0.25, -0.93, 0.27])
+    eye = tuple(e / 2.0 - 1.6 * max(ext) * f for e, f in zip(ext, fwd))
+    cams.append(synth.camera_persp(eye, tuple(fwd), (0.0, 0.0, 1.0), 40.0, W, H))
+    try:
+        res = {}
+        ref_tf, ref_vox = 0.0, 0.0
+        for q, cam in enumerate(cams):
+            img, ns = P.render(vol, cam, tf, -3.0, 30.0, step, 2.0)
+            g = torch.randn(img.shape, device=dev, generator=torch.Generator(device=dev).manual_seed(q))
+            rt, rv = oracle.render_backward(ref_cube, cam, tf_np, -3.0, 30.0, step,
+                                            g.cpu().numpy().astype(np.float64))
+            ref_tf, ref_vox = ref_tf + rt, ref_vox + rv
+            for mode in ("direct", "scratch"):
+                prev = res.get(mode)
+                gtf, gvox = P.render_backward(vol, cam, tf, -3.0, 30.0, step, img, ns, g, 2.0,
+                                              grad_tf=None if prev is None else prev[0],
+                                              grad_vox=None if prev is None else prev[1],
+                                              accumulate=prev is not None, vox_reduce=mode)
+                res[mode] = (gtf, gvox)
+        # the same three views in one call
+        imgs, nss, gs = [], [], []
+        for q, cam in enumerate(cams):
+            img, ns = P.render(vol, cam, tf, -3.0, 30.0, step, 2.0)
+            imgs.append(img)
+            nss.append(ns)
+            gs.append(torch.randn(img.shape, device=dev, generator=torch.Generator(device=dev).manual_seed(q)))
+        for mode in ("direct", "scratch"):
+            res["views_" + mode] = P.render_backward_views(vol, cams, tf, -3.0, 30.0, step, imgs, nss, gs, 2.0,
+                                                           vox_reduce=mode)
+        torch.cuda.synchronize()
+        for mode, (gtf, gvox) in res.items():
+            for got, ref in ((gtf.cpu().numpy(), ref_tf), (gvox.cpu().numpy().astype(np.float64), ref_vox)):
+                rel_norm = np.linalg.norm(got - ref) / np.linalg.norm(ref)
+                rel_max = np.abs(got - ref).max() / np.abs(ref).max()
+                assert rel_norm <= 1e-3 and rel_max <= 1e-3, (mode, rel_norm, rel_max)
+        d, s = res["direct"][1], res["scratch"][1]
+        assert (d - s).abs().max().item() <= 1e-4 * d.abs().max().item()
+        assert (s != 0).float().mean().item() > 0.05
+    finally:
+        vol.close()
+
+
 def test_backward_central_differences_table_and_voxels(P, torch):
     """Scaled-down form of the differentiation workload: L2 loss against a
     target rendered with a hidden table; FD on 32 table entries, 32 voxels."""
