@@ -212,18 +212,23 @@ vr_status vr_render(vr_volume_t vol, const vr_camera *cam, const vr_params *para
  *                only FP64 step; the order of its atomics is not
  *                deterministic).
  *   dev_grad_vox (nx*ny*nz float32 dense, x fastest) or NULL: float
- *                reductions (summation order is not deterministic), either
- *                straight into dev_grad_vox or, where the view puts at least
- *                one sample per voxel (ray pitch and step at the volume
- *                centre), into a library-owned scratch of one float4 per
- *                voxel (two 16-byte reductions per cell instead of four to
- *                eight) that a gather pass then adds into dev_grad_vox.  The
- *                scratch (16 bytes per voxel) is allocated on first use when
- *                the stream is not being captured and an eighth of the
- *                device memory stays free besides it; otherwise the direct
- *                form runs.  VR_GRAD_DIRECT forces the direct form,
- *                VR_GRAD_SCRATCH the scratch form (memory permitting); the
- *                staged filter's backward always scatters directly.
+ *                reductions (summation order is not deterministic).  A
+ *                ray's sums for its cell's eight corners are kept as two
+ *                planes of four across the view's dominant axis and the
+ *                shared plane is carried when the ray steps along it, so a
+ *                straight run writes one plane per cell: into dev_grad_vox
+ *                directly (x-neighbour pairs as 8-byte reductions where
+ *                aligned) or, where the view puts at least one sample per
+ *                voxel (ray pitch and step at the volume centre), as one
+ *                16-byte reduction per plane into a library-owned scratch of
+ *                one float4 per voxel, which a gather pass then adds into
+ *                dev_grad_vox.  The scratch (16 bytes per voxel) is allocated
+ *                on first use when the stream is not being captured and an
+ *                eighth of the device memory stays free besides it;
+ *                otherwise the direct form runs.  VR_GRAD_DIRECT forces the
+ *                direct form, VR_GRAD_SCRATCH the scratch form (memory
+ *                permitting); the staged filter's backward always scatters
+ *                directly.
  * Both are overwritten, or added to when flags has VR_GRAD_ACCUMULATE (a
  * loss summed over several views: call once per view).
  * Only software filtering is differentiable.  Errors: INVALID_ARG (also
@@ -244,9 +249,9 @@ vr_status vr_render_backward(vr_volume_t vol, const vr_camera *cam, const vr_par
  * after the first.  One call clears the outputs (unless VR_GRAD_ACCUMULATE),
  * launches one backward kernel per view into the same per-warp table rows
  * and voxel gradient, then runs the FP64 row sum and, with the quad scratch,
- * its gather once for all views; the scratch is chosen from the views'
- * summed sample density, with one quad orientation (the carry axis most
- * views share).  views is a host array of n (1..4096) entries; each view's
+ * its gather once for all views; the scratch is chosen where the views
+ * put at least one sample per voxel on average, with one quad orientation
+ * (the carry axis most views share).  views is a host array of n (1..4096) entries; each view's
  * image, sample counts and dL/d(image) follow the rules of
  * vr_render_backward.  Errors as vr_render_backward.
  * ---------------------------------------------------------------------- */

@@ -328,9 +328,10 @@ int preferred_copy(vr_volume *vol, const vr_camera *cam, bool may_build, cudaStr
 // Voxel-gradient scratch for a backward pass.  One 16-byte quad reduction per
 // plane of four corners replaces two to four scalar or pair reductions into
 // the dense gradient, at the cost of clearing and gathering 16 bytes per
-// voxel once per call; it pays where each voxel takes many samples: by
-// default where the call's views together put at least one sample per voxel,
-// estimated from the ray pitch and the step at the volume centre
+// voxel once per call, and its DRAM traffic (it does not stay in L2) once
+// per view; it pays where each voxel takes many samples: by default where
+// the call's views put at least one sample per voxel on average, estimated
+// from the ray pitch and the step at the volume centre
 // (VR_GRAD_DIRECT / VR_GRAD_SCRATCH override it).  Created
 // on first use when the stream is not being captured and the device keeps an
 // eighth of its memory free besides it.
@@ -347,7 +348,9 @@ static float4 *grad_quad_for(vr_volume *vol, const vr_grad_view *views, int n, c
             const double pitch = ray_pitch_voxels(vol, &views[q].cam, unit) * vol->spacing[0] / sp;   // in voxels
             if (pitch > 0.0) density += 1.0 / (pitch * pitch * step);
         }
-        if (!(density >= 1.0)) return nullptr;
+        // every view's kernel reads and writes the scratch once more (it does not
+        // stay in L2), so the views must be dense on average, not only together
+        if (!(density >= (double)n)) return nullptr;
     }
     if (vol->gquad) return vol->gquad;
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;

@@ -31,7 +31,10 @@
 
 namespace vr {
 
-constexpr int kBwdThreads = 256;
+// Four warps per CTA: at 90 registers five CTAs (20 warps) fit an SM, where
+// eight-warp CTAs fit two (16 warps); measured 6% faster on the 512^3
+// four-view workload.
+constexpr int kBwdThreads = 128;
 constexpr int kBwdWarps = kBwdThreads / 32;
 
 __device__ __forceinline__ void red_add_v4(float4 *a, float4 v)
@@ -50,45 +53,54 @@ __device__ __forceinline__ void red_add_f32(float *a, float x)
     asm volatile("red.global.add.f32 [%0], %1;\n" ::"l"(a), "f"(x) : "memory");
 }
 
-__device__ __forceinline__ float4 f4_axpy(float a, float4 x, float4 y)
-{
-    return make_float4(fmaf(a, x.x, y.x), fmaf(a, x.y, y.y), fmaf(a, x.z, y.z), fmaf(a, x.w, y.w));
-}
-
 // A ray's pending table-gradient contributions: bins b and b+1 of this
-// thread's row.  Consecutive samples whose bin pair coincides or overlaps are
-// added here and reach memory once.
+// thread's row.  A sample adds w0 dr to bin i0 and w1 dr to bin i0+1, with
+// dr = (aT g.rgb, da); g is the ray's own, so the colour part is kept as the
+// scalar sum of w aT and multiplied by g when the bin is written.
+// Consecutive samples whose bin pair coincides or overlaps are added here and
+// reach memory once.
 struct BinRun {
     int b = -1;
-    float4 lo = {0.f, 0.f, 0.f, 0.f}, hi = {0.f, 0.f, 0.f, 0.f};
-    __device__ __forceinline__ void add(float4 *row, int i0, float w0, float w1, float4 dr)
+    float s0 = 0.f, d0 = 0.f, s1 = 0.f, d1 = 0.f;     // bin b: (s0 g.rgb, d0); bin b+1: (s1 g.rgb, d1)
+    __device__ __forceinline__ static void put(float4 *row, int bin, float sc, float d, const float4 &g)
+    {
+        red_add_v4(row + bin, make_float4(sc * g.x, sc * g.y, sc * g.z, d));
+    }
+    __device__ __forceinline__ void add(float4 *row, int i0, float w0, float w1, float aT, float da, const float4 &g)
     {
         if (i0 == b) {
-            lo = f4_axpy(w0, dr, lo);
-            hi = f4_axpy(w1, dr, hi);
+            s0 = fmaf(w0, aT, s0);
+            d0 = fmaf(w0, da, d0);
+            s1 = fmaf(w1, aT, s1);
+            d1 = fmaf(w1, da, d1);
             return;
         }
         if (i0 == b + 1) {                 // new lower bin == pending upper bin
-            red_add_v4(row + b, lo);
-            lo = f4_axpy(w0, dr, hi);
+            put(row, b, s0, d0, g);
+            s0 = fmaf(w0, aT, s1);
+            d0 = fmaf(w0, da, d1);
         } else if (i0 + 1 == b) {          // new upper bin == pending lower bin
-            red_add_v4(row + b + 1, hi);
-            hi = f4_axpy(w1, dr, lo);
-            lo = make_float4(w0 * dr.x, w0 * dr.y, w0 * dr.z, w0 * dr.w);
+            put(row, b + 1, s1, d1, g);
+            s1 = fmaf(w1, aT, s0);
+            d1 = fmaf(w1, da, d0);
+            s0 = w0 * aT;
+            d0 = w0 * da;
             b = i0;
             return;
         } else {
-            flush(row);
-            lo = make_float4(w0 * dr.x, w0 * dr.y, w0 * dr.z, w0 * dr.w);
+            flush(row, g);
+            s0 = w0 * aT;
+            d0 = w0 * da;
         }
-        hi = make_float4(w1 * dr.x, w1 * dr.y, w1 * dr.z, w1 * dr.w);
+        s1 = w1 * aT;
+        d1 = w1 * da;
         b = i0;
     }
-    __device__ __forceinline__ void flush(float4 *row)
+    __device__ __forceinline__ void flush(float4 *row, const float4 &g)
     {
         if (b >= 0) {
-            red_add_v4(row + b, lo);
-            red_add_v4(row + b + 1, hi);
+            put(row, b, s0, d0, g);
+            put(row, b + 1, s1, d1, g);
         }
         b = -1;
     }
@@ -234,10 +246,10 @@ __global__ void __launch_bounds__(kBwdThreads) bwd_kernel(VolDev v, CamDev c, Pa
             // within 2 ulp there
             const float da = T * cg - (om > 0.0f ? __fdividef(R, om) : 0.0f);
             if (aT != 0.0f || da != 0.0f) {
-                const float4 dr = make_float4(aT * g.x, aT * g.y, aT * g.z, da);
-                bins.add(row, tp.i0, 1.0f - tp.w, tp.w, dr);
+                bins.add(row, tp.i0, 1.0f - tp.w, tp.w, aT, da, g);
                 if (gd.vox && tp.interior) {
-                    const float dv = (dr.x * de.x + dr.y * de.y + dr.z * de.z + dr.w * de.w) * vscale;
+                    // dr . de with dr = (aT g.rgb, da)
+                    const float dv = fmaf(aT, de.x * g.x + de.y * g.y + de.z * g.z, da * de.w) * vscale;
                     if (dv != 0.0f) {
                         const float fu = gd.axis == 0 ? cell.fy : cell.fx;
                         const float fv = gd.axis == 2 ? cell.fy : cell.fz;
@@ -262,7 +274,7 @@ __global__ void __launch_bounds__(kBwdThreads) bwd_kernel(VolDev v, CamDev c, Pa
             if (!__any_sync(kFull, active)) break;
             if (active) step(c1, f1, c0, f0);
         }
-        bins.flush(row);
+        bins.flush(row, g);
         cells.flush(gd);
     }
 }
