@@ -5,6 +5,9 @@
   python -m paper_1211_4896_gb300.profile_cases fwd16  # the same views of the cube stored as f16
   python -m paper_1211_4896_gb300.profile_cases bat    # the same 4 views in one batched call, f32
   python -m paper_1211_4896_gb300.profile_cases bwd    # 256^3 f32, 2 views at 512^2, step 0.5, table = ramp + 5% noise
+  python -m paper_1211_4896_gb300.profile_cases bwd512 # the 512^3 differentiation workload (1024^2, step 0.5):
+                                                       # backward of a z-view and an x-view, direct reductions
+                                                       # then through the quad scratch (4 bwd launches, 2 gathers)
   python -m paper_1211_4896_gb300.profile_cases stats  # 512^3 f32: moments, 256-bin histogram, median (twice)
   python -m paper_1211_4896_gb300.profile_cases skip   # the fwd views with a table transparent below v = 6,
                                                        # plain then with empty-space skipping
@@ -73,6 +76,31 @@ def case_bwd():
     print("ok", int(ns.sum()))
 
 
+def case_bwd512():
+    import torch
+    import synth
+    import paper_1211_4896_gb300 as P
+    dev = torch.device("cuda")
+    pre = synth.preset_diff_512()
+    vol = P.Volume(synth.hi_cube(pre["dims"], pre["n_blobs"], pre["n_disks"], pre["seed"], device=dev), "f32")
+    torch.cuda.empty_cache()
+    hidden = torch.from_numpy(synth.tf_ramp(256)).to(dev)
+    g = torch.Generator(device=dev)
+    g.manual_seed(5)
+    tf = (hidden + 0.05 * torch.rand(hidden.shape, device=dev, generator=g)).clamp(0, 1).contiguous()
+    views = []
+    for c in pre["cameras"][:2]:              # 0 deg (along z) and 90 deg (along x)
+        img, ns = P.render(vol, c, tf, synth.TF_VMIN, synth.TF_VMAX, pre["step"], 2.0)
+        views.append((c, img, ns, torch.randn_like(img)))
+    gvox = torch.empty(vol.shape, device=dev)
+    for mode in ("direct", "scratch"):
+        for c, img, ns, gr in views:
+            P.render_backward(vol, c, tf, synth.TF_VMIN, synth.TF_VMAX, pre["step"], img, ns, gr, 2.0,
+                              grad_vox=gvox, vox_reduce=mode)
+    torch.cuda.synchronize()
+    print("ok", sum(int(v[2].sum()) for v in views))
+
+
 def case_skip():
     import numpy as np
     import torch
@@ -109,5 +137,5 @@ def case_stats():
 if __name__ == "__main__":
     from paper_1211_4896_gb300 import build
     build.build()
-    {"fwd": case_fwd, "fwd16": lambda: case_fwd("f16"), "bat": case_bat, "bwd": case_bwd,
+    {"fwd": case_fwd, "fwd16": lambda: case_fwd("f16"), "bat": case_bat, "bwd": case_bwd, "bwd512": case_bwd512,
      "stats": case_stats, "skip": case_skip}[sys.argv[1] if len(sys.argv) > 1 else "fwd"]()
