@@ -392,7 +392,7 @@ extern "C" vr_status vr_autotune_batched(const vr_job *jobs, int n, vr_batch_opt
     if (!best) return (set_error("best is NULL"), VR_ERR_INVALID_ARG);
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
     const int shapes[4][2] = {{8, 4}, {4, 8}, {16, 2}, {32, 1}};
-    const int ctas_list[4] = {0, 1, 2, 4};
+    const int ctas_list[5] = {0, 1, 2, 3, 4};
     float best_ms = 1e30f;
     vr_batch_opts win = *best;
     cudaEvent_t e0, e1;

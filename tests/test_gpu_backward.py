@@ -264,3 +264,45 @@ def test_backward_rejects_opaque_background_and_texture(P, torch):
         P.render_backward(vol, cam, tf, -3, 50, 0.5, img, ns, img, bg=(0, 0, 0, 1.0))
     assert ei.value.status == -2
     vol.close()
+
+
+@pytest.mark.parametrize("filt", [0, 2])
+def test_multi_view_call_equals_accumulated_single_calls(P, torch, filt):
+    """vr_render_backward_views (one call for several views, with and
+    without VR_GRAD_ACCUMULATE on top of earlier sums) equals the per-view
+    calls accumulated, for the brick path and the staged filter, and leaves
+    the gradients untouched by views that miss the box."""
+    dev = torch.device("cuda")
+    dims = (30, 26, 34)
+    cube, vol, _ = _setup(torch, P, dims, seed=21, W=40, H=32)
+    tf = torch.from_numpy(synth.tf_random_pwl(seed=4, alpha_max=0.3)).to(dev)
+    cams = [synth.camera_random_persp(dims, seed=40 + q, width=40, height=32) for q in range(3)]
+    # a fourth view that looks away from the cube: no ray hits it
+    away = dict(cams[0], forward=tuple(-f for f in cams[0]["forward"]))
+    cams.append(away)
+    imgs, nss, gs = [], [], []
+    for q, cam in enumerate(cams):
+        img, ns = P.render(vol, cam, tf, -3.0, 30.0, 0.5, 2.0, filter=filt)
+        imgs.append(img)
+        nss.append(ns)
+        gs.append(torch.randn(img.shape, device=dev, generator=torch.Generator(device=dev).manual_seed(100 + q)))
+    assert int(nss[3].sum()) == 0
+    try:
+        ref_tf, ref_vox = None, None
+        for q, cam in enumerate(cams):
+            ref_tf, ref_vox = P.render_backward(vol, cam, tf, -3.0, 30.0, 0.5, imgs[q], nss[q], gs[q], 2.0,
+                                                grad_tf=ref_tf, grad_vox=ref_vox, accumulate=q > 0, filter=filt)
+        got_tf, got_vox = P.render_backward_views(vol, cams, tf, -3.0, 30.0, 0.5, imgs, nss, gs, 2.0, filter=filt)
+        # accumulate: the first two views, then the last two on top
+        acc_tf, acc_vox = P.render_backward_views(vol, cams[:2], tf, -3.0, 30.0, 0.5, imgs[:2], nss[:2], gs[:2],
+                                                  2.0, filter=filt)
+        acc_tf, acc_vox = P.render_backward_views(vol, cams[2:], tf, -3.0, 30.0, 0.5, imgs[2:], nss[2:], gs[2:],
+                                                  2.0, grad_tf=acc_tf, grad_vox=acc_vox, accumulate=True,
+                                                  filter=filt)
+        torch.cuda.synchronize()
+        for t, v in ((got_tf, got_vox), (acc_tf, acc_vox)):
+            assert (t - ref_tf).abs().max().item() <= 1e-5 * ref_tf.abs().max().item()
+            assert (v - ref_vox).abs().max().item() <= 1e-4 * ref_vox.abs().max().item()
+        assert ref_vox.abs().max().item() > 0
+    finally:
+        vol.close()
