@@ -386,6 +386,23 @@ vr_status vr_profile(vr_volume_t vol, const vr_camera *cam, float step, int i, i
 vr_status vr_render_subbox(vr_volume_t vol, const vr_camera *cam, const vr_params *params, const int cell_lo[3],
                            const int cell_hi[3], float *dev_partial, float *dev_depth, uint32_t *dev_count,
                            void *cuda_stream);
+
+/* vr_render_subbox_of: the same for a volume that holds only the voxels
+ * [offset, offset + dims) of a larger grid of global_dims voxels -- one
+ * GPU's sub-cube in the paper's object-space split, with the one-voxel
+ * overlap its far cells need.  The volume's origin is that of its own first
+ * voxel, so the whole grid's first voxel lies offset * spacing before it.
+ * Rays are clipped to the whole grid's box and sampled at the whole render's
+ * positions (the camera is set up in the whole grid's coordinates, so every
+ * sub-cube computes bit-identical sample positions and each sample falls in
+ * exactly one sub-box); cell_lo / cell_hi are cell indices of the whole grid
+ * with offset <= cell_lo < cell_hi <= offset + dims - 1 per axis.  With
+ * offset 0 and global_dims = dims it is vr_render_subbox.  Errors as
+ * vr_render_subbox. */
+vr_status vr_render_subbox_of(vr_volume_t vol, const int64_t global_dims[3], const int64_t offset[3],
+                              const vr_camera *cam, const vr_params *params, const int cell_lo[3],
+                              const int cell_hi[3], float *dev_partial, float *dev_depth, uint32_t *dev_count,
+                              void *cuda_stream);
 vr_status vr_composite(int k, const float *const *dev_partials, const float *const *dev_depths, int width,
                        int height, const float bg_rgba[4], float *dev_rgba_out, void *cuda_stream);
 

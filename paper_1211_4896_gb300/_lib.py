@@ -61,7 +61,8 @@ class vr_batch_opts(C.Structure):
 # every symbol include/vr.h declares
 EXPORTS = ("vr_volume_create", "vr_volume_update", "vr_volume_destroy", "vr_volume_info", "vr_render",
            "vr_render_backward", "vr_render_backward_views", "vr_render_batched", "vr_autotune_batched", "vr_render_batched_noalloc",
-           "vr_minimap", "vr_profile", "vr_render_subbox", "vr_composite", "vr_moments", "vr_histogram",
+           "vr_minimap", "vr_profile", "vr_render_subbox", "vr_render_subbox_of", "vr_composite", "vr_moments",
+           "vr_histogram",
            "vr_median", "vr_check", "vr_selftest_timeout", "vr_last_error", "vr_version")
 VR_NOALLOC_MAX_JOBS = 256
 
@@ -104,13 +105,16 @@ def load() -> C.CDLL:
         L.vr_profile.argtypes = [vp, P(vr_camera), C.c_float, C.c_int, C.c_int, vp, C.c_uint32, vp, vp]
         L.vr_render_subbox.argtypes = [vp, P(vr_camera), P(vr_params), P(C.c_int * 3), P(C.c_int * 3), vp, vp, vp,
                                        vp]
+        L.vr_render_subbox_of.argtypes = [vp, P(C.c_int64 * 3), P(C.c_int64 * 3), P(vr_camera), P(vr_params),
+                                          P(C.c_int * 3), P(C.c_int * 3), vp, vp, vp, vp]
         L.vr_composite.argtypes = [C.c_int, P(vp), P(vp), C.c_int, C.c_int, P(C.c_float * 4), vp, vp]
         L.vr_moments.argtypes = [vp, vp, vp]
         L.vr_histogram.argtypes = [vp, C.c_double, C.c_double, C.c_int, vp, vp]
         L.vr_median.argtypes = [vp, vp, vp]
         for name in ("vr_volume_create", "vr_volume_update", "vr_volume_destroy", "vr_volume_info", "vr_render",
                      "vr_render_backward", "vr_render_backward_views", "vr_render_batched", "vr_autotune_batched",
-                     "vr_render_batched_noalloc", "vr_minimap", "vr_profile", "vr_render_subbox", "vr_composite",
+                     "vr_render_batched_noalloc", "vr_minimap", "vr_profile", "vr_render_subbox", "vr_render_subbox_of",
+                     "vr_composite",
                      "vr_moments", "vr_histogram", "vr_median", "vr_check", "vr_selftest_timeout"):
             getattr(L, name).restype = C.c_int
         L.vr_last_error.argtypes = []
@@ -242,6 +246,16 @@ def vr_render_subbox(vol: int, cam: vr_camera, params: vr_params, cell_lo, cell_
                                                        C.byref((C.c_int * 3)(*[int(x) for x in cell_lo])),
                                                        C.byref((C.c_int * 3)(*[int(x) for x in cell_hi])),
                                                        dev_partial, dev_depth, dev_count, stream))
+
+
+def vr_render_subbox_of(vol: int, global_dims, offset, cam: vr_camera, params: vr_params, cell_lo, cell_hi,
+                        dev_partial: int, dev_depth: int, dev_count: int | None, stream: int = 0):
+    _check("vr_render_subbox_of",
+           load().vr_render_subbox_of(vol, C.byref((C.c_int64 * 3)(*[int(x) for x in global_dims])),
+                                      C.byref((C.c_int64 * 3)(*[int(x) for x in offset])), C.byref(cam),
+                                      C.byref(params), C.byref((C.c_int * 3)(*[int(x) for x in cell_lo])),
+                                      C.byref((C.c_int * 3)(*[int(x) for x in cell_hi])), dev_partial, dev_depth,
+                                      dev_count, stream))
 
 
 def vr_composite(dev_partials, dev_depths, width: int, height: int, bg, dev_rgba_out: int, stream: int = 0):

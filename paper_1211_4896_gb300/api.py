@@ -175,17 +175,24 @@ def profile(vol: Volume, cam: dict, step: float, i: int, j: int, max_values: int
 
 
 def render_subbox(vol: Volume, cam: dict, tf: torch.Tensor, vmin: float, vmax: float, step: float, cell_lo, cell_hi,
-                  stream=None):
+                  stream=None, global_dims=None, offset=None):
     """Sort-last partial render of the cells [cell_lo, cell_hi) (x, y, z):
     returns (partial (H, W, 4): premultiplied colour and transmittance,
-    depth (H, W): ray parameter of the first sample or inf, count (H, W))."""
+    depth (H, W): distance of the first sample from the eye or inf, count
+    (H, W)).  With global_dims and offset the volume holds the voxels
+    [offset, offset + dims) of a grid of global_dims voxels (its origin is
+    that of its own first voxel) and the cells are the whole grid's."""
     H, W = int(cam["height"]), int(cam["width"])
     partial = torch.empty((H, W, 4), device=vol.device, dtype=torch.float32)
     depth = torch.empty((H, W), device=vol.device, dtype=torch.float32)
     count = torch.empty((H, W), device=vol.device, dtype=torch.int32)
     p = _params(tf, vmin, vmax, step, 2.0, (0.0, 0.0, 0.0, 0.0), L.VR_FILTER_SOFTWARE)
-    L.vr_render_subbox(vol.handle, L.make_camera(cam), p, cell_lo, cell_hi, partial.data_ptr(), depth.data_ptr(),
-                       count.data_ptr(), _stream(stream))
+    if global_dims is None and offset is None:
+        L.vr_render_subbox(vol.handle, L.make_camera(cam), p, cell_lo, cell_hi, partial.data_ptr(), depth.data_ptr(),
+                           count.data_ptr(), _stream(stream))
+    else:
+        L.vr_render_subbox_of(vol.handle, global_dims, offset, L.make_camera(cam), p, cell_lo, cell_hi,
+                              partial.data_ptr(), depth.data_ptr(), count.data_ptr(), _stream(stream))
     return partial, depth, count
 
 

@@ -156,6 +156,14 @@ vr_status prepare_params(const vr_params *p, ParamDev *o)
 
 vr_status prepare_camera(const vr_volume *vol, const vr_camera *cam, CamDev *o)
 {
+    return prepare_camera_grid(vol->origin, vol->spacing, vol->dims, cam, o);
+}
+
+// The camera in the voxel coordinates of a grid of dims voxels whose first
+// voxel sits at origin (world units).
+vr_status prepare_camera_grid(const double origin[3], const double spacing[3], const int64_t dims[3],
+                              const vr_camera *cam, CamDev *o)
+{
     double f[3] = {cam->forward[0], cam->forward[1], cam->forward[2]};
     const double fl = std::sqrt(dot3(f, f));
     for (double &x : f) x /= fl;
@@ -167,7 +175,7 @@ vr_status prepare_camera(const vr_volume *vol, const vr_camera *cam, CamDev *o)
     const double W = cam->width, H = cam->height, aspect = W / H;
     // anchor plane through the volume centre, perpendicular to f
     double centre[3];
-    for (int a = 0; a < 3; ++a) centre[a] = vol->origin[a] + 0.5 * (double)(vol->dims[a] - 1) * vol->spacing[a];
+    for (int a = 0; a < 3; ++a) centre[a] = origin[a] + 0.5 * (double)(dims[a] - 1) * spacing[a];
     double ce[3] = {centre[0] - cam->eye[0], centre[1] - cam->eye[1], centre[2] - cam->eye[2]};
     const double D = dot3(ce, f);
     double Q0[3], A[3], B[3], wa[3], wb[3];
@@ -193,18 +201,18 @@ vr_status prepare_camera(const vr_volume *vol, const vr_camera *cam, CamDev *o)
     o->W = cam->width;
     o->H = cam->height;
     o->persp = cam->kind == VR_CAMERA_PERSPECTIVE;
-    o->q0 = make_float3((float)((Q0[0] - vol->origin[0]) / vol->spacing[0]),
-                        (float)((Q0[1] - vol->origin[1]) / vol->spacing[1]),
-                        (float)((Q0[2] - vol->origin[2]) / vol->spacing[2]));
-    o->qa = make_float3((float)(A[0] / vol->spacing[0]), (float)(A[1] / vol->spacing[1]),
-                        (float)(A[2] / vol->spacing[2]));
-    o->qb = make_float3((float)(B[0] / vol->spacing[0]), (float)(B[1] / vol->spacing[1]),
-                        (float)(B[2] / vol->spacing[2]));
+    o->q0 = make_float3((float)((Q0[0] - origin[0]) / spacing[0]),
+                        (float)((Q0[1] - origin[1]) / spacing[1]),
+                        (float)((Q0[2] - origin[2]) / spacing[2]));
+    o->qa = make_float3((float)(A[0] / spacing[0]), (float)(A[1] / spacing[1]),
+                        (float)(A[2] / spacing[2]));
+    o->qb = make_float3((float)(B[0] / spacing[0]), (float)(B[1] / spacing[1]),
+                        (float)(B[2] / spacing[2]));
     o->wf = make_float3((float)f[0], (float)f[1], (float)f[2]);
     o->wa = make_float3((float)wa[0], (float)wa[1], (float)wa[2]);
     o->wb = make_float3((float)wb[0], (float)wb[1], (float)wb[2]);
-    o->inv_sp = make_float3((float)(1.0 / vol->spacing[0]), (float)(1.0 / vol->spacing[1]),
-                            (float)(1.0 / vol->spacing[2]));
+    o->inv_sp = make_float3((float)(1.0 / spacing[0]), (float)(1.0 / spacing[1]),
+                            (float)(1.0 / spacing[2]));
     o->dist = (float)D;
     return VR_OK;
 }
@@ -815,40 +823,80 @@ vr_status vr_profile(vr_volume_t vol, const vr_camera *cam, float step, int i, i
     return VR_OK;
 }
 
-vr_status vr_render_subbox(vr_volume_t vol, const vr_camera *cam, const vr_params *params, const int cell_lo[3],
-                           const int cell_hi[3], float *dev_partial, float *dev_depth, uint32_t *dev_count,
-                           void *cuda_stream)
+static vr_status subbox_of(vr_volume_t vol, const int64_t gdims[3], const int64_t offset[3], const vr_camera *cam,
+                           const vr_params *params, const int cell_lo[3], const int cell_hi[3], float *dev_partial,
+                           float *dev_depth, uint32_t *dev_count, void *cuda_stream, const char *who)
 {
     g_err.clear();
     vr_status st = check_camera(cam);
     if (st == VR_OK) st = check_params(params);
-    if (st == VR_OK) st = check_mode_path(params, "vr_render_subbox");
+    if (st == VR_OK) st = check_mode_path(params, who);
     if (st != VR_OK) return st;
     if (params->filter != VR_FILTER_SOFTWARE)
-        return (set_error("vr_render_subbox: software filter only"), VR_ERR_UNSUPPORTED);
+        return (set_error(std::string(who) + ": software filter only"), VR_ERR_UNSUPPORTED);
     st = check_volume(vol);
     if (st == VR_OK) st = check_step(vol, params);
     if (st != VR_OK) return st;
+    if (!gdims || !offset) return invalid("global_dims and offset must not be NULL");
+    for (int a = 0; a < 3; ++a) {
+        if (gdims[a] < 2 || gdims[a] > (int64_t)1 << 30) return invalid("global_dims must be in [2, 2^30] per axis");
+        if (offset[a] < 0 || offset[a] + vol->dims[a] > gdims[a])
+            return invalid("need 0 <= offset and offset + dims <= global_dims per axis");
+    }
+    double d2 = 0.0;
+    for (int a = 0; a < 3; ++a) {
+        const double e = (double)(gdims[a] - 1) * vol->spacing[a];
+        d2 += e * e;
+    }
+    if (std::sqrt(d2) / (double)params->step > 16777216.0) return invalid("params.step too small: > 2^24 samples per ray");
     if (!cell_lo || !cell_hi) return invalid("cell_lo and cell_hi must not be NULL");
     for (int a = 0; a < 3; ++a)
-        if (cell_lo[a] < 0 || cell_hi[a] > vol->dims[a] - 1 || cell_lo[a] >= cell_hi[a])
-            return invalid("need 0 <= cell_lo < cell_hi <= dims - 1 (cells) per axis");
+        if (cell_lo[a] < offset[a] || cell_hi[a] > offset[a] + vol->dims[a] - 1 || cell_lo[a] >= cell_hi[a])
+            return invalid("need offset <= cell_lo < cell_hi <= offset + dims - 1 (cells) per axis");
     if (!dev_partial || !is_aligned16(dev_partial)) return invalid("dev_partial must be non-NULL and 16-byte aligned");
     if (!dev_depth || (reinterpret_cast<uintptr_t>(dev_depth) & 3u) != 0)
         return invalid("dev_depth must be non-NULL and 4-byte aligned");
     if ((reinterpret_cast<uintptr_t>(dev_count) & 3u) != 0) return invalid("dev_count must be 4-byte aligned");
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    // the camera in the whole grid's voxel coordinates: its first voxel sits
+    // offset voxels before this volume's
+    double gorigin[3];
+    for (int a = 0; a < 3; ++a) gorigin[a] = vol->origin[a] - (double)offset[a] * vol->spacing[a];
     CamDev c;
     ParamDev p;
-    prepare_camera(vol, cam, &c);
+    prepare_camera_grid(gorigin, vol->spacing, gdims, cam, &c);
     prepare_params(params, &p);
     unsigned *ctr;
     next_counter(vol, &ctr);
+    const int gd[3] = {(int)gdims[0], (int)gdims[1], (int)gdims[2]};
+    const int off[3] = {(int)offset[0], (int)offset[1], (int)offset[2]};
     cudaError_t e = launch_subbox(vol_dev_copy(vol, preferred_copy(vol, cam, true, s)), vol->store_dtype, c, p,
-                                  cell_lo, cell_hi, reinterpret_cast<float4 *>(dev_partial), dev_depth, dev_count,
-                                  ctr, s);
-    if (e != cudaSuccess) return cuda_fail(e, "vr_render_subbox launch");
+                                  cell_lo, cell_hi, gd, off, reinterpret_cast<float4 *>(dev_partial), dev_depth,
+                                  dev_count, ctr, s);
+    if (e != cudaSuccess) return cuda_fail(e, who);
     return VR_OK;
+}
+
+vr_status vr_render_subbox(vr_volume_t vol, const vr_camera *cam, const vr_params *params, const int cell_lo[3],
+                           const int cell_hi[3], float *dev_partial, float *dev_depth, uint32_t *dev_count,
+                           void *cuda_stream)
+{
+    if (!vol) {
+        g_err.clear();
+        return invalid("volume handle is NULL");
+    }
+    const int64_t zero[3] = {0, 0, 0};
+    return subbox_of(vol, vol->dims, zero, cam, params, cell_lo, cell_hi, dev_partial, dev_depth, dev_count,
+                     cuda_stream, "vr_render_subbox");
+}
+
+vr_status vr_render_subbox_of(vr_volume_t vol, const int64_t global_dims[3], const int64_t offset[3],
+                              const vr_camera *cam, const vr_params *params, const int cell_lo[3],
+                              const int cell_hi[3], float *dev_partial, float *dev_depth, uint32_t *dev_count,
+                              void *cuda_stream)
+{
+    return subbox_of(vol, global_dims, offset, cam, params, cell_lo, cell_hi, dev_partial, dev_depth, dev_count,
+                     cuda_stream, "vr_render_subbox_of");
 }
 
 vr_status vr_composite(int k, const float *const *dev_partials, const float *const *dev_depths, int width,

@@ -111,6 +111,8 @@ bool is_aligned16(const void *p);
 
 // Host-side preparation (vr_api.cpp).
 vr_status prepare_camera(const vr_volume *vol, const vr_camera *cam, CamDev *out);
+vr_status prepare_camera_grid(const double origin[3], const double spacing[3], const int64_t dims[3],
+                              const vr_camera *cam, CamDev *out);
 vr_status prepare_params(const vr_params *p, ParamDev *out);
 VolDev vol_dev(const vr_volume *vol);
 vr_status next_counter(vr_volume *vol, unsigned **ctr);
@@ -169,8 +171,8 @@ cudaError_t launch_profile(const VolDev &v, vr_dtype dt, const CamDev &c, float 
 // Sort-last sub-box render and depth-ordered composite (vr_modes.cu).
 constexpr int kMaxPartials = 64;
 cudaError_t launch_subbox(const VolDev &v, vr_dtype dt, const CamDev &c, const ParamDev &p, const int lo[3],
-                          const int hi[3], float4 *partial, float *depth, uint32_t *count, unsigned *counter,
-                          cudaStream_t s);
+                          const int hi[3], const int gdim[3], const int off[3], float4 *partial, float *depth,
+                          uint32_t *count, unsigned *counter, cudaStream_t s);
 cudaError_t launch_composite(int k, const float *const *partials, const float *const *depths, long long npx,
                              const float bg[4], float *out, cudaStream_t s);
 // Empty-space skipping (vr_skip.cu).

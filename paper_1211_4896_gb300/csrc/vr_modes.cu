@@ -261,8 +261,9 @@ __device__ __forceinline__ float eye_param(const CamDev &c, int i, int j)
 
 template <typename T, int LOG2B, int L>
 __global__ void __launch_bounds__(kModeThreads) subbox_kernel(VolDev v, CamDev c, ParamDev p, int3 lo, int3 hi,
-                                                               float4 *partial, float *depth, uint32_t *count,
-                                                               unsigned *counter, int tiles_x, unsigned ntiles)
+                                                               int3 gdim, float3 off, float4 *partial, float *depth,
+                                                               uint32_t *count, unsigned *counter, int tiles_x,
+                                                               unsigned ntiles)
 {
     const int lane = threadIdx.x & 31;
     for (;;) {
@@ -274,7 +275,9 @@ __global__ void __launch_bounds__(kModeThreads) subbox_kernel(VolDev v, CamDev c
         const int j = (int)(tile / tiles_x) * 4 + (lane >> 3);
         const bool inside_img = i < c.W && j < c.H;
         Ray ray;
-        bool active = inside_img && setup_ray(c, v.nx, v.ny, v.nz, p.step, i, j, ray);
+        // rays and samples of the whole grid (gdim voxels; the camera is in its
+        // coordinates); the volume holds its voxels from off on
+        bool active = inside_img && setup_ray(c, gdim.x, gdim.y, gdim.z, p.step, i, j, ray);
         // samples whose position lies in the sub-box widened by one voxel: the
         // exact cell test below decides each of them
         int k = 0, k_end = 0;
@@ -295,18 +298,26 @@ __global__ void __launch_bounds__(kModeThreads) subbox_kernel(VolDev v, CamDev c
         int first = -1, used = 0;
         Cell c0, c1;
         Gathered<T, L> f0, f1;
+        auto local = [&](int q) {
+            const float3 g = sample_pos(ray, q, p.step);
+            return make_float3(g.x - off.x, g.y - off.y, g.z - off.z);     // exact for 0 <= off <= g
+        };
         if (active) {
-            c0 = locate<LOG2B, L>(v, sample_pos(ray, k, p.step));
+            c0 = locate<LOG2B, L>(v, local(k));
             fetch_corners<T, LOG2B, L>(v, c0, f0);
         }
         auto step = [&](const Cell &cur, const Gathered<T, L> &fc, Cell &nxt, Gathered<T, L> &fn) {
             const bool more = k + 1 < k_end;
             if (more) {
-                nxt = locate<LOG2B, L>(v, sample_pos(ray, k + 1, p.step));
+                nxt = locate<LOG2B, L>(v, local(k + 1));
                 fetch_corners<T, LOG2B, L>(v, nxt, fn);
             }
-            if (cur.x0 >= lo.x && cur.x0 < hi.x && cur.y0 >= lo.y && cur.y0 < hi.y && cur.z0 >= lo.z &&
-                cur.z0 < hi.z) {
+            // the sample's cell in the whole grid, clamped as the whole render clamps it
+            // (x0 + fx is the local position exactly)
+            const int gx = min(max(__float2int_rd((float)cur.x0 + cur.fx) + (int)off.x, 0), gdim.x - 2);
+            const int gy = min(max(__float2int_rd((float)cur.y0 + cur.fy) + (int)off.y, 0), gdim.y - 2);
+            const int gz = min(max(__float2int_rd((float)cur.z0 + cur.fz) + (int)off.z, 0), gdim.z - 2);
+            if (gx >= lo.x && gx < hi.x && gy >= lo.y && gy < hi.y && gz >= lo.z && gz < hi.z) {
                 TfPos tp;
                 const float4 e = tf_lookup_l1(p, interp_corners(cur, fc), tp);
                 const float aT = e.w * Tt;
@@ -335,21 +346,23 @@ __global__ void __launch_bounds__(kModeThreads) subbox_kernel(VolDev v, CamDev c
 }
 
 cudaError_t launch_subbox(const VolDev &v, vr_dtype dt, const CamDev &c, const ParamDev &p, const int lo[3],
-                          const int hi[3], float4 *partial, float *depth, uint32_t *count, unsigned *counter,
-                          cudaStream_t s)
+                          const int hi[3], const int gdim[3], const int off[3], float4 *partial, float *depth,
+                          uint32_t *count, unsigned *counter, cudaStream_t s)
 {
     const int tiles_x = (c.W + 7) / 8, tiles_y = (c.H + 3) / 4;
     const unsigned ntiles = (unsigned)tiles_x * (unsigned)tiles_y;
     cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(unsigned), s);
     if (e != cudaSuccess) return e;
     const int3 l3 = make_int3(lo[0], lo[1], lo[2]), h3 = make_int3(hi[0], hi[1], hi[2]);
+    const int3 g3 = make_int3(gdim[0], gdim[1], gdim[2]);
+    const float3 o3 = make_float3((float)off[0], (float)off[1], (float)off[2]);
     return visit_layout(
         v, dt,
         [&](auto lay) {
             using Y = decltype(lay);
             auto fn = subbox_kernel<typename Y::type, Y::log2b, Y::order>;
-            fn<<<persistent_grid(fn, ntiles), kModeThreads, 0, s>>>(v, c, p, l3, h3, partial, depth, count, counter,
-                                                                    tiles_x, ntiles);
+            fn<<<persistent_grid(fn, ntiles), kModeThreads, 0, s>>>(v, c, p, l3, h3, g3, o3, partial, depth, count,
+                                                                    counter, tiles_x, ntiles);
             return cudaGetLastError();
         },
         cudaErrorInvalidValue);

@@ -113,6 +113,11 @@ def test_output_and_volume_validation(L):
         L.vr_render_backward_views(None, [L.vr_grad_view(cam, 4104, 4096, 4096)], p, 4096, None)
     with pytest.raises(L.VRError, match="volume handle is NULL"):
         L.vr_render_backward_views(None, [L.vr_grad_view(cam, 4096, 4096, 4096)] * 3, p, 4096, None)
+    with pytest.raises(L.VRError, match="volume handle is NULL"):
+        L.vr_render_subbox_of(None, (64, 64, 64), (0, 0, 0), cam, p, (0, 0, 0), (8, 8, 8), 4096, 4096, None)
+    with pytest.raises(L.VRError, match="software filter"):
+        L.vr_render_subbox_of(None, (64, 64, 64), (0, 0, 0), cam, L.make_params(4096, 256, -3, 50, 0.5, filter=1),
+                              (0, 0, 0), (8, 8, 8), 4096, 4096, None)
 
 
 def test_volume_create_validation(L):

@@ -104,3 +104,48 @@ def test_composite_follows_depth_and_checks_arguments(P, torch):
         assert e.value.status == L.VR_ERR_INVALID_ARG
     finally:
         vol.close()
+
+
+@pytest.mark.parametrize("store,parts,kind", [("f32", 2, "persp"), ("f32", 6, "ortho"), ("f16", 4, "persp")])
+def test_sub_cube_volumes_give_the_whole_volume_partials(P, torch, store, parts, kind):
+    """Object-space split as across GPUs (Section 3.2): each box of cells
+    rendered from a volume holding only its sub-cube (voxels [lo, hi], origin
+    at lo) with the whole grid's placement gives bit for bit the partial,
+    depth and count of the same box rendered from the whole volume, and the
+    depth-ordered composite of the pieces equals the whole render."""
+    from paper_1211_4896_gb300.sortlast import split_cells, sub_cube
+    dims = (45, 38, 52)
+    cube = synth.hi_cube(dims, n_blobs=6, n_disks=1, seed=77).cuda()
+    whole_vol = P.Volume(cube, store)
+    tf_np = synth.tf_random_pwl(seed=12, alpha_max=0.3)
+    tf = torch.from_numpy(tf_np).cuda()
+    cam = synth.camera_random_persp(dims, seed=parts, width=44, height=36, fov_y_deg=35.0)
+    if kind == "ortho":
+        cam = dict(cam, kind=0, ortho_height=1.1 * max(dims), fov_y_deg=0.0)
+    bg = (0.0, 0.05, 0.1, 0.2)
+    vols = []
+    try:
+        whole, ns = P.render(whole_vol, cam, tf, -3.0, 30.0, 0.55, 2.0, bg=bg)
+        pieces, depths, counts = [], [], []
+        for lo, hi in split_cells([d - 1 for d in dims], parts):
+            vol = P.Volume(sub_cube(cube, lo, hi), store, origin=tuple(float(x) for x in lo))
+            vols.append(vol)
+            part, depth, count = P.render_subbox(vol, cam, tf, -3.0, 30.0, 0.55, lo, hi, global_dims=dims, offset=lo)
+            ref_p, ref_d, ref_c = P.render_subbox(whole_vol, cam, tf, -3.0, 30.0, 0.55, lo, hi)
+            assert torch.equal(part, ref_p) and torch.equal(depth, ref_d) and torch.equal(count, ref_c)
+            pieces.append(part)
+            depths.append(depth)
+            counts.append(count)
+        assert torch.equal(sum(counts), ns)
+        got = P.composite(pieces, depths, bg=bg)
+        assert (got - whole).abs().max().item() <= 2e-6
+        assert whole[..., 3].max().item() > 0.1
+        from paper_1211_4896_gb300 import _lib as L
+        with pytest.raises(L.VRError) as e:       # a box beyond the sub-cube's voxels
+            P.render_subbox(vols[0], cam, tf, -3.0, 30.0, 0.55, (0, 0, 0), tuple(d - 1 for d in dims),
+                            global_dims=dims, offset=(0, 0, 0))
+        assert e.value.status == L.VR_ERR_INVALID_ARG
+    finally:
+        for v in vols:
+            v.close()
+        whole_vol.close()
