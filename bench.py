@@ -751,22 +751,28 @@ def run_sortlast_1024(args):
     sub-boxes of cells (the paper's sub-cubes), eight 1080p orbit views, step 1,
     no early termination: 8 sub-box renders + one depth-ordered composite per
     view, against the whole render of the same views; pixel error of the
-    composite against the oracle on three rows of view 0."""
+    composite against the oracle on three rows of view 0.  The same split
+    once more as across GPUs: each box rendered from a volume that holds only
+    its sub-cube (vr_render_subbox_of), whose composite must equal the
+    whole-volume form bit for bit."""
     import torch
     import oracle
     import paper_1211_4896_gb300 as P
+    from paper_1211_4896_gb300.sortlast import sub_cube
     dev = torch.device("cuda")
     pre = synth.preset_scale_1024()
     cube = make_cube(pre, dev)
     vol = P.Volume(cube, "f32")
+    e = (0, 511, 1023)                        # 1023 cells per axis, split in two
+    boxes = [((e[x], e[y], e[z]), (e[x + 1], e[y + 1], e[z + 1])) for z in (0, 1) for y in (0, 1) for x in (0, 1)]
+    sub_vols = [P.Volume(sub_cube(cube, lo, hi), "f32", origin=tuple(float(q) for q in lo)) for lo, hi in boxes]
+    dims = tuple(vol.shape[::-1])
     host = cube.cpu().numpy()
     del cube
     torch.cuda.empty_cache()
     tf_np = synth.tf_ramp(256)
     tf = torch.from_numpy(tf_np).to(dev)
     cams = pre["cameras"]
-    e = (0, 511, 1023)                        # 1023 cells per axis, split in two
-    boxes = [((e[x], e[y], e[z]), (e[x + 1], e[y + 1], e[z + 1])) for z in (0, 1) for y in (0, 1) for x in (0, 1)]
     whole = [torch.empty((1080, 1920, 4), device=dev) for _ in cams]
     nss = [torch.empty((1080, 1920), device=dev, dtype=torch.int32) for _ in cams]
     outs = [torch.empty((1080, 1920, 4), device=dev) for _ in cams]
@@ -788,9 +794,21 @@ def run_sortlast_1024(args):
                                    None, s)
             L.vr_composite([p.data_ptr() for p in parts[v]], [d.data_ptr() for d in depths[v]], 1920, 1080,
                            (0, 0, 0, 0), outs[v].data_ptr(), s)
+    outs_sub = [torch.empty((1080, 1920, 4), device=dev) for _ in cams]
+
+    def f_sub_cubes():
+        for v, c in enumerate(cams):
+            cc = L.make_camera(c)
+            for b, (lo, hi) in enumerate(boxes):
+                L.vr_render_subbox_of(sub_vols[b].handle, dims, lo, cc, par, lo, hi, parts[v][b].data_ptr(),
+                                      depths[v][b].data_ptr(), None, s)
+            L.vr_composite([p.data_ptr() for p in parts[v]], [d.data_ptr() for d in depths[v]], 1920, 1080,
+                           (0, 0, 0, 0), outs_sub[v].data_ptr(), s)
     reps = max(3, args.steps)
     t_whole = _time_ms(torch, f_whole, reps)
+    t_sub = _time_ms(torch, f_sub_cubes, reps)
     t_sl = _time_ms(torch, f_sort_last, reps)
+    same = all(torch.equal(a, b) for a, b in zip(outs, outs_sub))
     samples = sum(int(n.sum()) for n in nss)
     rows = [440, 540, 640]
     ref = oracle.render(host, cams[0], tf_np, synth.TF_VMIN, synth.TF_VMAX, 1.0, 2.0, rows=(rows[0], rows[-1] + 1))
@@ -799,7 +817,10 @@ def run_sortlast_1024(args):
                       "whole_ms_8_views": t_whole, "sort_last_ms_8_views": t_sl, "overhead": t_sl / t_whole,
                       "samples": samples, "sort_last_gsamples_per_s": samples / t_sl / 1e6,
                       "max_diff_vs_whole": float(max((o - w).abs().max().item() for o, w in zip(outs, whole))),
+                      "sub_cube_volumes_ms_8_views": t_sub, "sub_cube_volumes_bit_identical": same,
                       "px_err": err}))
+    for sv in sub_vols:
+        sv.close()
     vol.close()
 
 
