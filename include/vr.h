@@ -184,6 +184,15 @@ vr_status vr_volume_destroy(vr_volume_t vol);
 
 vr_status vr_volume_info(vr_volume_t vol, vr_volume_info_t *out);
 
+/* The brick layout a software-filter render of this view reads as things
+ * stand: *layout = -1 for the x-fastest bricks, else the copy id (1, 2: plain
+ * copies with y / z fastest; 3, 4, 5: paired 16-bit copies with x / y / z
+ * fastest; bit `id` of vr_volume_info's copies).  Builds nothing: a preferred
+ * copy that does not exist yet reports -1 until a render builds it.  A batched
+ * call launches one kernel per distinct layout of its views.  Errors:
+ * INVALID_ARG. */
+vr_status vr_view_layout(vr_volume_t vol, const vr_camera *cam, int *layout);
+
 /* ------------------------------------------------------------------------
  * Forward render (Sections 3.3-3.4 and 4.4).
  *

@@ -59,7 +59,8 @@ class vr_batch_opts(C.Structure):
 
 
 # every symbol include/vr.h declares
-EXPORTS = ("vr_volume_create", "vr_volume_update", "vr_volume_destroy", "vr_volume_info", "vr_render",
+EXPORTS = ("vr_volume_create", "vr_volume_update", "vr_volume_destroy", "vr_volume_info", "vr_view_layout",
+           "vr_render",
            "vr_render_backward", "vr_render_backward_views", "vr_render_batched", "vr_autotune_batched", "vr_render_batched_noalloc",
            "vr_minimap", "vr_profile", "vr_render_subbox", "vr_render_subbox_of", "vr_composite", "vr_moments",
            "vr_histogram",
@@ -93,6 +94,7 @@ def load() -> C.CDLL:
         L.vr_volume_update.argtypes = [vp, vp, C.c_int, vp]
         L.vr_volume_destroy.argtypes = [vp]
         L.vr_volume_info.argtypes = [vp, P(vr_volume_info_t)]
+        L.vr_view_layout.argtypes = [vp, P(vr_camera), P(C.c_int)]
         L.vr_render.argtypes = [vp, P(vr_camera), P(vr_params), vp, vp, vp]
         L.vr_render_backward.argtypes = [vp, P(vr_camera), P(vr_params), vp, vp, vp, vp, vp, C.c_uint, vp]
         L.vr_render_backward_views.argtypes = [vp, P(vr_grad_view), C.c_int, P(vr_params), vp, vp, C.c_uint, vp]
@@ -111,7 +113,8 @@ def load() -> C.CDLL:
         L.vr_moments.argtypes = [vp, vp, vp]
         L.vr_histogram.argtypes = [vp, C.c_double, C.c_double, C.c_int, vp, vp]
         L.vr_median.argtypes = [vp, vp, vp]
-        for name in ("vr_volume_create", "vr_volume_update", "vr_volume_destroy", "vr_volume_info", "vr_render",
+        for name in ("vr_volume_create", "vr_volume_update", "vr_volume_destroy", "vr_volume_info", "vr_view_layout",
+                     "vr_render",
                      "vr_render_backward", "vr_render_backward_views", "vr_render_batched", "vr_autotune_batched",
                      "vr_render_batched_noalloc", "vr_minimap", "vr_profile", "vr_render_subbox", "vr_render_subbox_of",
                      "vr_composite",
@@ -175,6 +178,13 @@ def vr_volume_update(vol: int, dev_cube: int, src_dtype: int, stream: int = 0):
 
 def vr_volume_destroy(vol: int):
     _check("vr_volume_destroy", load().vr_volume_destroy(vol))
+
+
+def vr_view_layout(vol: int, cam: vr_camera) -> int:
+    """-1 for the x-fastest bricks, else the id of the copy this view reads."""
+    out = C.c_int(0)
+    _check("vr_view_layout", load().vr_view_layout(vol, C.byref(cam), C.byref(out)))
+    return out.value
 
 
 def vr_volume_info(vol: int) -> dict:

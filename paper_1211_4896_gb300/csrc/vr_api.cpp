@@ -588,6 +588,17 @@ vr_status vr_volume_destroy(vr_volume_t vol)
     return VR_OK;
 }
 
+vr_status vr_view_layout(vr_volume_t vol, const vr_camera *cam, int *layout)
+{
+    g_err.clear();
+    vr_status st = check_camera(cam);
+    if (st != VR_OK) return st;
+    if (!vol) return invalid("volume handle is NULL");
+    if (!layout) return invalid("layout is NULL");
+    *layout = preferred_copy(vol, cam, false, nullptr);
+    return VR_OK;
+}
+
 vr_status vr_volume_info(vr_volume_t vol, vr_volume_info_t *out)
 {
     g_err.clear();

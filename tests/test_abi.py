@@ -114,6 +114,10 @@ def test_output_and_volume_validation(L):
     with pytest.raises(L.VRError, match="volume handle is NULL"):
         L.vr_render_backward_views(None, [L.vr_grad_view(cam, 4096, 4096, 4096)] * 3, p, 4096, None)
     with pytest.raises(L.VRError, match="volume handle is NULL"):
+        L.vr_view_layout(None, cam)
+    with pytest.raises(L.VRError, match="camera"):
+        L.vr_view_layout(None, L.make_camera(dict(_cam(), width=0)))
+    with pytest.raises(L.VRError, match="volume handle is NULL"):
         L.vr_render_subbox_of(None, (64, 64, 64), (0, 0, 0), cam, p, (0, 0, 0), (8, 8, 8), 4096, 4096, None)
     with pytest.raises(L.VRError, match="software filter"):
         L.vr_render_subbox_of(None, (64, 64, 64), (0, 0, 0), cam, L.make_params(4096, 256, -3, 50, 0.5, filter=1),

@@ -96,10 +96,15 @@ def test_rolled_view_reads_a_copy_bit_identically(P, torch, scene, kind, pair, s
     try:
         assert _copies(P, vol) == 0
         camA, camB = _cam(fa, ua, kind), _cam(fb, ub, kind)
+        L = P._lib
+        layout = lambda cam: L.vr_view_layout(vol.handle, L.make_camera(cam))   # noqa: E731
+        assert layout(camA) == -1 and layout(camB) == -1          # nothing built yet
         a, na = P.render(vol, camA, tf, VMIN, VMAX, STEP)
         assert _copies(P, vol) == x_copy
+        assert layout(camA) == (-1 if store == "f32" else 3)
         b, nb = P.render(vol, camB, tf, VMIN, VMAX, STEP)
         torch.cuda.synchronize()
+        assert layout(camB) == (order if store == "f32" else 3 + order)
         info = P._lib.vr_volume_info(vol.handle)
         assert info["copies"] == x_copy | b_copy
         per_copy = info["bytes"] * (1 if store == "f32" else 2)
