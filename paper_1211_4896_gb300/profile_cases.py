@@ -3,6 +3,9 @@
 
   python -m paper_1211_4896_gb300.profile_cases fwd    # 512^3 f32, 4 orbit views at 960x540, step 1, ERT 0.99
   python -m paper_1211_4896_gb300.profile_cases fwd16  # the same views of the cube stored as f16
+  python -m paper_1211_4896_gb300.profile_cases views16 # 512^3 f16 at 1920x1080: an axis view (0 deg) and an
+                                                       # oblique one (45 deg), forward only, each rendered twice
+  python -m paper_1211_4896_gb300.profile_cases views32 # the same views of the cube stored f32
   python -m paper_1211_4896_gb300.profile_cases bat    # the same 4 views in one batched call, f32
   python -m paper_1211_4896_gb300.profile_cases bwd    # 256^3 f32, 2 views at 512^2, step 0.5, table = ramp + 5% noise
   python -m paper_1211_4896_gb300.profile_cases bwd512 # the 512^3 differentiation workload (1024^2, step 0.5):
@@ -37,6 +40,24 @@ def case_fwd(store="f32"):
         P.render_backward(vol, c, tf, -3.0, 50.0, 1.0, img, ns, torch.randn_like(img), 0.99)
     torch.cuda.synchronize()
     print("ok", int(ns.sum()))
+
+
+def case_views(store="f16"):
+    import torch
+    import synth
+    import paper_1211_4896_gb300 as P
+    dev = torch.device("cuda")
+    dims = (512, 512, 512)
+    vol = P.Volume(synth.hi_cube(dims, 250, 25, 9, device=dev), store)
+    tf = torch.from_numpy(synth.tf_ramp(256)).to(dev)
+    ns = None
+    total = 0
+    for c in synth.orbit_cameras(dims, 8, 40.0, 1920, 1080)[:2]:       # 0 and 45 degrees
+        P.render(vol, c, tf, -3.0, 50.0, 1.0, 0.99)                       # builds the copy it reads
+        img, ns = P.render(vol, c, tf, -3.0, 50.0, 1.0, 0.99)
+        total += int(ns.sum())
+    torch.cuda.synchronize()
+    print("ok", total)
 
 
 def case_bat():
@@ -137,5 +158,5 @@ def case_stats():
 if __name__ == "__main__":
     from paper_1211_4896_gb300 import build
     build.build()
-    {"fwd": case_fwd, "fwd16": lambda: case_fwd("f16"), "bat": case_bat, "bwd": case_bwd, "bwd512": case_bwd512,
+    {"fwd": case_fwd, "fwd16": lambda: case_fwd("f16"), "bat": case_bat, "bwd": case_bwd, "bwd512": case_bwd512, "views16": case_views, "views32": lambda: case_views("f32"),
      "stats": case_stats, "skip": case_skip}[sys.argv[1] if len(sys.argv) > 1 else "fwd"]()
