@@ -277,9 +277,11 @@ vr_status vr_render_backward_views(vr_volume_t vol, const vr_grad_view *views, i
 /* ------------------------------------------------------------------------
  * Batched render (not in the paper; its "many smaller cubes" future-work
  * item motivates it): n jobs, each with its own volume, camera, parameters
- * and output, rendered by ONE persistent kernel launch whose CTAs pull ray
- * tiles of all jobs from a shared work queue (one launch per brick copy
- * the views read, so at most four).  Results equal n vr_render calls.
+ * and output, rendered by one persistent kernel launch per brick layout the
+ * views read (vr_view_layout: at most three for float storage, six for
+ * 16-bit), whose CTAs pull the ray tiles of all its jobs from a shared work
+ * queue; with use_graph the launches are replayed as one CUDA graph.
+ * Results equal n vr_render calls.
  * Software filter only.
  * ---------------------------------------------------------------------- */
 typedef struct {
