@@ -19,8 +19,12 @@
  *   - Pointers named dev_* are CUDA device pointers owned by the caller.  The
  *     library owns only what it allocates inside a vr_volume_t.
  *   - Every call that takes `cuda_stream` (a cudaStream_t, NULL = legacy
- *     default stream) only enqueues work on that stream and returns; nothing
- *     is synchronised except in vr_volume_create / vr_volume_destroy.
+ *     default stream) enqueues work on that stream and returns.  It
+ *     synchronises only in vr_volume_create / vr_volume_destroy, vr_check,
+ *     and on the first use of something a volume builds or grows lazily (a
+ *     brick copy, the per-brick value ranges of empty-space skipping, a
+ *     larger backward scratch, a batch plan), as the entry points say; device
+ *     allocations happen only then too.
  *   - Arguments are validated on the host before anything is enqueued; an
  *     invalid call returns a negative vr_status, enqueues nothing, and sets a
  *     thread-local message readable with vr_last_error().
@@ -137,6 +141,9 @@ typedef struct {
     int64_t copy_bytes;       /* device bytes of the brick copies (see vr_volume_create) */
     int copies;               /* which copies exist: bit 1 / 2 plain y- / z-fastest; bit 3 / 4 / 5
                                  paired x- / y- / z-fastest (16-bit storage) */
+    int64_t scratch_bytes;    /* device bytes of the backward scratch: the per-warp table-gradient
+                                 rows and, once a dense view has used it, the voxel-gradient quad
+                                 scratch (16 bytes per voxel) */
 } vr_volume_info_t;
 
 /* ------------------------------------------------------------------------

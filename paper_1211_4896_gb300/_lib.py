@@ -42,7 +42,7 @@ class vr_params(C.Structure):
 class vr_volume_info_t(C.Structure):
     _fields_ = [("dims", C.c_int64 * 3), ("store_dtype", C.c_int), ("brick", C.c_int),
                 ("bricks", C.c_int64 * 3), ("bytes", C.c_int64), ("dense_bytes", C.c_int64),
-                ("copy_bytes", C.c_int64), ("copies", C.c_int)]
+                ("copy_bytes", C.c_int64), ("copies", C.c_int), ("scratch_bytes", C.c_int64)]
 
 
 class vr_job(C.Structure):
@@ -192,7 +192,7 @@ def vr_volume_info(vol: int) -> dict:
     _check("vr_volume_info", load().vr_volume_info(vol, C.byref(info)))
     return dict(dims=tuple(info.dims), store_dtype=info.store_dtype, brick=info.brick,
                 bricks=tuple(info.bricks), bytes=info.bytes, dense_bytes=info.dense_bytes,
-                copy_bytes=info.copy_bytes, copies=info.copies)
+                copy_bytes=info.copy_bytes, copies=info.copies, scratch_bytes=info.scratch_bytes)
 
 
 def vr_render(vol: int, cam: vr_camera, params: vr_params, dev_rgba_out: int, dev_nsamples_out: int | None,

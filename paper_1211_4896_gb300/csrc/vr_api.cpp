@@ -614,6 +614,8 @@ vr_status vr_volume_info(vr_volume_t vol, vr_volume_info_t *out)
     out->dense_bytes = (int64_t)vol->dense_bytes;
     out->copy_bytes = 0;
     out->copies = 0;
+    out->scratch_bytes = (int64_t)(vol->wtab_cap * sizeof(float)) +
+                         (vol->gquad ? (int64_t)sizeof(float4) * vol->dims[0] * vol->dims[1] * vol->dims[2] : 0);
     for (int c = 1; c < kCopyIds; ++c)
         if (vol->copies[c]) {
             out->copy_bytes += (int64_t)copy_bytes(vol, c);

@@ -129,6 +129,8 @@ def test_voxel_gradient_direct_and_scratch_reductions_agree(P, torch, dims, bric
         d, s = res["direct"][1], res["scratch"][1]
         assert (d - s).abs().max().item() <= 1e-4 * d.abs().max().item()
         assert (s != 0).float().mean().item() > 0.05
+        info = P._lib.vr_volume_info(vol.handle)                # the quad scratch is held and reported
+        assert info["scratch_bytes"] >= 16 * int(np.prod(dims))
     finally:
         vol.close()
 
