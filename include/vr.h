@@ -452,10 +452,24 @@ vr_status vr_median(vr_volume_t vol, double *dev_median, void *cuda_stream);
 /* Synchronises cuda_stream and reports whether a bounded device-side wait of an
  * earlier call on this volume gave up (the staged kernels wait on the copy
  * engine with an iteration limit; a timeout leaves that call's results
- * invalid).  Returns VR_OK, or VR_ERR_TIMEOUT once per occurrence (the flag is
- * cleared).  The paper has no such mechanism; it is part of this library's
- * failure detection. */
+ * invalid): VR_ERR_TIMEOUT; or whether the bounds-check build caught an index
+ * outside its buffer (and skipped that access): VR_ERR_INTERNAL.  Returns
+ * VR_OK otherwise; each report is given once (the flags are cleared).  The
+ * paper has no such mechanism; it is part of this library's failure
+ * detection. */
 vr_status vr_check(vr_volume_t vol, void *cuda_stream);
+
+/* 1 when this library is the bounds-check build (compiled with
+ * -DVR_BOUNDS_CHECK: every voxel gather, gradient scatter, table-bin,
+ * per-brick and mini-map index is tested against its buffer in the kernels
+ * before the access, a stand-in for a memory checker), else 0. */
+int vr_bounds_checked(void);
+
+/* Self-test of the bounds-check report (no counterpart in the paper): a
+ * one-thread kernel tests an index one past the end of a range -- nothing is
+ * read or written -- so the next vr_check returns VR_ERR_INTERNAL once.
+ * Works in either build.  Errors: INVALID_ARG, CUDA. */
+vr_status vr_selftest_bounds(vr_volume_t vol, void *cuda_stream);
 
 /* Failure-detection self-test (no counterpart in the paper): enqueues on
  * cuda_stream one wait, with the staged kernels' bounded mbarrier wait, on a

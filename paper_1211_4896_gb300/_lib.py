@@ -12,7 +12,9 @@ import os
 import threading
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "_build", "libvr.so")
+# VR_LIBRARY selects another build of the library (the bounds-check variant
+# _build/libvr_checked.so); the default is the in-tree libvr.so.
+LIB_PATH = os.environ.get("VR_LIBRARY") or os.path.join(_HERE, "_build", "libvr.so")
 
 VR_OK, VR_ERR_INVALID_ARG, VR_ERR_UNSUPPORTED, VR_ERR_OOM, VR_ERR_CUDA, VR_ERR_TIMEOUT, VR_ERR_INTERNAL = \
     0, -1, -2, -3, -4, -5, -6
@@ -64,7 +66,8 @@ EXPORTS = ("vr_volume_create", "vr_volume_update", "vr_volume_destroy", "vr_volu
            "vr_render_backward", "vr_render_backward_views", "vr_render_batched", "vr_autotune_batched", "vr_render_batched_noalloc",
            "vr_minimap", "vr_profile", "vr_render_subbox", "vr_render_subbox_of", "vr_composite", "vr_moments",
            "vr_histogram",
-           "vr_median", "vr_check", "vr_selftest_timeout", "vr_last_error", "vr_version")
+           "vr_median", "vr_check", "vr_selftest_timeout", "vr_selftest_bounds", "vr_bounds_checked",
+           "vr_last_error", "vr_version")
 VR_NOALLOC_MAX_JOBS = 256
 
 _lock = threading.Lock()
@@ -103,6 +106,9 @@ def load() -> C.CDLL:
         L.vr_render_batched_noalloc.argtypes = [P(vr_job), C.c_int, C.c_int, C.c_int, vp]
         L.vr_check.argtypes = [vp, vp]
         L.vr_selftest_timeout.argtypes = [vp, vp]
+        L.vr_selftest_bounds.argtypes = [vp, vp]
+        L.vr_bounds_checked.argtypes = []
+        L.vr_bounds_checked.restype = C.c_int
         L.vr_minimap.argtypes = [vp, P(C.c_int * 3), vp, vp]
         L.vr_profile.argtypes = [vp, P(vr_camera), C.c_float, C.c_int, C.c_int, vp, C.c_uint32, vp, vp]
         L.vr_render_subbox.argtypes = [vp, P(vr_camera), P(vr_params), P(C.c_int * 3), P(C.c_int * 3), vp, vp, vp,
@@ -118,7 +124,8 @@ def load() -> C.CDLL:
                      "vr_render_backward", "vr_render_backward_views", "vr_render_batched", "vr_autotune_batched",
                      "vr_render_batched_noalloc", "vr_minimap", "vr_profile", "vr_render_subbox", "vr_render_subbox_of",
                      "vr_composite",
-                     "vr_moments", "vr_histogram", "vr_median", "vr_check", "vr_selftest_timeout"):
+                     "vr_moments", "vr_histogram", "vr_median", "vr_check", "vr_selftest_timeout",
+                     "vr_selftest_bounds"):
             getattr(L, name).restype = C.c_int
         L.vr_last_error.argtypes = []
         L.vr_last_error.restype = C.c_char_p
@@ -285,6 +292,15 @@ def vr_histogram(vol: int, lo: float, hi: float, nbins: int, dev_counts: int, st
 
 def vr_median(vol: int, dev_median: int, stream: int = 0):
     _check("vr_median", load().vr_median(vol, dev_median, stream))
+
+
+def vr_selftest_bounds(vol: int, stream: int = 0):
+    _check("vr_selftest_bounds", load().vr_selftest_bounds(vol, stream))
+
+
+def vr_bounds_checked() -> bool:
+    """True for the bounds-check build of the library."""
+    return bool(load().vr_bounds_checked())
 
 
 def vr_selftest_timeout(vol: int, stream: int = 0):

@@ -257,7 +257,7 @@ def render_diff(cube, tf, vol, cam, vmin, vmax, step, ert=2.0, bg=(0.0, 0.0, 0.0
 def render_batched(jobs, use_graph: bool = True, tile=(8, 4), ctas_per_sm: int = 0, stream=None,
                    opts: L.vr_batch_opts | None = None):
     """jobs: list of dicts with keys vol, cam, tf, vmin, vmax, step, ert, bg, out, nsamples (optional).
-    Renders all of them in one persistent launch."""
+    Renders all of them in one persistent launch per brick layout their views read."""
     cj = []
     for j in jobs:
         p = _params(j["tf"], j["vmin"], j["vmax"], j["step"], j.get("ert", 2.0), j.get("bg", (0, 0, 0, 0)),

@@ -14,6 +14,12 @@ namespace vr {
 
 static thread_local std::string g_err;
 
+#ifdef VR_BOUNDS_CHECK
+static constexpr bool kBoundsChecked = true;
+#else
+static constexpr bool kBoundsChecked = false;
+#endif
+
 void set_error(const std::string &msg) { g_err = msg; }
 
 vr_status cuda_fail(cudaError_t e, const char *what)
@@ -231,6 +237,8 @@ VolDev vol_dev(const vr_volume *vol)
     v.stride = vol->stride;
     v.order = 0;
     v.paired = 0;
+    v.nelem = vol->nb[0] * vol->nb[1] * vol->nb[2] * vol->stride;
+    v.status = vol->counters + vol->counter_slots - 1;
     return v;
 }
 
@@ -1001,6 +1009,18 @@ vr_status vr_selftest_timeout(vr_volume_t vol, void *cuda_stream)
     return VR_OK;
 }
 
+vr_status vr_selftest_bounds(vr_volume_t vol, void *cuda_stream)
+{
+    g_err.clear();
+    vr_status st = check_volume(vol);
+    if (st != VR_OK) return st;
+    cudaError_t e = launch_bounds_selftest(status_word(vol), static_cast<cudaStream_t>(cuda_stream));
+    if (e != cudaSuccess) return cuda_fail(e, "vr_selftest_bounds launch");
+    return VR_OK;
+}
+
+int vr_bounds_checked(void) { return kBoundsChecked ? 1 : 0; }
+
 vr_status vr_check(vr_volume_t vol, void *cuda_stream)
 {
     g_err.clear();
@@ -1014,8 +1034,13 @@ vr_status vr_check(vr_volume_t vol, void *cuda_stream)
     if (flag) {
         cudaMemsetAsync(status_word(vol), 0, sizeof(unsigned), s);
         cudaStreamSynchronize(s);
-        set_error("a bounded device-side wait gave up in an earlier call on this volume (its results are invalid)");
-        return VR_ERR_TIMEOUT;
+        if (flag & kStatusTimeout) {
+            set_error("a bounded device-side wait gave up in an earlier call on this volume (its results are invalid)");
+            return VR_ERR_TIMEOUT;
+        }
+        set_error("an index outside its buffer was caught in an earlier call on this volume and the access "
+                  "skipped (its results are invalid)");
+        return VR_ERR_INTERNAL;
     }
     return VR_OK;
 }

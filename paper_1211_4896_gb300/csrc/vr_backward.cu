@@ -115,6 +115,8 @@ struct GradDev {
     float4 *quad;
     long long su, sv, sw;
     int axis;
+    long long n;              // voxels (the bounds-check build tests indices against it)
+    unsigned *status;
 };
 
 // A ray's pending voxel-gradient sums for the cell whose corner (x0, y0, z0)
@@ -152,6 +154,10 @@ struct CellRun {
     }
     __device__ __forceinline__ static void plane(const GradDev &g, long long base, const float (&p)[4])
     {
+        if constexpr (kBoundsCheck) {
+            if (!index_ok(g.status, base, g.n) || !index_ok(g.status, base + (g.quad ? 0 : g.su + g.sv), g.n))
+                return;
+        }
         if (g.quad) {
             red_add_v4(g.quad + base, make_float4(p[0], p[1], p[2], p[3]));
         } else if (g.su == 1) {                               // (0,0)-(1,0) and (0,1)-(1,1) are x-neighbours
@@ -245,7 +251,9 @@ __global__ void __launch_bounds__(kBwdThreads) bwd_kernel(VolDev v, CamDev c, Pa
             // om is in (0, 1] where it divides: the fast reciprocal-based division is
             // within 2 ulp there
             const float da = T * cg - (om > 0.0f ? __fdividef(R, om) : 0.0f);
-            if (aT != 0.0f || da != 0.0f) {
+            bool bins_ok = true;                        // bins i0 and i0 + 1 exist
+            if constexpr (kBoundsCheck) bins_ok = index_ok(v.status, tp.i0, p.K - 1);
+            if (bins_ok && (aT != 0.0f || da != 0.0f)) {
                 bins.add(row, tp.i0, 1.0f - tp.w, tp.w, aT, da, g);
                 if (gd.vox && tp.interior) {
                     // dr . de with dr = (aT g.rgb, da)
@@ -326,6 +334,8 @@ static GradDev grad_dev(const VolDev &v, float *grad_vox, float4 *grad_quad, int
     gd.su = axis == 0 ? nx : 1;
     gd.sv = axis == 2 ? nx : nyx;
     gd.sw = axis == 0 ? 1 : (axis == 1 ? nx : nyx);
+    gd.n = nyx * v.nz;
+    gd.status = v.status;
     return gd;
 }
 

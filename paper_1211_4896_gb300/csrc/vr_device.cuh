@@ -14,6 +14,25 @@ namespace vr {
 
 constexpr unsigned kFull = 0xffffffffu;
 
+// Bounds-check build (-DVR_BOUNDS_CHECK, a stand-in for a memory checker):
+// every voxel gather, gradient scatter, table-bin and per-brick index is
+// tested against its buffer before the access; a failing index sets
+// kStatusOutOfBounds in the volume's status word (vr_check reports it) and the
+// access is skipped.  The normal build compiles the tests away.
+#ifdef VR_BOUNDS_CHECK
+constexpr bool kBoundsCheck = true;
+#else
+constexpr bool kBoundsCheck = false;
+#endif
+
+// True when 0 <= i < n; otherwise records the violation in *status.
+__device__ __forceinline__ bool index_ok(unsigned *status, long long i, long long n)
+{
+    if (i >= 0 && i < n) return true;
+    if (status) atomicOr(status, kStatusOutOfBounds);
+    return false;
+}
+
 // ---------------------------------------------------------------------------
 // Voxel loads (read-only path), widened to float.
 // ---------------------------------------------------------------------------
@@ -251,6 +270,14 @@ template <typename T, int LOG2B, int L>
 __device__ __forceinline__ void fetch_corners(const VolDev &v, const Cell &c, Gathered<T, L> &f)
 {
     using O = BrickOrder<LOG2B, L>;
+    if constexpr (kBoundsCheck) {
+        constexpr long long span = is_pair<T>::value ? (L == 0 ? O::SY : O::SX) + (L == 2 ? O::SY : O::SZ)
+                                                     : O::SX + O::SY + O::SZ;
+        if (!index_ok(v.status, c.base, v.nelem) || !index_ok(v.status, c.base + span, v.nelem)) {
+            f = Gathered<T, L>{};
+            return;
+        }
+    }
     if constexpr (is_pair<T>::value) {
         using V = typename T::V;
         const V *b = static_cast<const V *>(v.data) + c.base;

@@ -52,6 +52,8 @@ struct VolDev {
     long long stride;      // elements per brick (>= (B+1)^3, padded)
     int order;             // element order inside a brick (0: x, 1: y, 2: z fastest)
     int paired;            // 1: each element holds (own value, next value along the fastest axis)
+    long long nelem;       // elements in the buffer (bricks x stride), for the bounds-check build
+    unsigned *status;      // the volume's status word (timeouts, caught out-of-range indices)
 };
 
 // Dense copy of the volume, x fastest, rows padded to a multiple of 8
@@ -127,6 +129,10 @@ cudaError_t launch_forward_texture(const vr_volume *vol, const CamDev &c, const 
                                    uint32_t *nsamples, unsigned *counter, cudaStream_t s);
 // Brick copy a software-filter view reads: -1 the bricks themselves, else a
 // copy id of vr_volume.copies (element order copy_order, paired if >= 3).
+// Bits of a volume's device status word (read and cleared by vr_check).
+constexpr unsigned kStatusTimeout = 1u;        // a bounded wait gave up
+constexpr unsigned kStatusOutOfBounds = 2u;    // an index outside its buffer was caught and skipped
+
 constexpr int kCopyIds = 6;
 inline bool copy_paired(int copy) { return copy >= 3; }
 inline int copy_order(int copy) { return copy >= 3 ? copy - 3 : copy; }
@@ -160,6 +166,7 @@ cudaError_t launch_backward_staged(const DenseDev &d, vr_dtype dt, const CamDev 
                                    unsigned *counter, unsigned *status, cudaStream_t s);
 int occupancy_blocks(const void *fn, int threads, size_t smem);
 cudaError_t launch_wait_selftest(unsigned *status, cudaStream_t s);
+cudaError_t launch_bounds_selftest(unsigned *status, cudaStream_t s);
 // Other uses of the march (vr_modes.cu).
 cudaError_t launch_mip(const VolDev &v, vr_dtype dt, const CamDev &c, const ParamDev &p, float4 *out,
                        uint32_t *nsamples, unsigned *counter, cudaStream_t s);

@@ -101,6 +101,7 @@ struct MiniDev {
     const float2 *mm;
     int mx, my, mz;
     float rx, ry, rz;          // 1 / region size
+    unsigned *status;          // the bounds-check build's report
 };
 
 __device__ __forceinline__ void mini_axis(float p, float rinv, int m, int &i0, int &i1, float &w)
@@ -129,6 +130,11 @@ struct SigmaMap {
         mini_axis((float)c.y0 + c.fy, m.ry, m.my, y0, y1, wy);
         mini_axis((float)c.z0 + c.fz, m.rz, m.mz, z0, z1, wz);
         const long long sy = m.mx, sz = (long long)m.mx * m.my;
+        if constexpr (kBoundsCheck) {
+            if (!index_ok(m.status, z0 * sz + y0 * sy + x0, sz * m.mz) ||
+                !index_ok(m.status, z1 * sz + y1 * sy + x1, sz * m.mz))
+                return 0.0f;
+        }
         const float2 *b0 = m.mm + z0 * sz, *b1 = m.mm + z1 * sz;
         const float2 a000 = __ldg(b0 + y0 * sy + x0), a100 = __ldg(b0 + y0 * sy + x1);
         const float2 a010 = __ldg(b0 + y1 * sy + x0), a110 = __ldg(b0 + y1 * sy + x1);
@@ -206,6 +212,7 @@ cudaError_t launch_sigma(const VolDev &v, vr_dtype dt, const CamDev &c, const Pa
     m.rx = (float)(1.0 / region[0]);
     m.ry = (float)(1.0 / region[1]);
     m.rz = (float)(1.0 / region[2]);
+    m.status = v.status;
     const int tiles_x = (c.W + 7) / 8, tiles_y = (c.H + 3) / 4;
     const unsigned ntiles = (unsigned)tiles_x * (unsigned)tiles_y;
     cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(unsigned), s);

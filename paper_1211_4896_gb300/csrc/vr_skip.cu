@@ -148,7 +148,9 @@ __global__ void __launch_bounds__(kSkipThreads) skip_kernel(VolDev v, CamDev c, 
                 const long long brick = ((long long)bz * v.nby + by) * v.nbx + bx;
                 if (brick != last) {
                     last = brick;
-                    last_empty = brick_transparent(__ldg(range + brick), p, nz_prefix);
+                    bool ok = true;
+                    if constexpr (kBoundsCheck) ok = index_ok(v.status, brick, (long long)v.nbx * v.nby * v.nbz);
+                    last_empty = ok && brick_transparent(__ldg(range + brick), p, nz_prefix);
                     if (last_empty) {
                         // every sample more than one step before the ray leaves the brick's
                         // box is inside it: jump there; the last ones are stepped one by one

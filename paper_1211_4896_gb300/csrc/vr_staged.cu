@@ -80,7 +80,7 @@ __device__ __forceinline__ void mbar_wait(uint64_t *bar, unsigned parity, unsign
                      : "=r"(done) : "r"(a), "r"(parity) : "memory");
         if (done) return;
     }
-    atomicOr(status, 1u);
+    atomicOr(status, kStatusTimeout);
 }
 
 // Failure-detection self-test: one thread waits, with the bounded wait of the
@@ -96,6 +96,20 @@ __global__ void wait_selftest_kernel(unsigned *status, unsigned spins)
         mbar_wait(&bar, 0u, status, spins);
         asm volatile("mbarrier.inval.shared::cta.b64 [%0];\n" ::"r"(smem_u32(&bar)) : "memory");
     }
+}
+
+// Failure-detection self-test of the bounds-check report: tests an index one
+// past the end of an n-element range (nothing is accessed), so the volume's
+// status word records a caught violation.
+__global__ void bounds_selftest_kernel(unsigned *status)
+{
+    if (threadIdx.x == 0) index_ok(status, 1, 1);
+}
+
+cudaError_t launch_bounds_selftest(unsigned *status, cudaStream_t s)
+{
+    bounds_selftest_kernel<<<1, 32, 0, s>>>(status);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_wait_selftest(unsigned *status, cudaStream_t s)
