@@ -465,6 +465,14 @@ vr_status vr_check(vr_volume_t vol, void *cuda_stream);
  * before the access, a stand-in for a memory checker), else 0. */
 int vr_bounds_checked(void);
 
+/* Failure injection for tests (no counterpart in the paper): the library's
+ * device allocation that follows `after` successful ones fails once, as if
+ * the device were out of memory; a negative value cancels.  Every entry point
+ * then reports VR_ERR_OOM or falls back as documented (a brick copy or the
+ * backward's quad scratch that cannot be allocated is simply not used), and
+ * leaves its handle usable.  Process-wide. */
+void vr_debug_fail_alloc(int after);
+
 /* Self-test of the bounds-check report (no counterpart in the paper): a
  * one-thread kernel tests an index one past the end of a range -- nothing is
  * read or written -- so the next vr_check returns VR_ERR_INTERNAL once.

@@ -67,7 +67,7 @@ EXPORTS = ("vr_volume_create", "vr_volume_update", "vr_volume_destroy", "vr_volu
            "vr_minimap", "vr_profile", "vr_render_subbox", "vr_render_subbox_of", "vr_composite", "vr_moments",
            "vr_histogram",
            "vr_median", "vr_check", "vr_selftest_timeout", "vr_selftest_bounds", "vr_bounds_checked",
-           "vr_last_error", "vr_version")
+           "vr_debug_fail_alloc", "vr_last_error", "vr_version")
 VR_NOALLOC_MAX_JOBS = 256
 
 _lock = threading.Lock()
@@ -107,6 +107,8 @@ def load() -> C.CDLL:
         L.vr_check.argtypes = [vp, vp]
         L.vr_selftest_timeout.argtypes = [vp, vp]
         L.vr_selftest_bounds.argtypes = [vp, vp]
+        L.vr_debug_fail_alloc.argtypes = [C.c_int]
+        L.vr_debug_fail_alloc.restype = None
         L.vr_bounds_checked.argtypes = []
         L.vr_bounds_checked.restype = C.c_int
         L.vr_minimap.argtypes = [vp, P(C.c_int * 3), vp, vp]
@@ -296,6 +298,12 @@ def vr_median(vol: int, dev_median: int, stream: int = 0):
 
 def vr_selftest_bounds(vol: int, stream: int = 0):
     _check("vr_selftest_bounds", load().vr_selftest_bounds(vol, stream))
+
+
+def vr_debug_fail_alloc(after: int):
+    """Makes the library's device allocation after `after` successful ones
+    fail once (negative: cancel)."""
+    load().vr_debug_fail_alloc(int(after))
 
 
 def vr_bounds_checked() -> bool:

@@ -30,6 +30,26 @@ vr_status cuda_fail(cudaError_t e, const char *what)
 
 bool is_aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
+// Every device allocation of the library goes through dev_alloc, so that a
+// test can make one of them fail (vr_debug_fail_alloc) and check the error
+// paths and fallbacks.
+static std::mutex g_fail_mu;
+static long long g_fail_after = -1;      // successful allocations before the injected failure; -1: none
+
+cudaError_t dev_alloc(void **p, size_t bytes)
+{
+    {
+        std::lock_guard<std::mutex> g(g_fail_mu);
+        if (g_fail_after == 0) {
+            g_fail_after = -1;
+            *p = nullptr;
+            return cudaErrorMemoryAllocation;
+        }
+        if (g_fail_after > 0) --g_fail_after;
+    }
+    return cudaMalloc(p, bytes);
+}
+
 static vr_status invalid(const std::string &msg)
 {
     set_error(msg);
@@ -327,7 +347,7 @@ int preferred_copy(vr_volume *vol, const vr_camera *cam, bool may_build, cudaStr
         return -1;
     }
     void *p = nullptr;
-    if (cudaMalloc(&p, bytes) != cudaSuccess) {
+    if (dev_alloc(&p, bytes) != cudaSuccess) {
         cudaGetLastError();
         return -1;
     }
@@ -381,7 +401,7 @@ static float4 *grad_quad_for(vr_volume *vol, const vr_grad_view *views, int n, c
         return nullptr;
     }
     void *p = nullptr;
-    if (cudaMalloc(&p, bytes) != cudaSuccess) {
+    if (dev_alloc(&p, bytes) != cudaSuccess) {
         cudaGetLastError();
         return nullptr;
     }
@@ -424,7 +444,7 @@ cudaError_t ensure_wtab(vr_volume *vol, size_t floats, cudaStream_t s)
         vol->wtab = nullptr;
         vol->wtab_cap = 0;
     }
-    cudaError_t e = cudaMalloc(&vol->wtab, floats * sizeof(float));
+    cudaError_t e = dev_alloc(reinterpret_cast<void **>(&vol->wtab), floats * sizeof(float));
     if (e != cudaSuccess) {
         vol->wtab = nullptr;
         return e;
@@ -441,7 +461,7 @@ static vr_status ensure_dense(vr_volume *vol, cudaStream_t s)
     const int px = (int)((vol->dims[0] + 7) / 8 * 8);
     const size_t bytes = (size_t)px * (size_t)vol->dims[1] * (size_t)vol->dims[2] * (vol->store_dtype == VR_F32 ? 4 : 2);
     void *p = nullptr;
-    if (cudaMalloc(&p, bytes) != cudaSuccess) {
+    if (dev_alloc(&p, bytes) != cudaSuccess) {
         cudaGetLastError();
         set_error("staged filter: cannot allocate the dense copy (" + std::to_string(bytes) + " bytes)");
         return VR_ERR_OOM;
@@ -541,7 +561,7 @@ vr_status vr_volume_create(const void *dev_cube, vr_dtype src_dtype, vr_dtype st
     vol->bytes = (size_t)nbricks * (size_t)vol->stride * dtype_size(store_dtype);
     cudaError_t e = cudaGetDevice(&vol->device);
     if (e != cudaSuccess) { free_volume(vol); return cuda_fail(e, "cudaGetDevice"); }
-    e = cudaMalloc(&vol->bricks, vol->bytes);
+    e = dev_alloc(&vol->bricks, vol->bytes);
     if (e != cudaSuccess) {
         vol->bricks = nullptr;
         free_volume(vol);
@@ -550,7 +570,7 @@ vr_status vr_volume_create(const void *dev_cube, vr_dtype src_dtype, vr_dtype st
         return VR_ERR_OOM;
     }
     vol->counter_slots = 64;
-    e = cudaMalloc(&vol->counters, sizeof(unsigned) * vol->counter_slots);
+    e = dev_alloc(reinterpret_cast<void **>(&vol->counters), sizeof(unsigned) * vol->counter_slots);
     if (e != cudaSuccess) { vol->counters = nullptr; free_volume(vol); return cuda_fail(e, "cudaMalloc(counters)"); }
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
     e = cudaMemsetAsync(vol->counters, 0, sizeof(unsigned) * vol->counter_slots, s);
@@ -661,7 +681,7 @@ vr_status vr_render(vr_volume_t vol, const vr_camera *cam, const vr_params *para
     if (params->skip_empty) {
         if (!vol->brick_range) {
             const size_t n = (size_t)(vol->nb[0] * vol->nb[1] * vol->nb[2]);
-            e = cudaMalloc(&vol->brick_range, n * sizeof(float2));
+            e = dev_alloc(reinterpret_cast<void **>(&vol->brick_range), n * sizeof(float2));
             if (e != cudaSuccess) {
                 vol->brick_range = nullptr;
                 return cuda_fail(e, "vr_render: brick ranges");
@@ -945,7 +965,7 @@ vr_status vr_composite(int k, const float *const *dev_partials, const float *con
 static vr_status ensure_stats(vr_volume *vol)
 {
     if (vol->stats) return VR_OK;
-    cudaError_t e = cudaMalloc(&vol->stats, stats_scratch_bytes());
+    cudaError_t e = dev_alloc(&vol->stats, stats_scratch_bytes());
     if (e != cudaSuccess) {
         vol->stats = nullptr;
         return cuda_fail(e, "statistics scratch");
@@ -1007,6 +1027,12 @@ vr_status vr_selftest_timeout(vr_volume_t vol, void *cuda_stream)
     cudaError_t e = launch_wait_selftest(status_word(vol), static_cast<cudaStream_t>(cuda_stream));
     if (e != cudaSuccess) return cuda_fail(e, "vr_selftest_timeout launch");
     return VR_OK;
+}
+
+void vr_debug_fail_alloc(int after)
+{
+    std::lock_guard<std::mutex> g(g_fail_mu);
+    g_fail_after = after < 0 ? -1 : after;
 }
 
 vr_status vr_selftest_bounds(vr_volume_t vol, void *cuda_stream)

@@ -354,8 +354,8 @@ extern "C" vr_status vr_render_batched(const vr_job *jobs, int n, const vr_batch
         for (int g = 0; g < kGroups; ++g) plan->seg[g] = seg[g];
         plan->log2_tw = log2_of(tile_w);
         plan->device = dev;
-        cudaError_t e = cudaMalloc(&plan->djobs, sizeof(JobDev) * (size_t)n);
-        if (e == cudaSuccess) e = cudaMalloc(&plan->counter, kGroups * sizeof(unsigned));
+        cudaError_t e = dev_alloc(reinterpret_cast<void **>(&plan->djobs), sizeof(JobDev) * (size_t)n);
+        if (e == cudaSuccess) e = dev_alloc(reinterpret_cast<void **>(&plan->counter), kGroups * sizeof(unsigned));
         if (e == cudaSuccess)
             e = cudaMemcpyAsync(plan->djobs, hj.data(), sizeof(JobDev) * (size_t)n, cudaMemcpyHostToDevice, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);

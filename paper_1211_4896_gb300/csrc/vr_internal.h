@@ -110,6 +110,7 @@ namespace vr {
 void set_error(const std::string &msg);
 vr_status cuda_fail(cudaError_t e, const char *what);
 bool is_aligned16(const void *p);
+cudaError_t dev_alloc(void **p, size_t bytes);     // every device allocation of the library
 
 // Host-side preparation (vr_api.cpp).
 vr_status prepare_camera(const vr_volume *vol, const vr_camera *cam, CamDev *out);
