@@ -1,6 +1,8 @@
 // vr_api.cpp -- host side of the C ABI declared in include/vr.h: argument
 // validation, volume handles, camera preparation and kernel dispatch.
 #include <cmath>
+#include <cstdarg>
+#include <cstdio>
 #include <cstdlib>
 #include <cstring>
 #include <mutex>
@@ -29,6 +31,29 @@ vr_status cuda_fail(cudaError_t e, const char *what)
 }
 
 bool is_aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+// VR_LOG=1 in the environment: one line on stderr per launch decision (brick
+// layout of a view, grid of a launch, the backward's voxel-gradient form, the
+// groups of a batch).
+bool log_enabled()
+{
+    static const bool on = [] {
+        const char *e = std::getenv("VR_LOG");
+        return e && e[0] && e[0] != '0';
+    }();
+    return on;
+}
+
+void log_line(const char *fmt, ...)
+{
+    if (!log_enabled()) return;
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    std::vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    std::fprintf(stderr, "vr: %s\n", buf);
+}
 
 // Every device allocation of the library goes through dev_alloc, so that a
 // test can make one of them fail (vr_debug_fail_alloc) and check the error
@@ -335,6 +360,8 @@ int preferred_copy(vr_volume *vol, const vr_camera *cam, bool may_build, cudaStr
     if (copy == 0) return -1;
     if (vol->copies[copy]) return copy;
     if (!may_build) return -1;
+    log_line("view %dx%d prefers brick copy %d (%s); building it", cam->width, cam->height, copy,
+             copy_paired(copy) ? "paired" : "plain");
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
         cudaGetLastError();
@@ -386,8 +413,13 @@ static float4 *grad_quad_for(vr_volume *vol, const vr_grad_view *views, int n, c
         }
         // every view's kernel reads and writes the scratch once more (it does not
         // stay in L2), so the views must be dense on average, not only together
-        if (!(density >= (double)n)) return nullptr;
+        if (!(density >= (double)n)) {
+            log_line("backward of %d view(s): direct voxel-gradient reductions (%.2f samples per voxel per view)", n,
+                     density / n);
+            return nullptr;
+        }
     }
+    log_line("backward of %d view(s): voxel gradient through the quad scratch", n);
     if (vol->gquad) return vol->gquad;
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) {

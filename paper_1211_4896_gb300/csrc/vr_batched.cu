@@ -212,6 +212,8 @@ static void size_grids(Segment seg[kGroups], int ctas)
         const unsigned grid = (unsigned)(per_sm * sm_count());
         const unsigned useful = (g.total_tiles + kBatThreads / 32 - 1) / (kBatThreads / 32);
         g.grid = grid < useful ? grid : (useful ? useful : 1);
+        log_line("batch, brick layout %d: %d job(s), %u tiles, grid %u x %d threads", o - 1, g.njobs, g.total_tiles,
+                 g.grid, kBatThreads);
     }
 }
 

@@ -129,6 +129,8 @@ static cudaError_t launch_fwd_t(const VolDev &v, const CamDev &c, const ParamDev
     if (grid < 1) grid = 1;
     cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(unsigned), s);
     if (e != cudaSuccess) return e;
+    log_line("forward %dx%d: layout order %d%s, %u tiles of 8x4 rays, grid %u x %d threads (%d per SM)", c.W, c.H,
+             v.order, v.paired ? " paired" : "", ntiles, grid, kFwdThreads, per_sm);
     fn<<<grid, kFwdThreads, 0, s>>>(v, c, p, out, nsamples, counter, tiles_x, ntiles);
     return cudaGetLastError();
 }

@@ -111,6 +111,8 @@ void set_error(const std::string &msg);
 vr_status cuda_fail(cudaError_t e, const char *what);
 bool is_aligned16(const void *p);
 cudaError_t dev_alloc(void **p, size_t bytes);     // every device allocation of the library
+bool log_enabled();                                  // VR_LOG set
+void log_line(const char *fmt, ...);                 // one "vr: ..." line on stderr when VR_LOG is set
 
 // Host-side preparation (vr_api.cpp).
 vr_status prepare_camera(const vr_volume *vol, const vr_camera *cam, CamDev *out);
