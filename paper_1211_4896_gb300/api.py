@@ -254,6 +254,53 @@ def render_diff(cube, tf, vol, cam, vmin, vmax, step, ert=2.0, bg=(0.0, 0.0, 0.0
     return RenderFunction.apply(cube, tf, vol, cam, vmin, vmax, step, ert, bg)
 
 
+def autotune_key(jobs) -> str:
+    """Cache key of a job list for the batched autotuner: the device, the
+    storage type and brick size, and every job's volume and image size."""
+    import hashlib
+    dev = torch.cuda.get_device_name(jobs[0]["vol"].device) if torch.cuda.is_available() else "cpu"
+    parts = [dev, str(jobs[0]["vol"].store_dtype), str(jobs[0]["vol"].info["brick"])]
+    for j in jobs:
+        parts.append("%s:%dx%d" % ("x".join(map(str, j["vol"].shape[::-1])), int(j["cam"]["width"]),
+                                   int(j["cam"]["height"])))
+    return hashlib.sha1("|".join(parts).encode()).hexdigest()
+
+
+def cached_tuning(key: str, tune, cache_path=None) -> dict:
+    """Looks `key` up in the JSON file cache_path (else $VR_AUTOTUNE_CACHE;
+    no cache when neither is set); on a miss calls tune() -> dict and stores
+    its result (written to a temporary file, then renamed)."""
+    import json
+    import os
+    path = cache_path or os.environ.get("VR_AUTOTUNE_CACHE")
+    table = {}
+    if path and os.path.exists(path):
+        with open(path) as f:
+            table = json.load(f)
+        if key in table:
+            return dict(table[key])
+    best = dict(tune())
+    if path:
+        table[key] = best
+        tmp = "%s.tmp%d" % (path, os.getpid())
+        with open(tmp, "w") as f:
+            json.dump(table, f, indent=1, sort_keys=True)
+        os.replace(tmp, path)
+    return best
+
+
+def autotune_batched(jobs, cache_path=None, stream=None) -> L.vr_batch_opts:
+    """Ray-tile shape and CTAs per SM for this job list (vr_autotune_batched
+    tries each and keeps the fastest), remembered across processes in the
+    autotune cache (cache_path or $VR_AUTOTUNE_CACHE) under autotune_key."""
+    def tune():
+        cj = render_batched(jobs, use_graph=False, stream=stream)
+        best = L.vr_autotune_batched(cj, L.vr_batch_opts(0, 0, 0, 0), _stream(stream))
+        return {"tile_w": best.tile_w, "tile_h": best.tile_h, "ctas_per_sm": best.ctas_per_sm}
+    b = cached_tuning(autotune_key(jobs), tune, cache_path)
+    return L.vr_batch_opts(1, b["tile_w"], b["tile_h"], b["ctas_per_sm"])
+
+
 def render_batched(jobs, use_graph: bool = True, tile=(8, 4), ctas_per_sm: int = 0, stream=None,
                    opts: L.vr_batch_opts | None = None):
     """jobs: list of dicts with keys vol, cam, tf, vmin, vmax, step, ert, bg, out, nsamples (optional).

@@ -90,3 +90,25 @@ def test_autotune_and_validation(P, torch):
         P.render_batched(jobs[:1], tile=(5, 6))
     for j in jobs:
         j["vol"].close()
+
+
+def test_autotune_cache_round_trip(P, torch, tmp_path):
+    """The tuned options are stored under the job list's key and read back
+    (no second tuning); rendering with them equals single renders."""
+    import json
+    jobs, _ = _jobs(torch, P, n=3, store="f16")
+    path = str(tmp_path / "tune.json")
+    a = P.autotune_batched(jobs, cache_path=path)
+    table = json.load(open(path))
+    assert list(table) == [P.api.autotune_key(jobs)]
+    table[P.api.autotune_key(jobs)]["ctas_per_sm"] = 2          # a hit returns the stored entry as is
+    json.dump(table, open(path, "w"))
+    b = P.autotune_batched(jobs, cache_path=path)
+    assert (b.tile_w, b.tile_h, b.ctas_per_sm) == (a.tile_w, a.tile_h, 2)
+    assert a.tile_w * a.tile_h == 32
+    P.render_batched(jobs, opts=b)
+    torch.cuda.synchronize()
+    for j in jobs:
+        img, ns = P.render(j["vol"], j["cam"], j["tf"], j["vmin"], j["vmax"], j["step"], j["ert"])
+        assert torch.equal(j["out"], img) and torch.equal(j["nsamples"], ns)
+        j["vol"].close()
