@@ -878,7 +878,7 @@ WORKLOADS = {"plain_128": run_plain_128, "precision_4096": run_precision_4096, "
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="scale_1024", choices=["scale_1024"] + sorted(WORKLOADS))
