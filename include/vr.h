@@ -127,7 +127,9 @@ typedef struct {
                                    and do not change T; images and sample counts are bit-identical
                                    to skip_empty = 0).  Composite mode, VR_FILTER_SOFTWARE, vr_render
                                    only; the first such call builds a per-brick value range
-                                   (8 bytes per brick) and synchronises cuda_stream. */
+                                   (8 bytes per brick, plus one transparency bit per brick that
+                                   each call recomputes for its table) and synchronises
+                                   cuda_stream. */
 } vr_params;
 
 typedef struct {

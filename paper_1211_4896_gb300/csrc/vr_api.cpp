@@ -711,9 +711,11 @@ vr_status vr_render(vr_volume_t vol, const vr_camera *cam, const vr_params *para
         return (set_error("vr_render: skip_empty needs VR_MODE_COMPOSITE and VR_FILTER_SOFTWARE"),
                 VR_ERR_UNSUPPORTED);
     if (params->skip_empty) {
+        const size_t nbr = (size_t)(vol->nb[0] * vol->nb[1] * vol->nb[2]);
         if (!vol->brick_range) {
-            const size_t n = (size_t)(vol->nb[0] * vol->nb[1] * vol->nb[2]);
-            e = dev_alloc(reinterpret_cast<void **>(&vol->brick_range), n * sizeof(float2));
+            // the ranges, then one transparency bit per brick (rewritten by every call)
+            e = dev_alloc(reinterpret_cast<void **>(&vol->brick_range),
+                          nbr * sizeof(float2) + (nbr + 31) / 32 * sizeof(uint32_t));
             if (e != cudaSuccess) {
                 vol->brick_range = nullptr;
                 return cuda_fail(e, "vr_render: brick ranges");
@@ -727,7 +729,8 @@ vr_status vr_render(vr_volume_t vol, const vr_camera *cam, const vr_params *para
             }
         }
         e = launch_forward_skip(vol_dev_copy(vol, preferred_copy(vol, cam, true, s)), vol->store_dtype, c, p,
-                                vol->brick_range, reinterpret_cast<float4 *>(dev_rgba_out), dev_nsamples_out, ctr, s);
+                                vol->brick_range, reinterpret_cast<uint32_t *>(vol->brick_range + nbr),
+                                reinterpret_cast<float4 *>(dev_rgba_out), dev_nsamples_out, ctr, s);
     } else if (params->mode == VR_MODE_MIP) {
         e = launch_mip(vol_dev_copy(vol, preferred_copy(vol, cam, true, s)), vol->store_dtype, c, p,
                        reinterpret_cast<float4 *>(dev_rgba_out), dev_nsamples_out, ctr, s);

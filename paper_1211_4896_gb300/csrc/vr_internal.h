@@ -188,8 +188,8 @@ cudaError_t launch_composite(int k, const float *const *partials, const float *c
 // Empty-space skipping (vr_skip.cu).
 cudaError_t launch_brick_range(const VolDev &v, vr_dtype dt, float2 *range, cudaStream_t s);
 cudaError_t launch_forward_skip(const VolDev &v, vr_dtype dt, const CamDev &c, const ParamDev &p,
-                                const float2 *range, float4 *out, uint32_t *nsamples, unsigned *counter,
-                                cudaStream_t s);
+                                const float2 *range, uint32_t *mask, float4 *out, uint32_t *nsamples,
+                                unsigned *counter, cudaStream_t s);
 // Global statistics (vr_stats.cu).
 size_t stats_scratch_bytes();
 cudaError_t launch_moments(const VolDev &v, vr_dtype dt, void *scratch, double *out, cudaStream_t s);

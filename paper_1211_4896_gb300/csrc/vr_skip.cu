@@ -7,10 +7,11 @@
 // the transmittance unchanged (C += T * 0 * c, T *= 1 - 0), so the march jumps
 // over them: the image and the sample counts are bit-identical to the plain
 // march.  The emptiness test is per brick and per table: a prefix count of
-// the table's non-zero opacities in shared memory, and the brick's range
-// mapped to entries with one entry of margin on each side (the rounding of an
-// interpolated value near the range's ends).  A brick holding a NaN voxel is
-// never skipped.
+// the table's non-zero opacities, and the brick's range mapped to entries with
+// one entry of margin on each side (the rounding of an interpolated value near
+// the range's ends); a first kernel turns it into one bit per brick, which
+// the march reads from shared memory.  A brick holding a NaN voxel is never
+// skipped.
 #include "vr_device.cuh"
 
 #include <cmath>
@@ -97,19 +98,11 @@ __device__ __forceinline__ bool brick_transparent(float2 r, const ParamDev &p, c
     return nz_prefix[ihi + 1] - nz_prefix[ilo] == 0;
 }
 
-// Ray parameter where the ray leaves [a, b] along one axis (its larger slab
-// end), folded into s1; inv = 1 / direction (infinite for a zero component).
-__device__ __forceinline__ void slab_exit(float q, float inv, float a, float b, float &s1)
-{
-    if (isinf(inv)) return;
-    const float t0 = (a - q) * inv, t1 = (b - q) * inv;
-    s1 = fminf(s1, fmaxf(t0, t1));
-}
-
-template <typename T, int LOG2B, int L>
-__global__ void __launch_bounds__(kSkipThreads) skip_kernel(VolDev v, CamDev c, ParamDev p, const float2 *range,
-                                                             float4 *out, uint32_t *nsamples, unsigned *counter,
-                                                             int tiles_x, unsigned ntiles)
+// One bit per brick for the table of this call: set when the brick is
+// transparent.  One thread per brick; the table's prefix count of non-zero
+// opacities is built in shared memory first.
+__global__ void __launch_bounds__(256) brick_mask_kernel(const float2 *__restrict__ range, ParamDev p,
+                                                          uint32_t *mask, long long nbricks)
 {
     extern __shared__ int nz_prefix[];          // K + 1 counts of non-zero opacities below each entry
     if (threadIdx.x == 0) {
@@ -121,6 +114,38 @@ __global__ void __launch_bounds__(kSkipThreads) skip_kernel(VolDev v, CamDev c, 
         nz_prefix[p.K] = acc;
     }
     __syncthreads();
+    const long long b = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool empty = b < nbricks && brick_transparent(__ldg(range + b), p, nz_prefix);
+    const unsigned word = __ballot_sync(kFull, empty);
+    if ((threadIdx.x & 31) == 0 && b < nbricks) mask[b >> 5] = word;
+}
+
+// Ray parameter where the ray leaves [a, b] along one axis (its larger slab
+// end), folded into s1; inv = 1 / direction (infinite for a zero component).
+__device__ __forceinline__ void slab_exit(float q, float inv, float a, float b, float &s1)
+{
+    if (isinf(inv)) return;
+    const float t0 = (a - q) * inv, t1 = (b - q) * inv;
+    s1 = fminf(s1, fmaxf(t0, t1));
+}
+
+// The transparency bits, copied into shared memory when they fit (a bit test
+// there instead of a dependent global load per brick a ray enters).
+constexpr int kMaskSmemWords = 12288;          // 48 KB: 393216 bricks (a 1024^3 cube has 262144)
+
+template <typename T, int LOG2B, int L>
+__global__ void __launch_bounds__(kSkipThreads) skip_kernel(VolDev v, CamDev c, ParamDev p,
+                                                             const uint32_t *__restrict__ gmask, int mask_words,
+                                                             bool mask_in_smem, float4 *out, uint32_t *nsamples,
+                                                             unsigned *counter, int tiles_x, unsigned ntiles)
+{
+    extern __shared__ uint32_t smask[];
+    if (mask_in_smem) {
+        for (int q = threadIdx.x; q < mask_words; q += blockDim.x) smask[q] = __ldg(gmask + q);
+        __syncthreads();
+    }
+    const uint32_t *mask = mask_in_smem ? smask : gmask;
+    const long long nbricks = (long long)v.nbx * v.nby * v.nbz;
     constexpr int B = 1 << LOG2B;
     const int lane = threadIdx.x & 31;
     for (;;) {
@@ -149,8 +174,8 @@ __global__ void __launch_bounds__(kSkipThreads) skip_kernel(VolDev v, CamDev c, 
                 if (brick != last) {
                     last = brick;
                     bool ok = true;
-                    if constexpr (kBoundsCheck) ok = index_ok(v.status, brick, (long long)v.nbx * v.nby * v.nbz);
-                    last_empty = ok && brick_transparent(__ldg(range + brick), p, nz_prefix);
+                    if constexpr (kBoundsCheck) ok = index_ok(v.status, brick, nbricks);
+                    last_empty = ok && ((mask[brick >> 5] >> (brick & 31)) & 1u);
                     if (last_empty) {
                         // every sample more than one step before the ray leaves the brick's
                         // box is inside it: jump there; the last ones are stepped one by one
@@ -207,25 +232,35 @@ __global__ void __launch_bounds__(kSkipThreads) skip_kernel(VolDev v, CamDev c, 
 }
 
 cudaError_t launch_forward_skip(const VolDev &v, vr_dtype dt, const CamDev &c, const ParamDev &p,
-                                const float2 *range, float4 *out, uint32_t *nsamples, unsigned *counter,
-                                cudaStream_t s)
+                                const float2 *range, uint32_t *mask, float4 *out, uint32_t *nsamples,
+                                unsigned *counter, cudaStream_t s)
 {
+    const long long nbricks = (long long)v.nbx * v.nby * v.nbz;
+    const int mask_words = (int)((nbricks + 31) / 32);
+    brick_mask_kernel<<<(unsigned)((nbricks + 255) / 256), 256, sizeof(int) * (size_t)(p.K + 1), s>>>(range, p, mask,
+                                                                                                   nbricks);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
     const int tiles_x = (c.W + 7) / 8, tiles_y = (c.H + 3) / 4;
     const unsigned ntiles = (unsigned)tiles_x * (unsigned)tiles_y;
-    cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(unsigned), s);
+    e = cudaMemsetAsync(counter, 0, sizeof(unsigned), s);
     if (e != cudaSuccess) return e;
-    const size_t smem = sizeof(int) * (size_t)(p.K + 1);
+    const bool in_smem = mask_words <= kMaskSmemWords;
+    const size_t smem = in_smem ? sizeof(uint32_t) * (size_t)mask_words : 0;
     return visit_layout(
         v, dt,
         [&](auto lay) {
             using Y = decltype(lay);
-            auto fn = skip_kernel<typename Y::type, Y::log2b, Y::order>;
+            auto fn = skip_kernel<typename Y::type, Y::log2b, Y::order>;   // smem <= 48 KB: no opt-in
             const int per_sm = occupancy_blocks((const void *)fn, kSkipThreads, smem);
             unsigned grid = (unsigned)(per_sm * sm_count());
             const unsigned useful = (ntiles + kSkipThreads / 32 - 1) / (kSkipThreads / 32);
             if (grid > useful) grid = useful;
             if (grid < 1) grid = 1;
-            fn<<<grid, kSkipThreads, smem, s>>>(v, c, p, range, out, nsamples, counter, tiles_x, ntiles);
+            log_line("skip %dx%d: %lld bricks, transparency bits in %s memory, grid %u", c.W, c.H, nbricks,
+                     in_smem ? "shared" : "global", grid);
+            fn<<<grid, kSkipThreads, smem, s>>>(v, c, p, mask, mask_words, in_smem, out, nsamples, counter, tiles_x,
+                                                ntiles);
             return cudaGetLastError();
         },
         cudaErrorInvalidValue);
