@@ -24,6 +24,18 @@ def _need_cuda(t: torch.Tensor, name: str):
         raise ValueError("%s must be contiguous" % name)
 
 
+def _need(t: torch.Tensor, name: str, shape, dtype, device):
+    """A caller-provided buffer the library reads or writes through a raw
+    pointer: it must have exactly this shape and dtype and live on the
+    volume's device (the C ABI cannot check sizes)."""
+    _need_cuda(t, name)
+    if tuple(t.shape) != tuple(shape) or t.dtype != dtype:
+        raise ValueError("%s must be a %s tensor of shape %s (got %s %s)" % (name, dtype, tuple(shape), t.dtype,
+                                                                            tuple(t.shape)))
+    if t.device != torch.device(device):
+        raise ValueError("%s must be on %s (got %s)" % (name, device, t.device))
+
+
 class Volume:
     """A bricked, device-resident copy of a dense cube (nz, ny, nx), x fastest."""
 
@@ -73,6 +85,8 @@ def _params(tf: torch.Tensor, vmin, vmax, step, ert, bg, filter, mode=L.VR_MODE_
         if minimap is None:
             raise ValueError("mode VR_MODE_SIGMA needs the volume's minimap (see minimap())")
         _need_cuda(minimap, "minimap")
+        if minimap.dtype != torch.float32 or minimap.dim() != 4 or minimap.shape[3] != 2:
+            raise ValueError("minimap must be the (mz, my, mx, 2) float32 tensor of minimap()")
         mm = minimap.data_ptr()
     return L.make_params(tf.data_ptr(), tf.shape[0], vmin, vmax, step, ert, bg, filter, mode, mm, region,
                          skip_empty)
@@ -90,8 +104,15 @@ def render(vol: Volume, cam: dict, tf: torch.Tensor, vmin: float, vmax: float, s
     H, W = int(cam["height"]), int(cam["width"])
     if out is None:
         out = torch.empty((H, W, 4), device=vol.device, dtype=torch.float32)
+    _need(out, "out", (H, W, 4), torch.float32, vol.device)
     if want_nsamples and nsamples is None:
         nsamples = torch.empty((H, W), device=vol.device, dtype=torch.int32)
+    if want_nsamples:
+        _need(nsamples, "nsamples", (H, W), torch.int32, vol.device)
+    if mode == L.VR_MODE_SIGMA and minimap is not None:
+        nz, ny, nx = vol.shape
+        m = [-(-n // int(r)) for n, r in zip((nx, ny, nz), region)]
+        _need(minimap, "minimap", (m[2], m[1], m[0], 2), torch.float32, vol.device)
     p = _params(tf, vmin, vmax, step, ert, bg, filter, mode, minimap, region, skip_empty)
     L.vr_render(vol.handle, L.make_camera(cam), p, out.data_ptr(),
                 nsamples.data_ptr() if (want_nsamples and nsamples is not None) else None, _stream(stream))
@@ -105,12 +126,11 @@ def render_backward(vol: Volume, cam: dict, tf: torch.Tensor, vmin, vmax, step, 
     """Adjoint: returns (grad_tf (K, 4) float64, grad_vox (nz, ny, nx) float32 or None).
     vox_reduce: None (the library picks), "direct" (reductions straight into
     grad_vox) or "scratch" (through the 16-byte-per-voxel quad scratch)."""
-    for t, n in ((rgba, "rgba"), (nsamples, "nsamples"), (grad_rgba, "grad_rgba")):
-        _need_cuda(t, n)
-    if grad_tf is None:
-        grad_tf = torch.empty(tuple(tf.shape), device=vol.device, dtype=torch.float64)
-    if want_vox and grad_vox is None:
-        grad_vox = torch.empty(vol.shape, device=vol.device, dtype=torch.float32)
+    H, W = int(cam["height"]), int(cam["width"])
+    _need(rgba, "rgba", (H, W, 4), torch.float32, vol.device)
+    _need(nsamples, "nsamples", (H, W), torch.int32, vol.device)
+    _need(grad_rgba, "grad_rgba", (H, W, 4), torch.float32, vol.device)
+    grad_tf, grad_vox = _grad_outputs(vol, tf, want_vox, grad_tf, grad_vox)
     p = _params(tf, vmin, vmax, step, ert, bg, filter)
     L.vr_render_backward(vol.handle, L.make_camera(cam), p, rgba.data_ptr(), nsamples.data_ptr(),
                          grad_rgba.data_ptr(), grad_tf.data_ptr(), grad_vox.data_ptr() if want_vox else None,
@@ -119,6 +139,17 @@ def render_backward(vol: Volume, cam: dict, tf: torch.Tensor, vmin, vmax, step, 
 
 
 _VOX_REDUCE = {None: 0, "direct": L.VR_GRAD_DIRECT, "scratch": L.VR_GRAD_SCRATCH}
+
+
+def _grad_outputs(vol: Volume, tf: torch.Tensor, want_vox: bool, grad_tf, grad_vox):
+    if grad_tf is None:
+        grad_tf = torch.empty(tuple(tf.shape), device=vol.device, dtype=torch.float64)
+    _need(grad_tf, "grad_tf", tuple(tf.shape), torch.float64, vol.device)
+    if want_vox:
+        if grad_vox is None:
+            grad_vox = torch.empty(vol.shape, device=vol.device, dtype=torch.float32)
+        _need(grad_vox, "grad_vox", vol.shape, torch.float32, vol.device)
+    return grad_tf, grad_vox
 
 
 def render_backward_views(vol: Volume, cams, tf: torch.Tensor, vmin, vmax, step, rgbas, nsamples, grad_rgbas,
@@ -130,13 +161,12 @@ def render_backward_views(vol: Volume, cams, tf: torch.Tensor, vmin, vmax, step,
     render_backward per view with accumulate after the first."""
     if not (len(cams) == len(rgbas) == len(nsamples) == len(grad_rgbas)) or not cams:
         raise ValueError("cams, rgbas, nsamples and grad_rgbas must be non-empty and of equal length")
-    for q in range(len(cams)):
-        for t, n in ((rgbas[q], "rgbas"), (nsamples[q], "nsamples"), (grad_rgbas[q], "grad_rgbas")):
-            _need_cuda(t, n)
-    if grad_tf is None:
-        grad_tf = torch.empty(tuple(tf.shape), device=vol.device, dtype=torch.float64)
-    if want_vox and grad_vox is None:
-        grad_vox = torch.empty(vol.shape, device=vol.device, dtype=torch.float32)
+    for q, cam in enumerate(cams):
+        H, W = int(cam["height"]), int(cam["width"])
+        _need(rgbas[q], "rgbas[%d]" % q, (H, W, 4), torch.float32, vol.device)
+        _need(nsamples[q], "nsamples[%d]" % q, (H, W), torch.int32, vol.device)
+        _need(grad_rgbas[q], "grad_rgbas[%d]" % q, (H, W, 4), torch.float32, vol.device)
+    grad_tf, grad_vox = _grad_outputs(vol, tf, want_vox, grad_tf, grad_vox)
     views = [L.vr_grad_view(L.make_camera(c), r.data_ptr(), n.data_ptr(), g.data_ptr())
              for c, r, n, g in zip(cams, rgbas, nsamples, grad_rgbas)]
     p = _params(tf, vmin, vmax, step, ert, bg, filter)
@@ -154,6 +184,7 @@ def minimap(vol: Volume, region, out: torch.Tensor | None = None, stream=None) -
     m = [-(-n // int(r)) for n, r in zip((nx, ny, nz), region)]
     if out is None:
         out = torch.empty((m[2], m[1], m[0], 2), device=vol.device, dtype=torch.float32)
+    _need(out, "out", (m[2], m[1], m[0], 2), torch.float32, vol.device)
     L.vr_minimap(vol.handle, region, out.data_ptr(), _stream(stream))
     return out
 
@@ -198,7 +229,12 @@ def render_subbox(vol: Volume, cam: dict, tf: torch.Tensor, vmin: float, vmax: f
 
 def composite(partials, depths, bg=(0.0, 0.0, 0.0, 0.0), stream=None) -> torch.Tensor:
     """Over-composite of partial images (from render_subbox) in per-pixel depth order."""
+    if not partials or len(partials) != len(depths):
+        raise ValueError("partials and depths must be non-empty and of equal length")
     H, W = depths[0].shape
+    for q, (pt, d) in enumerate(zip(partials, depths)):
+        _need(pt, "partials[%d]" % q, (H, W, 4), torch.float32, depths[0].device)
+        _need(d, "depths[%d]" % q, (H, W), torch.float32, depths[0].device)
     out = torch.empty((H, W, 4), device=depths[0].device, dtype=torch.float32)
     L.vr_composite([p.data_ptr() for p in partials], [d.data_ptr() for d in depths], W, H, bg, out.data_ptr(),
                    _stream(stream))
@@ -310,6 +346,10 @@ def render_batched(jobs, use_graph: bool = True, tile=(8, 4), ctas_per_sm: int =
         p = _params(j["tf"], j["vmin"], j["vmax"], j["step"], j.get("ert", 2.0), j.get("bg", (0, 0, 0, 0)),
                     L.VR_FILTER_SOFTWARE)
         ns = j.get("nsamples")
+        H, W = int(j["cam"]["height"]), int(j["cam"]["width"])
+        _need(j["out"], "jobs[%d].out" % len(cj), (H, W, 4), torch.float32, j["vol"].device)
+        if ns is not None:
+            _need(ns, "jobs[%d].nsamples" % len(cj), (H, W), torch.int32, j["vol"].device)
         cj.append(L.vr_job(j["vol"].handle, L.make_camera(j["cam"]), p, j["out"].data_ptr(),
                            ns.data_ptr() if ns is not None else None))
     if opts is None:

@@ -234,3 +234,39 @@ def test_staged_and_brick_paths_are_bit_identical(P, torch, store):
     # no bounded device wait gave up in any of these calls
     P._lib.vr_check(vol.handle, int(torch.cuda.current_stream().cuda_stream))
     vol.close()
+
+
+def test_api_rejects_mismatched_buffers(P, torch):
+    """The C ABI takes raw pointers and cannot check sizes: the Python layer
+    refuses any caller buffer whose shape, dtype or device does not match
+    before anything is launched."""
+    dev = torch.device("cuda")
+    dims = (20, 18, 22)
+    vol = P.Volume(synth.hi_cube(dims, 2, 0, 3).to(dev), "f32")
+    tf = torch.from_numpy(synth.tf_ramp(32)).to(dev)
+    cam = synth.camera_random_persp(dims, seed=2, width=24, height=16)
+    try:
+        img, ns = P.render(vol, cam, tf, -3.0, 30.0, 0.5)
+        bad = [dict(out=torch.empty((16, 25, 4), device=dev)),                   # wrong width
+               dict(out=torch.empty((16, 24, 4), device=dev, dtype=torch.float64)),
+               dict(nsamples=torch.empty((16, 24), device=dev, dtype=torch.int64)),
+               dict(out=torch.empty((16, 24, 4), device=dev)[:, :12])]          # not contiguous
+        for kw in bad:
+            with pytest.raises(ValueError):
+                P.render(vol, cam, tf, -3.0, 30.0, 0.5, **kw)
+        with pytest.raises(ValueError):
+            P.render_backward(vol, cam, tf, -3.0, 30.0, 0.5, img[:8].contiguous(), ns, img)
+        with pytest.raises(ValueError):
+            P.render_backward(vol, cam, tf, -3.0, 30.0, 0.5, img, ns, img,
+                              grad_vox=torch.empty((22, 18, 19), device=dev))
+        with pytest.raises(ValueError):
+            P.render(vol, cam, tf, 0.0, 5.0, 0.5, mode=P.VR_MODE_SIGMA, minimap=P.minimap(vol, (4, 4, 4)),
+                     region=(5, 5, 5))                                          # mini-map of another region
+        with pytest.raises(ValueError):
+            P.composite([img], [ns.float()[:, :10].contiguous()])
+        with pytest.raises(ValueError):
+            P.render_batched([dict(vol=vol, cam=cam, tf=tf, vmin=-3.0, vmax=30.0, step=0.5,
+                                   out=torch.empty((8, 8, 4), device=dev))])
+        P.render(vol, cam, tf, -3.0, 30.0, 0.5, out=torch.empty((16, 24, 4), device=dev))    # the right ones pass
+    finally:
+        vol.close()
