@@ -49,6 +49,13 @@ def _env_int(name, default):
         return default
 
 
+def gather_rate_frac(gsamples_per_s: float, bytes_per_voxel: int) -> float:
+    """Fraction of the HBM gather rate R = BW / (8 s): samples per second
+    times the trilinear footprint's 8 s bytes, over the measured copy
+    bandwidth."""
+    return gsamples_per_s * 8 * bytes_per_voxel / measured_peaks()[0]
+
+
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -499,6 +506,7 @@ def run_plain_128(args):
     t_cpu = time.perf_counter() - t0
     err = _px_err(out.cpu().numpy(), ns.cpu().numpy(), ref, range(256))
     print(json.dumps({"workload": "plain_128", "gsamples_per_s": samples / ms / 1e6, "ms": ms, "samples": samples,
+                      "roofline_frac": gather_rate_frac(samples / ms / 1e6, 4),
                       "px_err": err, "oracle_gsamples_per_s": samples / t_cpu / 1e9, "oracle_cores": os.cpu_count()}))
 
 
@@ -551,6 +559,7 @@ def run_precision_4096(args):
         gs = samples / ms / 1e6
         base = base or gs
         res[store] = {"gsamples_per_s": gs, "ms_4_views": ms, "fps": 4e3 / ms, "vs_f32": gs / base,
+                      "roofline_frac": gather_rate_frac(gs, 4 if store == "f32" else 2),
                       "bricked_gb": vol.info["bytes"] / 1e9,
                       "crop_px_err_max": max(e["max_abs"] for e in errs),
                       "crop_px_err_mean": float(np.mean([e["mean_abs"] for e in errs]))}
@@ -599,6 +608,7 @@ def run_batch_64(args):
     print(json.dumps({"workload": "batch_64", "jobs": 64, "samples": samples,
                       "graph_ms": t_graph, "separate_ms": t_sep, "speedup": t_sep / t_graph,
                       "graph_gsamples_per_s": samples / t_graph / 1e6, "separate_gsamples_per_s": samples / t_sep / 1e6,
+                      "graph_roofline_frac": gather_rate_frac(samples / t_graph / 1e6, 2),
                       "autotuned": {"tile": [best.tile_w, best.tile_h], "ctas_per_sm": best.ctas_per_sm}}))
     for j in jobs:
         j["vol"].close()
@@ -649,6 +659,7 @@ def run_diff_512(args):
     print(json.dumps({"workload": "diff_512", "samples": samples, "fwd_ms_4_views": t_f, "bwd_ms_4_views": t_b,
                       "bwd_over_fwd": t_b / t_f, "bwd_ms_per_view_calls": t_bv, "bwd_per_view_calls_over_fwd":
                       t_bv / t_f, "fwd_gsamples_per_s": samples / t_f / 1e6,
+                      "fwd_roofline_frac": gather_rate_frac(samples / t_f / 1e6, 4),
                       "fwd_bwd_gsamples_per_s": samples / (t_f + t_b) / 1e6}))
     vol.close()
 
@@ -819,6 +830,7 @@ def run_sortlast_1024(args):
     print(json.dumps({"workload": "sortlast_1024", "subboxes": len(boxes), "views": len(cams),
                       "whole_ms_8_views": t_whole, "sort_last_ms_8_views": t_sl, "overhead": t_sl / t_whole,
                       "samples": samples, "sort_last_gsamples_per_s": samples / t_sl / 1e6,
+                      "sort_last_roofline_frac": gather_rate_frac(samples / t_sl / 1e6, 4),
                       "max_diff_vs_whole": float(max((o - w).abs().max().item() for o, w in zip(outs, whole))),
                       "sub_cube_volumes_ms_8_views": t_sub, "sub_cube_volumes_bit_identical": same,
                       "px_err": err}))
@@ -865,6 +877,7 @@ def run_skip_1024(args):
     print(json.dumps({"workload": "skip_1024", "views": len(cams), "plain_ms_8_views": t_plain,
                       "skip_ms_8_views": t_skip, "speedup": t_plain / t_skip, "nominal_samples": samples,
                       "plain_gsamples_per_s": samples / t_plain / 1e6, "skip_gsamples_per_s": samples / t_skip / 1e6,
+                      "skip_roofline_frac_nominal": gather_rate_frac(samples / t_skip / 1e6, 4),
                       "bit_identical": bool(same)}))
     vol.close()
 
