@@ -311,9 +311,12 @@ typedef struct {
 } vr_batch_opts;
 
 /* All volumes of one batch must share store dtype and brick size
- * (UNSUPPORTED otherwise).  A job list is keyed by its bytes: the first call
- * with a new list uploads its descriptors (synchronising cuda_stream); with
- * use_graph the first call also builds the graph.  Within a layout the jobs
+ * (UNSUPPORTED otherwise).  A job list is cached under its stream, options and
+ * the named fields of its jobs (never the structs' padding): the first call
+ * with a new list on a stream uploads its descriptors (synchronising
+ * cuda_stream); with use_graph the first call also builds the graph.  A list
+ * owns one work counter, so the same list on two streams gets two plans.
+ * Past 64 cached lists the cache is emptied after a device synchronisation.  Within a layout the jobs
  * with the most work (pixels x samples along the box diagonal) are handed out
  * first.  Later calls with the same list only launch.  Errors: INVALID_ARG,
  * UNSUPPORTED, OOM, CUDA. */
@@ -327,10 +330,12 @@ vr_status vr_autotune_batched(const vr_job *jobs, int n, vr_batch_opts *best, vo
 /* ------------------------------------------------------------------------
  * Batched render that allocates nothing (the paper has no counterpart).
  *
- * For callers that cannot call cudaMalloc while rendering: code recorded
- * into a CUDA stream capture (an allocation would break the capture), services
- * with a fixed device-memory budget, or processes whose device memory belongs
- * to another allocator's pool.  vr_render_batched allocates a descriptor table
+ * For callers that cannot call cudaMalloc while rendering: services that
+ * run inside a fixed device-memory budget, processes whose device memory is
+ * handed out by another allocator's pool (an allocation outside the pool
+ * would break its accounting), and frame loops that cannot take the
+ * device-wide synchronisation a cudaMalloc or cudaFree may cause.
+ * vr_render_batched allocates a descriptor table
  * and a work counter for every new job list; this variant keeps both in one
  * static device array sized for VR_NOALLOC_MAX_JOBS jobs (about 64 KB, held by
  * every GPU that loads the library until the process exits), uploads the
@@ -342,8 +347,8 @@ vr_status vr_autotune_batched(const vr_job *jobs, int n, vr_batch_opts *best, vo
  * earlier call built it.
  *   - n > VR_NOALLOC_MAX_JOBS returns VR_ERR_INVALID_ARG and launches nothing.
  *   - The first call on a device looks up the device address of the static
- *     array (cudaGetSymbolAddress) and the kernel's occupancy; make that first
- *     call before any stream capture.
+ *     array (cudaGetSymbolAddress) and the kernels' occupancy (both cached
+ *     afterwards); make that first call before any stream capture.
  *   - Every call reuses the same array: calls that overlap on the GPU (two
  *     streams, or two host threads) race and must be serialised by the caller.
  * Errors: INVALID_ARG, UNSUPPORTED, CUDA.

@@ -102,6 +102,7 @@ struct Segment {
 // and (optionally) the instantiated graph of one launch.
 struct BatchPlan {
     std::vector<unsigned char> key;
+    std::vector<const vr_volume *> vols;   // the volumes its jobs read (dropped with any of them)
     JobDev *djobs = nullptr;
     unsigned *counter = nullptr;       // one work counter per group
     int njobs = 0;
@@ -113,6 +114,52 @@ struct BatchPlan {
 
 static std::mutex g_plans_mu;
 static std::map<std::vector<unsigned char>, BatchPlan *> g_plans;
+constexpr size_t kMaxPlans = 64;
+
+// Cache key of a job list: the device, the stream, the options and every
+// named field of every job (never the raw struct bytes, whose padding a
+// caller need not initialise).  The stream is part of the key because a plan
+// owns one work counter: two streams replaying one plan at the same time
+// would share it.
+template <typename V> static void key_put(std::vector<unsigned char> &k, const V &v)
+{
+    const unsigned char *b = reinterpret_cast<const unsigned char *>(&v);
+    k.insert(k.end(), b, b + sizeof(V));
+}
+
+static std::vector<unsigned char> plan_key(int dev, cudaStream_t s, int tile_w, int ctas, const vr_job *jobs, int n)
+{
+    std::vector<unsigned char> k;
+    k.reserve(64 + (size_t)n * 200);
+    key_put(k, dev);
+    key_put(k, s);
+    key_put(k, tile_w);
+    key_put(k, ctas);
+    for (int q = 0; q < n; ++q) {
+        const vr_job &J = jobs[q];
+        key_put(k, J.vol);
+        const vr_camera &c = J.cam;
+        key_put(k, c.kind);
+        for (int a = 0; a < 3; ++a) key_put(k, c.eye[a]), key_put(k, c.forward[a]), key_put(k, c.up[a]);
+        key_put(k, c.fov_y_deg);
+        key_put(k, c.ortho_height);
+        key_put(k, c.width);
+        key_put(k, c.height);
+        const vr_params &p = J.params;
+        key_put(k, p.tf_rgba);
+        key_put(k, p.tf_size);
+        key_put(k, p.vmin);
+        key_put(k, p.vmax);
+        key_put(k, p.step);
+        key_put(k, p.ert_threshold);
+        for (int a = 0; a < 4; ++a) key_put(k, p.bg_rgba[a]);
+        key_put(k, p.filter);
+        key_put(k, p.mode);
+        key_put(k, J.dev_rgba_out);
+        key_put(k, J.dev_nsamples_out);
+    }
+    return k;
+}
 
 static int log2_of(int x)
 {
@@ -203,12 +250,7 @@ static void size_grids(Segment seg[kGroups], int ctas)
     for (int o = 0; o < kGroups; ++o) {
         Segment &g = seg[o];
         if (!g.njobs) continue;
-        int per_sm = ctas;
-        if (per_sm == 0 &&
-            (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void *)g.fn, kBatThreads, 0) !=
-                 cudaSuccess ||
-             per_sm < 1))
-            per_sm = 1;
+        const int per_sm = ctas > 0 ? ctas : occupancy_blocks((const void *)g.fn, kBatThreads, 0);   // cached
         const unsigned grid = (unsigned)(per_sm * sm_count());
         const unsigned useful = (g.total_tiles + kBatThreads / 32 - 1) / (kBatThreads / 32);
         g.grid = grid < useful ? grid : (useful ? useful : 1);
@@ -296,14 +338,8 @@ void purge_plans(const vr_volume *vol)
 {
     std::lock_guard<std::mutex> g(g_plans_mu);
     for (auto it = g_plans.begin(); it != g_plans.end();) {
-        const vr_job *js = reinterpret_cast<const vr_job *>(it->first.data() + sizeof(int) * 3);
-        bool uses = false;
-        for (int q = 0; q < it->second->njobs && !uses; ++q) {
-            vr_job J;
-            std::memcpy(&J, js + q, sizeof J);
-            uses = J.vol == vol;
-        }
-        if (uses) {
+        const std::vector<const vr_volume *> &vs = it->second->vols;
+        if (std::find(vs.begin(), vs.end(), vol) != vs.end()) {
             destroy_plan(it->second);
             it = g_plans.erase(it);
         } else {
@@ -331,11 +367,7 @@ extern "C" vr_status vr_render_batched(const vr_job *jobs, int n, const vr_batch
     int dev = 0;
     cudaGetDevice(&dev);
 
-    // plan key: device, options and the raw job list
-    std::vector<unsigned char> key(sizeof(int) * 3 + sizeof(vr_job) * (size_t)n);
-    int hdr[3] = {dev, tile_w, ctas};
-    std::memcpy(key.data(), hdr, sizeof hdr);
-    std::memcpy(key.data() + sizeof hdr, jobs, sizeof(vr_job) * (size_t)n);
+    const std::vector<unsigned char> key = plan_key(dev, s, tile_w, ctas, jobs, n);
 
     std::lock_guard<std::mutex> g(g_plans_mu);
     BatchPlan *plan = nullptr;
@@ -353,6 +385,9 @@ extern "C" vr_status vr_render_batched(const vr_job *jobs, int n, const vr_batch
         plan = new BatchPlan();
         plan->key = key;
         plan->njobs = n;
+        for (int q = 0; q < n; ++q)
+            if (std::find(plan->vols.begin(), plan->vols.end(), jobs[q].vol) == plan->vols.end())
+                plan->vols.push_back(jobs[q].vol);
         for (int g = 0; g < kGroups; ++g) plan->seg[g] = seg[g];
         plan->log2_tw = log2_of(tile_w);
         plan->device = dev;
@@ -365,8 +400,10 @@ extern "C" vr_status vr_render_batched(const vr_job *jobs, int n, const vr_batch
             destroy_plan(plan);
             return cuda_fail(e, "vr_render_batched: plan upload");
         }
-        if (g_plans.size() > 64) {           // bound the cache
-            cudaStreamSynchronize(s);
+        if (g_plans.size() >= kMaxPlans) {
+            // bound the cache: the plans may still run on any stream, so the
+            // device is synchronised before they are freed
+            cudaDeviceSynchronize();
             for (auto &kv : g_plans) destroy_plan(kv.second);
             g_plans.clear();
         }
@@ -435,9 +472,9 @@ done:
 //
 // vr_render_batched allocates a descriptor table and a work counter on the
 // device the first time it sees a job list.  Callers that must not allocate
-// device memory at call time -- code running inside a stream capture, where
-// an allocation would break the capture; services with a fixed memory
-// budget; processes whose memory belongs to another allocator's pool -- use
+// device memory at call time -- services with a fixed memory budget,
+// processes whose memory belongs to another allocator's pool, frame loops
+// that cannot take the synchronisation an allocation may cause -- use
 // vr_render_batched_noalloc instead.  Its scratch (the descriptors of up to
 // kNoAllocMaxJobs jobs and the counter) is one static device array of about
 // 64 KB that every GPU loading this library holds until the process exits.
