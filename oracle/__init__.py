@@ -67,6 +67,9 @@ def lib():
             L.orc_render_backward.argtypes = [P(Volume), P(Camera), P(Params), C.c_int, C.c_int, C.c_void_p,
                                               C.c_void_p, C.c_void_p, C.c_int]
             L.orc_render_backward.restype = C.c_int
+            L.orc_render_backward_kinks.argtypes = [P(Volume), P(Camera), P(Params), C.c_int, C.c_int, C.c_void_p,
+                                                    C.c_void_p, C.c_void_p, C.c_void_p, C.c_double, C.c_int]
+            L.orc_render_backward_kinks.restype = C.c_int
             L.orc_trilinear.argtypes = [P(Volume), P(C.c_double * 3)]
             L.orc_trilinear.restype = C.c_double
             L.orc_tf_lookup.argtypes = [P(Params), C.c_double, P(C.c_double * 4)]
@@ -156,9 +159,12 @@ def render(cube, cam, tf, vmin, vmax, step, ert=2.0, bg=(0.0, 0.0, 0.0, 0.0), or
 
 def render_backward(cube, cam, tf, vmin, vmax, step, grad_rgba, ert=2.0, bg=(0.0, 0.0, 0.0, 0.0),
                     origin=(0.0, 0.0, 0.0), spacing=(1.0, 1.0, 1.0), want_vox=True, nthreads=None,
-                    bits=None, rows=None):
+                    bits=None, rows=None, kink_eps=None):
     """FP64 gradients (grad_tf (K,4), grad_vox (nz,ny,nx) or None) of
-    L given dL/dI = grad_rgba (H,W,4)."""
+    L given dL/dI = grad_rgba (H,W,4).  With kink_eps (in table entries) a
+    third array is returned: per voxel, the bound on how far its gradient
+    moves when samples within kink_eps of a table-interval end (vmin and vmax
+    included) take the slope of the other side (orc_render_backward_kinks)."""
     c = _Call(cube, cam, tf, vmin, vmax, step, ert, bg, origin, spacing, bits)
     g = np.ascontiguousarray(np.asarray(grad_rgba, dtype=np.float64))
     if g.shape != (c.cam.height, c.cam.width, 4):
@@ -167,11 +173,19 @@ def render_backward(cube, cam, tf, vmin, vmax, step, grad_rgba, ert=2.0, bg=(0.0
     gvox = np.zeros(c.cube.shape, dtype=np.float64) if want_vox else None
     nt = nthreads or os.cpu_count() or 1
     r0, r1 = rows if rows is not None else (0, c.cam.height)
-    rc = lib().orc_render_backward(C.byref(c.vol), C.byref(c.cam), C.byref(c.par), int(r0), int(r1), g.ctypes.data,
-                                   gtf.ctypes.data, gvox.ctypes.data if gvox is not None else None, int(nt))
+    if kink_eps is None:
+        rc = lib().orc_render_backward(C.byref(c.vol), C.byref(c.cam), C.byref(c.par), int(r0), int(r1),
+                                       g.ctypes.data, gtf.ctypes.data, gvox.ctypes.data if gvox is not None else None,
+                                       int(nt))
+    else:
+        kink = np.zeros(c.cube.shape, dtype=np.float64)
+        rc = lib().orc_render_backward_kinks(C.byref(c.vol), C.byref(c.cam), C.byref(c.par), int(r0), int(r1),
+                                             g.ctypes.data, gtf.ctypes.data,
+                                             gvox.ctypes.data if gvox is not None else None, kink.ctypes.data,
+                                             float(kink_eps), int(nt))
     if rc != 0:
         raise ValueError("orc_render_backward failed (%d)" % rc)
-    return gtf, gvox
+    return (gtf, gvox) if kink_eps is None else (gtf, gvox, kink)
 
 
 def trilinear(cube, p, origin=(0.0, 0.0, 0.0), spacing=(1.0, 1.0, 1.0), bits=None):

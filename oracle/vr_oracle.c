@@ -351,6 +351,8 @@ typedef struct {
     const double *grad_rgba;
     double *grad_tf;          /* private K*4 */
     double *grad_vox;         /* private nx*ny*nz or NULL */
+    double *kink_vox;         /* private nx*ny*nz or NULL: see orc_render_backward_kinks */
+    double kink_eps;          /* table-coordinate distance that counts as "at a kink" */
 } job;
 
 /* Pixels of rows [row0, row1) are dealt to the threads round-robin. */
@@ -426,6 +428,7 @@ int orc_render(const orc_volume *v, const orc_camera *c, const orc_params *P, in
 /* ------------------------------------------------------------------------ */
 
 typedef struct {
+    double val;               /* interpolated sample value */
     double rgba[4];
     double T;                 /* transmittance in front of the sample */
     tf_pos pos;
@@ -454,6 +457,7 @@ static void backward_pixel(job *J, int i, int j, stored_sample **buf, int64_t *c
         sample_pos(&rs, P, k, p);
         double val = trilinear(v, p, &S[k].cs);
         tf_lookup(P, val, S[k].rgba, &S[k].pos);
+        S[k].val = val;
         S[k].T = T;
         T *= (1.0 - S[k].rgba[3]);
         used = k + 1;
@@ -492,6 +496,34 @@ static void backward_pixel(job *J, int i, int j, stored_sample **buf, int64_t *c
             dv *= scale;
             for (int q = 0; q < 8; ++q) J->grad_vox[s->cs.idx[q]] += s->cs.wt[q] * dv;
         }
+        if (J->kink_vox) {
+            /* The voxel gradient uses the slope of the table interval that holds
+             * u = (v - vmin)/(vmax - vmin) (K-1).  Within kink_eps of an interval
+             * end the interval is decided by rounding: the other side's slope
+             * (or no slope past vmin / vmax) is an equally valid one-sided
+             * derivative.  The largest change of this sample's voxel term that
+             * such a choice makes is added to its eight corners' bound. */
+            double u = (s->val - P->vmin) / (P->vmax - P->vmin) * (P->K - 1);   /* unclamped */
+            double alt = -1.0;            /* |dv| change, or < 0 when not at a kink */
+            double m = floor(u + 0.5);    /* nearest interval end */
+            if (fabs(u - m) < J->kink_eps && m >= 0.0 && m <= (double)(P->K - 1)) {
+                int mi = (int)m;
+                int ci = s->pos.interior ? i0 : -1;   /* interval of the chosen slope; -1: none */
+                int oi;                               /* interval on the other side of end m */
+                if (!s->pos.interior) oi = mi == 0 ? 0 : P->K - 2;
+                else if (mi == i0) oi = mi - 1;       /* u at or just above m */
+                else oi = mi;                         /* u just below m */
+                if (oi > P->K - 2) oi = -1;           /* past vmax: no slope */
+                double cur = 0.0, oth = 0.0;
+                for (int ch = 0; ch < 4; ++ch) {
+                    if (ci >= 0) cur += dr[ch] * (P->tf[4 * (ci + 1) + ch] - P->tf[4 * ci + ch]);
+                    if (oi >= 0) oth += dr[ch] * (P->tf[4 * (oi + 1) + ch] - P->tf[4 * oi + ch]);
+                }
+                alt = fabs(oth - cur) * scale;
+            }
+            if (alt > 0.0)
+                for (int q = 0; q < 8; ++q) J->kink_vox[s->cs.idx[q]] += s->cs.wt[q] * alt;
+        }
     }
 }
 
@@ -512,8 +544,27 @@ static void *bwd_worker(void *arg)
  * voxels, given dL/dI (H*W*4), over the pixels of rows [row0, row1).  Both outputs are overwritten.  Per-thread
  * partial sums are added in thread order, so the result is deterministic for
  * a given thread count. */
+int orc_render_backward_kinks(const orc_volume *v, const orc_camera *c, const orc_params *P, int row0, int row1,
+                              const double *grad_rgba, double *grad_tf, double *grad_vox, double *kink_vox,
+                              double kink_eps, int nthreads);
+
 int orc_render_backward(const orc_volume *v, const orc_camera *c, const orc_params *P, int row0, int row1,
                         const double *grad_rgba, double *grad_tf, double *grad_vox, int nthreads)
+{
+    return orc_render_backward_kinks(v, c, P, row0, row1, grad_rgba, grad_tf, grad_vox, NULL, 0.0, nthreads);
+}
+
+/* The same, also writing (when kink_vox is not NULL) a per-voxel bound on
+ * how far the voxel gradient may move when the table interval of samples
+ * within kink_eps (in table entries) of an interval end -- including vmin
+ * and vmax -- is decided the other way, as a lower-precision evaluation of
+ * the same samples may do: the sum over such samples of the change of their
+ * voxel term, weighted like the term itself.  The voxel gradient of a
+ * piecewise-linear table is discontinuous at those ends; the bound says how
+ * much of a result is decided there rather than by the method. */
+int orc_render_backward_kinks(const orc_volume *v, const orc_camera *c, const orc_params *P, int row0, int row1,
+                              const double *grad_rgba, double *grad_tf, double *grad_vox, double *kink_vox,
+                              double kink_eps, int nthreads)
 {
     if (check_args(v, c, P) || !grad_rgba || !grad_tf) return -1;
     if (nthreads < 1) nthreads = 1;
@@ -530,19 +581,24 @@ int orc_render_backward(const orc_volume *v, const orc_camera *c, const orc_para
         jobs[t].grad_rgba = grad_rgba;
         jobs[t].grad_tf = (double *)calloc((size_t)P->K * 4, sizeof(double));
         jobs[t].grad_vox = grad_vox ? (double *)calloc((size_t)nvox, sizeof(double)) : NULL;
-        if (!jobs[t].grad_tf || (grad_vox && !jobs[t].grad_vox)) rc = -3;
+        jobs[t].kink_vox = kink_vox ? (double *)calloc((size_t)nvox, sizeof(double)) : NULL;
+        jobs[t].kink_eps = kink_eps;
+        if (!jobs[t].grad_tf || (grad_vox && !jobs[t].grad_vox) || (kink_vox && !jobs[t].kink_vox)) rc = -3;
     }
     if (rc == 0) rc = run_threads(jobs, nthreads, bwd_worker);
     if (rc == 0) {
         memset(grad_tf, 0, sizeof(double) * (size_t)P->K * 4);
         if (grad_vox) memset(grad_vox, 0, sizeof(double) * (size_t)nvox);
+        if (kink_vox) memset(kink_vox, 0, sizeof(double) * (size_t)nvox);
         for (int t = 0; t < nthreads; ++t) {
             for (int q = 0; q < P->K * 4; ++q) grad_tf[q] += jobs[t].grad_tf[q];
             if (grad_vox)
                 for (int64_t q = 0; q < nvox; ++q) grad_vox[q] += jobs[t].grad_vox[q];
+            if (kink_vox)
+                for (int64_t q = 0; q < nvox; ++q) kink_vox[q] += jobs[t].kink_vox[q];
         }
     }
-    for (int t = 0; t < nthreads; ++t) { free(jobs[t].grad_tf); free(jobs[t].grad_vox); }
+    for (int t = 0; t < nthreads; ++t) { free(jobs[t].grad_tf); free(jobs[t].grad_vox); free(jobs[t].kink_vox); }
     free(jobs);
     return rc;
 }

@@ -10,8 +10,9 @@ rank over-composites the pieces of its band in per-pixel depth order
 
 One process per GPU; torch.distributed carries the exchange (NCCL between
 GPUs).  The partition, the exchange and the gather take and return plain
-tensors, so they run on any backend and device; the compositing arithmetic
-is `composite`'s."""
+tensors, so they run on any backend and device (with a backend whose
+collectives take host tensors only, such as gloo, device tensors are staged
+through host memory); the compositing arithmetic is `composite`'s."""
 from __future__ import annotations
 
 import torch
@@ -60,6 +61,11 @@ def band_rows(height: int, parts: int):
     return [(height * b // parts, height * (b + 1) // parts) for b in range(parts)]
 
 
+def _host_staged(group) -> bool:
+    """True when the group's backend takes host tensors only (gloo)."""
+    return dist.get_backend(group) == "gloo"
+
+
 def exchange_bands(partial: torch.Tensor, depth: torch.Tensor, group=None):
     """All-to-all of horizontal bands: this rank sends band b of its partial
     image (H, W, 4) and depth (H, W) to rank b and receives its own band from
@@ -71,11 +77,13 @@ def exchange_bands(partial: torch.Tensor, depth: torch.Tensor, group=None):
     rows = band_rows(H, world)
     sizes = [r1 - r0 for r0, r1 in rows]
     h = sizes[rank]
-    out_p = torch.empty((world * h, W, 4), dtype=partial.dtype, device=partial.device)
-    out_d = torch.empty((world * h, W), dtype=depth.dtype, device=depth.device)
-    dist.all_to_all_single(out_p, partial.contiguous(), [h] * world, sizes, group=group)
-    dist.all_to_all_single(out_d, depth.contiguous(), [h] * world, sizes, group=group)
-    return list(out_p.split(h)), list(out_d.split(h))
+    dev = partial.device
+    cdev = torch.device("cpu") if _host_staged(group) else dev
+    out_p = torch.empty((world * h, W, 4), dtype=partial.dtype, device=cdev)
+    out_d = torch.empty((world * h, W), dtype=depth.dtype, device=cdev)
+    dist.all_to_all_single(out_p, partial.contiguous().to(cdev), [h] * world, sizes, group=group)
+    dist.all_to_all_single(out_d, depth.contiguous().to(cdev), [h] * world, sizes, group=group)
+    return list(out_p.to(dev).split(h)), list(out_d.to(dev).split(h))
 
 
 def gather_bands(band: torch.Tensor, height: int, group=None) -> torch.Tensor:
@@ -84,11 +92,12 @@ def gather_bands(band: torch.Tensor, height: int, group=None) -> torch.Tensor:
     world = dist.get_world_size(group)
     rows = band_rows(height, world)
     hmax = max(r1 - r0 for r0, r1 in rows)
-    pad = torch.zeros((hmax,) + tuple(band.shape[1:]), dtype=band.dtype, device=band.device)
-    pad[:band.shape[0]] = band
+    cdev = torch.device("cpu") if _host_staged(group) else band.device
+    pad = torch.zeros((hmax,) + tuple(band.shape[1:]), dtype=band.dtype, device=cdev)
+    pad[:band.shape[0]] = band.to(cdev)
     got = [torch.empty_like(pad) for _ in range(world)]
     dist.all_gather(got, pad, group=group)
-    return torch.cat([g[:r1 - r0] for g, (r0, r1) in zip(got, rows)])
+    return torch.cat([g[:r1 - r0] for g, (r0, r1) in zip(got, rows)]).to(band.device)
 
 
 def render_sortlast(vol, global_dims, offset, cell_lo, cell_hi, cam: dict, tf: torch.Tensor, vmin: float,

@@ -107,3 +107,77 @@ def test_zero_opacity_table_has_zero_colour_gradient(oracle_lib):
     gtf, _ = oracle_lib.render_backward(V, cam, tf, -5, 5, 0.5, g, want_vox=False)
     assert np.abs(gtf[:, :3]).max() == 0.0
     assert np.abs(gtf[:, 3]).max() > 0.0
+
+
+# ---------------------------------------------------------------------------
+# The kink bound of the voxel gradient (orc_render_backward_kinks)
+# ---------------------------------------------------------------------------
+
+def _kink_scene(value):
+    """Constant cube along z with an opacity-only table of three entries over
+    [0, 4] (u = v / 2), orthographic rays along z, loss L = sum of output
+    opacity (dL/dI = (0, 0, 0, 1)): every sample's opacity term has the same
+    sign, so the bound (a sum of magnitudes) equals the gap between the two
+    one-sided derivatives."""
+    V = np.full((10, 6, 6), value, np.float64)
+    tf = np.array([[0.0, 0.0, 0.0, 0.05], [0.0, 0.0, 0.0, 0.2], [0.0, 0.0, 0.0, 0.1]])
+    cam = cam_ortho((2.5, 2.5, -20.0), (0, 0, 1), (0, 1, 0), 4.0, 4, 4)
+    g = np.zeros((4, 4, 4))
+    g[..., 3] = 1.0
+    return V, tf, cam, g
+
+
+def _one_sided(orc, V, tf, cam, voxel, h=1e-6):
+    def L(x):
+        W = V.copy()
+        W[voxel] = x
+        return float(orc.render(W, cam, tf, 0.0, 4.0, 0.7, nthreads=1)["rgba"][..., 3].sum())
+    x = V[voxel]
+    return (L(x + h) - L(x)) / h, (L(x) - L(x - h)) / h
+
+
+@pytest.mark.parametrize("value,end", [(2.0, 2.0), (4.0, 4.0), (2.6, None), (2.0 + 1e-3, 2.0)])
+def test_kink_bound_is_the_gap_between_one_sided_derivatives(oracle_lib, value, end):
+    """u = 1 is the end between the table's two intervals (opacity slopes
+    +0.15 and -0.1 per entry, i.e. per 2 units of value): the voxel gradient
+    there is either one-sided derivative, and the bound is their gap.  u = 2
+    is vmax: one side has no slope at all.  u = 1.3 is inside an interval: no
+    bound.  u = 1 + 5e-4 is within the 1e-3 tolerance of the end u = 1: its
+    bound is the gap of the one-sided derivatives at that end."""
+    V, tf, cam, g = _kink_scene(value)
+    _, gvox, kink = oracle_lib.render_backward(V, cam, tf, 0.0, 4.0, 0.7, g, nthreads=1, kink_eps=1e-3)
+    kinked = end is not None
+    for voxel in ((4, 2, 2), (7, 3, 2), (1, 2, 3)):
+        Vk = _kink_scene(end)[0] if kinked else V
+        d_plus, d_minus = _one_sided(oracle_lib, Vk, tf, cam, voxel)
+        if kinked:
+            assert abs(d_plus - d_minus) > 1e-2
+            # near the end (not on it) the samples' weights differ from those at
+            # the end by O(u - end) = 5e-4, and so does the bound
+            np.testing.assert_allclose(kink[voxel], abs(d_plus - d_minus), rtol=1e-4 if value == end else 3e-3,
+                                       atol=1e-9)
+            if value == end:
+                lo, hi = min(d_plus, d_minus), max(d_plus, d_minus)
+                assert lo - 1e-5 <= gvox[voxel] <= hi + 1e-5
+        else:
+            assert kink[voxel] == 0.0
+            np.testing.assert_allclose(gvox[voxel], d_plus, rtol=1e-4, atol=1e-9)
+            np.testing.assert_allclose(d_plus, d_minus, rtol=1e-4, atol=1e-9)
+    # a tolerance below the distance to the end finds no kink
+    if value == 2.0 + 1e-3:
+        _, _, kink = oracle_lib.render_backward(V, cam, tf, 0.0, 4.0, 0.7, g, nthreads=1, kink_eps=1e-4)
+        assert (kink == 0.0).all()
+
+
+def test_kink_bound_leaves_gradients_unchanged(oracle_lib):
+    """Asking for the bound does not change the gradients; random data with a
+    wide tolerance flags only voxels that some sample near an interval end
+    touches."""
+    V, tf, vmin, vmax, cam, target, kw = _setup(4)
+    _, I = _loss(oracle_lib, V, tf, vmin, vmax, cam, target, kw)
+    gI = 2.0 * (I - target)
+    a = oracle_lib.render_backward(V, cam, tf, vmin, vmax, 0.45, gI, nthreads=1, **kw)
+    b = oracle_lib.render_backward(V, cam, tf, vmin, vmax, 0.45, gI, nthreads=1, kink_eps=0.05, **kw)
+    np.testing.assert_array_equal(a[0], b[0])
+    np.testing.assert_array_equal(a[1], b[1])
+    assert (b[2] >= 0).all() and 0 < (b[2] > 0).sum() < (a[1] != 0).sum()
