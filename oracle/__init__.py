@@ -68,7 +68,8 @@ def lib():
                                               C.c_void_p, C.c_void_p, C.c_int]
             L.orc_render_backward.restype = C.c_int
             L.orc_render_backward_kinks.argtypes = [P(Volume), P(Camera), P(Params), C.c_int, C.c_int, C.c_void_p,
-                                                    C.c_void_p, C.c_void_p, C.c_void_p, C.c_double, C.c_int]
+                                                    C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_double,
+                                                    C.c_int]
             L.orc_render_backward_kinks.restype = C.c_int
             L.orc_trilinear.argtypes = [P(Volume), P(C.c_double * 3)]
             L.orc_trilinear.restype = C.c_double
@@ -161,10 +162,12 @@ def render_backward(cube, cam, tf, vmin, vmax, step, grad_rgba, ert=2.0, bg=(0.0
                     origin=(0.0, 0.0, 0.0), spacing=(1.0, 1.0, 1.0), want_vox=True, nthreads=None,
                     bits=None, rows=None, kink_eps=None):
     """FP64 gradients (grad_tf (K,4), grad_vox (nz,ny,nx) or None) of
-    L given dL/dI = grad_rgba (H,W,4).  With kink_eps (in table entries) a
-    third array is returned: per voxel, the bound on how far its gradient
+    L given dL/dI = grad_rgba (H,W,4).  With kink_eps (in table entries) two
+    more arrays are returned: per voxel, the bound on how far its gradient
     moves when samples within kink_eps of a table-interval end (vmin and vmax
-    included) take the slope of the other side (orc_render_backward_kinks)."""
+    included) take the slope of the other side, and the sum of the
+    magnitudes that make up its gradient terms before cancellation
+    (orc_render_backward_kinks)."""
     c = _Call(cube, cam, tf, vmin, vmax, step, ert, bg, origin, spacing, bits)
     g = np.ascontiguousarray(np.asarray(grad_rgba, dtype=np.float64))
     if g.shape != (c.cam.height, c.cam.width, 4):
@@ -179,13 +182,14 @@ def render_backward(cube, cam, tf, vmin, vmax, step, grad_rgba, ert=2.0, bg=(0.0
                                        int(nt))
     else:
         kink = np.zeros(c.cube.shape, dtype=np.float64)
+        mag = np.zeros(c.cube.shape, dtype=np.float64)
         rc = lib().orc_render_backward_kinks(C.byref(c.vol), C.byref(c.cam), C.byref(c.par), int(r0), int(r1),
                                              g.ctypes.data, gtf.ctypes.data,
                                              gvox.ctypes.data if gvox is not None else None, kink.ctypes.data,
-                                             float(kink_eps), int(nt))
+                                             mag.ctypes.data, float(kink_eps), int(nt))
     if rc != 0:
         raise ValueError("orc_render_backward failed (%d)" % rc)
-    return (gtf, gvox) if kink_eps is None else (gtf, gvox, kink)
+    return (gtf, gvox) if kink_eps is None else (gtf, gvox, kink, mag)
 
 
 def trilinear(cube, p, origin=(0.0, 0.0, 0.0), spacing=(1.0, 1.0, 1.0), bits=None):

@@ -352,6 +352,7 @@ typedef struct {
     double *grad_tf;          /* private K*4 */
     double *grad_vox;         /* private nx*ny*nz or NULL */
     double *kink_vox;         /* private nx*ny*nz or NULL: see orc_render_backward_kinks */
+    double *mag_vox;          /* private nx*ny*nz or NULL: see orc_render_backward_kinks */
     double kink_eps;          /* table-coordinate distance that counts as "at a kink" */
 } job;
 
@@ -481,6 +482,7 @@ static void backward_pixel(job *J, int i, int j, stored_sample **buf, int64_t *c
         double dr[4];
         for (int ch = 0; ch < 3; ++ch) dr[ch] = s->T * a * g[ch];     /* dL/dc_k */
         dr[3] = s->T * (cg - Ssuf - gT * Psuf);                        /* dL/da_k */
+        const double Ssuf_k = Ssuf, Psuf_k = Psuf;                      /* behind sample k */
         Ssuf = a * cg + (1.0 - a) * Ssuf;
         Psuf = (1.0 - a) * Psuf;
 
@@ -495,6 +497,17 @@ static void backward_pixel(job *J, int i, int j, stored_sample **buf, int64_t *c
         if (J->grad_vox && s->pos.interior) {
             dv *= scale;
             for (int q = 0; q < 8; ++q) J->grad_vox[s->cs.idx[q]] += s->cs.wt[q] * dv;
+        }
+        if (J->mag_vox && s->pos.interior) {
+            /* the magnitudes that make up this sample's voxel term before any
+             * cancellation: |dL/dc| |dc/dv| per colour channel and, for the
+             * opacity, T (|c.g| + |suffix colour| + |suffix transmittance term|) |da/dv| */
+            double mag = 0.0;
+            for (int ch = 0; ch < 3; ++ch)
+                mag += fabs(dr[ch]) * fabs(P->tf[4 * (i0 + 1) + ch] - P->tf[4 * i0 + ch]);
+            mag += s->T * (fabs(cg) + fabs(Ssuf_k) + fabs(gT * Psuf_k)) * fabs(P->tf[4 * (i0 + 1) + 3] - P->tf[4 * i0 + 3]);
+            mag *= scale;
+            for (int q = 0; q < 8; ++q) J->mag_vox[s->cs.idx[q]] += s->cs.wt[q] * mag;
         }
         if (J->kink_vox) {
             /* The voxel gradient uses the slope of the table interval that holds
@@ -546,12 +559,13 @@ static void *bwd_worker(void *arg)
  * a given thread count. */
 int orc_render_backward_kinks(const orc_volume *v, const orc_camera *c, const orc_params *P, int row0, int row1,
                               const double *grad_rgba, double *grad_tf, double *grad_vox, double *kink_vox,
-                              double kink_eps, int nthreads);
+                              double *mag_vox, double kink_eps, int nthreads);
 
 int orc_render_backward(const orc_volume *v, const orc_camera *c, const orc_params *P, int row0, int row1,
                         const double *grad_rgba, double *grad_tf, double *grad_vox, int nthreads)
 {
-    return orc_render_backward_kinks(v, c, P, row0, row1, grad_rgba, grad_tf, grad_vox, NULL, 0.0, nthreads);
+    return orc_render_backward_kinks(v, c, P, row0, row1, grad_rgba, grad_tf, grad_vox, NULL, NULL, 0.0,
+                                     nthreads);
 }
 
 /* The same, also writing (when kink_vox is not NULL) a per-voxel bound on
@@ -561,10 +575,13 @@ int orc_render_backward(const orc_volume *v, const orc_camera *c, const orc_para
  * the same samples may do: the sum over such samples of the change of their
  * voxel term, weighted like the term itself.  The voxel gradient of a
  * piecewise-linear table is discontinuous at those ends; the bound says how
- * much of a result is decided there rather than by the method. */
+ * much of a result is decided there rather than by the method.  mag_vox
+ * (when not NULL) receives per voxel the sum of the magnitudes that make up
+ * its gradient terms before any cancellation (the scale of the rounding
+ * error an evaluation in lower precision can make). */
 int orc_render_backward_kinks(const orc_volume *v, const orc_camera *c, const orc_params *P, int row0, int row1,
                               const double *grad_rgba, double *grad_tf, double *grad_vox, double *kink_vox,
-                              double kink_eps, int nthreads)
+                              double *mag_vox, double kink_eps, int nthreads)
 {
     if (check_args(v, c, P) || !grad_rgba || !grad_tf) return -1;
     if (nthreads < 1) nthreads = 1;
@@ -582,23 +599,31 @@ int orc_render_backward_kinks(const orc_volume *v, const orc_camera *c, const or
         jobs[t].grad_tf = (double *)calloc((size_t)P->K * 4, sizeof(double));
         jobs[t].grad_vox = grad_vox ? (double *)calloc((size_t)nvox, sizeof(double)) : NULL;
         jobs[t].kink_vox = kink_vox ? (double *)calloc((size_t)nvox, sizeof(double)) : NULL;
+        jobs[t].mag_vox = mag_vox ? (double *)calloc((size_t)nvox, sizeof(double)) : NULL;
         jobs[t].kink_eps = kink_eps;
-        if (!jobs[t].grad_tf || (grad_vox && !jobs[t].grad_vox) || (kink_vox && !jobs[t].kink_vox)) rc = -3;
+        if (!jobs[t].grad_tf || (grad_vox && !jobs[t].grad_vox) || (kink_vox && !jobs[t].kink_vox) ||
+            (mag_vox && !jobs[t].mag_vox))
+            rc = -3;
     }
     if (rc == 0) rc = run_threads(jobs, nthreads, bwd_worker);
     if (rc == 0) {
         memset(grad_tf, 0, sizeof(double) * (size_t)P->K * 4);
         if (grad_vox) memset(grad_vox, 0, sizeof(double) * (size_t)nvox);
         if (kink_vox) memset(kink_vox, 0, sizeof(double) * (size_t)nvox);
+        if (mag_vox) memset(mag_vox, 0, sizeof(double) * (size_t)nvox);
         for (int t = 0; t < nthreads; ++t) {
             for (int q = 0; q < P->K * 4; ++q) grad_tf[q] += jobs[t].grad_tf[q];
             if (grad_vox)
                 for (int64_t q = 0; q < nvox; ++q) grad_vox[q] += jobs[t].grad_vox[q];
             if (kink_vox)
                 for (int64_t q = 0; q < nvox; ++q) kink_vox[q] += jobs[t].kink_vox[q];
+            if (mag_vox)
+                for (int64_t q = 0; q < nvox; ++q) mag_vox[q] += jobs[t].mag_vox[q];
         }
     }
-    for (int t = 0; t < nthreads; ++t) { free(jobs[t].grad_tf); free(jobs[t].grad_vox); free(jobs[t].kink_vox); }
+    for (int t = 0; t < nthreads; ++t) {
+        free(jobs[t].grad_tf); free(jobs[t].grad_vox); free(jobs[t].kink_vox); free(jobs[t].mag_vox);
+    }
     free(jobs);
     return rc;
 }

@@ -15,8 +15,14 @@
 // Persistent warps pull 8x4 ray tiles from the same atomic queue as the
 // forward.  Every warp owns a private FP32 row of K RGBA gradient bins in
 // global memory (L2-resident); a sample adds its two weighted contributions
-// with two fire-and-forget 16-byte vector reductions.  One final kernel sums
-// the warps' rows in FP64 (the only FP64 arithmetic: the cross-block sum).
+// with two fire-and-forget 16-byte vector reductions.  Samples of zero
+// opacity (a = 0: no colour gradient, only the two opacity bins change) whose
+// bins lie in the table's longest run of zero-opacity entries -- where
+// transfer functions put the noise floor -- go instead to lane-private
+// columns of 32 opacity bins in shared memory (plain loads and stores, no
+// conflicts), summed into the warp's row when it has no tiles left.  One
+// final kernel sums the warps' rows in FP64 (the only FP64 arithmetic: the
+// cross-block sum).
 // The voxel gradient is scattered with reductions.  A ray's pending sums for
 // the eight corners of its current cell are kept as two planes of four
 // corners across the carry axis (the view's dominant axis); when the ray
@@ -105,6 +111,46 @@ struct BinRun {
         b = -1;
     }
 };
+
+// Lane-private opacity bins for zero-opacity samples: kWin bins [lo, lo +
+// kWin) over the table's longest run of zero-opacity entries; bin lo + q of
+// lane l is col[q * 32] with col = window + l (bank l: no conflicts).
+constexpr int kWin = 32;
+struct OpacityWindow {
+    float *col;
+    int lo;
+    // Adds w0 da to bin i0 and w1 da to bin i0 + 1 when both are in the window.
+    __device__ __forceinline__ bool add(int i0, float w0, float w1, float da) const
+    {
+        const int q = i0 - lo;
+        if ((unsigned)q >= (unsigned)(kWin - 1)) return false;
+        col[q * 32] += w0 * da;
+        col[(q + 1) * 32] += w1 * da;
+        return true;
+    }
+};
+
+// First entry of the longest run of table entries with zero opacity (kWin
+// entries from there, moved down to fit the table), or a value that puts
+// every bin outside the window when no two neighbouring entries have zero
+// opacity.  Called by one whole warp.
+__device__ int zero_opacity_window(const ParamDev &p, int lane)
+{
+    int run = 0, best = 0, best_lo = 0;
+    for (int base = 0; base < p.K; base += 32) {
+        const int q = base + lane;
+        const unsigned m = __ballot_sync(kFull, q < p.K && __ldg(&p.tf[q].w) == 0.0f);
+        for (int b = 0; b < 32 && base + b < p.K; ++b) {
+            if ((m >> b) & 1u) {
+                if (++run > best) best = run, best_lo = base + b - run + 1;
+            } else {
+                run = 0;
+            }
+        }
+    }
+    if (best < 2) return -2 * kWin;
+    return max(0, min(best_lo, p.K - kWin));
+}
 
 // Where the voxel gradient goes.  Axes u, v, w: w is the carry axis, u and
 // v the other two in x, y, z order; su, sv, sw their strides in the dense
@@ -199,6 +245,15 @@ __global__ void __launch_bounds__(kBwdThreads) bwd_kernel(VolDev v, CamDev c, Pa
     float4 *row = wtab + ((size_t)blockIdx.x * kBwdWarps + warp) * (size_t)p.K;     // this warp's bins
     const float vscale = p.km1 * p.scale01;    // du/dv inside the range
     const long long nyx = (long long)v.ny * v.nx;
+    __shared__ float window[kBwdWarps][kWin][32];
+    __shared__ int window_lo;
+    for (int q = threadIdx.x; q < kBwdWarps * kWin * 32; q += blockDim.x) (&window[0][0][0])[q] = 0.0f;
+    if (warp == 0) {
+        const int lo = zero_opacity_window(p, lane);
+        if (lane == 0) window_lo = lo;
+    }
+    __syncthreads();
+    const OpacityWindow win{&window[warp][0][lane], window_lo};
 
     for (;;) {
         unsigned tile = 0;
@@ -254,7 +309,8 @@ __global__ void __launch_bounds__(kBwdThreads) bwd_kernel(VolDev v, CamDev c, Pa
             bool bins_ok = true;                        // bins i0 and i0 + 1 exist
             if constexpr (kBoundsCheck) bins_ok = index_ok(v.status, tp.i0, p.K - 1);
             if (bins_ok && (aT != 0.0f || da != 0.0f)) {
-                bins.add(row, tp.i0, 1.0f - tp.w, tp.w, aT, da, g);
+                if (aT != 0.0f || !win.add(tp.i0, 1.0f - tp.w, tp.w, da))
+                    bins.add(row, tp.i0, 1.0f - tp.w, tp.w, aT, da, g);
                 if (gd.vox && tp.interior) {
                     // dr . de with dr = (aT g.rgb, da)
                     const float dv = fmaf(aT, de.x * g.x + de.y * g.y + de.z * g.z, da * de.w) * vscale;
@@ -285,6 +341,14 @@ __global__ void __launch_bounds__(kBwdThreads) bwd_kernel(VolDev v, CamDev c, Pa
         bins.flush(row, g);
         cells.flush(gd);
     }
+    // the warp's opacity window into its row: lane l sums bin lo + l over the
+    // 32 lanes' columns (skewed so that the lanes read distinct banks)
+    __syncwarp();
+    float sum = 0.0f;
+#pragma unroll 8
+    for (int j = 0; j < 32; ++j) sum += window[warp][lane][(j + lane) & 31];
+    const int bin = window_lo + lane;
+    if (sum != 0.0f && bin >= 0 && bin < p.K) red_add_f32(&row[bin].w, sum);
 }
 
 // Dense voxel gradient from the quad scratch: the voxel at (u, v) of its

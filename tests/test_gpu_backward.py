@@ -308,3 +308,99 @@ def test_multi_view_call_equals_accumulated_single_calls(P, torch, filt):
         assert ref_vox.abs().max().item() > 0
     finally:
         vol.close()
+
+
+@pytest.mark.slow
+def test_differentiation_workload_crop_elementwise_against_fp64(P, torch):
+    """The differentiation workload's kernel configuration checked element by
+    element against the FP64 store-all reverse sweep on a 32^3 crop: the 512^3
+    float32 cube of that workload, cropped around its brightest voxel; its four
+    orbit views refitted to the crop at the workload's ray pitch (0.9 voxel at
+    the centre, so 64^2 images: the same samples per voxel as the 1024^2 views
+    of the whole cube), step 0.5, no early termination; L2 loss against
+    targets rendered with the hidden ramp table; gradients of the loss over
+    the four views from one vr_render_backward_views call, which takes the
+    quad scratch by itself (the views are dense).
+
+    Every table entry must satisfy |g - ref| <= 1e-3 max(|ref|, 1e-3 max|ref|).
+    So must every voxel, up to two allowances the oracle computes:
+      - its kink bound: the voxel gradient of a piecewise-linear table jumps
+        where a sample's value crosses an interval end, and a sample within
+        FP32 rounding of one (tolerance from the crop's largest value gradient
+        and a 1e-5 voxel position error) may take either side's slope; the
+        bound is the largest change that choice can make;
+      - the FP32 forward error of the re-march, 2 N u times the sum of the
+        magnitudes the voxel's terms are made of (u = 2^-24, N the longest
+        ray's sample count): the suffix colour is formed by running sums
+        along the ray, so where the terms cancel to a small gradient the
+        rounding of the large parts remains (the one-sided FD rule's floor,
+        1e-6 max|ref|, is below it there)."""
+    from paper_1211_4896_gb300 import _lib as L
+    dev = torch.device("cuda")
+    pre = synth.preset_diff_512()
+    cube = synth.hi_cube(pre["dims"], pre["n_blobs"], pre["n_disks"], pre["seed"], device=dev)
+    n = 32
+    flat = int(torch.argmax(cube).item())
+    centre = np.unravel_index(flat, cube.shape)                     # (z, y, x)
+    lo = [int(min(max(c - n // 2, 0), s - n)) for c, s in zip(centre, cube.shape)]
+    crop = cube[lo[0]:lo[0] + n, lo[1]:lo[1] + n, lo[2]:lo[2] + n].contiguous()
+    del cube
+    torch.cuda.empty_cache()
+    crop_np = crop.cpu().numpy()
+    vol = P.Volume(crop, "f32")
+    cams = synth.orbit_cameras((n, n, n), 4, 40.0, 64, 64, start_deg=20.0)
+    hidden_np = synth.tf_ramp(256)
+    rng = np.random.default_rng(5)
+    tf_np = np.clip(hidden_np + 0.05 * rng.uniform(size=hidden_np.shape), 0.0, 1.0).astype(np.float32)
+    hidden = torch.from_numpy(hidden_np).to(dev)
+    tf = torch.from_numpy(tf_np).to(dev)
+    step, vmin, vmax = pre["step"], synth.TF_VMIN, synth.TF_VMAX
+    outs, nss, grads = [], [], []
+    for c in cams:
+        tgt, _ = P.render(vol, c, hidden, vmin, vmax, step, 2.0)
+        img, ns = P.render(vol, c, tf, vmin, vmax, step, 2.0)
+        outs.append(img)
+        nss.append(ns)
+        grads.append(2.0 * (img - tgt))
+    gtf, gvox = P.render_backward_views(vol, cams, tf, vmin, vmax, step, outs, nss, grads, 2.0)
+    torch.cuda.synchronize()
+    assert L.vr_volume_info(vol.handle)["scratch_bytes"] >= 16 * n ** 3, \
+        "the dense views should have taken the quad scratch"
+    # tolerance of "at an interval end", in table entries
+    grad = max(float(np.abs(np.diff(crop_np, axis=a)).max()) for a in range(3))
+    eps_u = (255.0 / (vmax - vmin)) * (grad * np.sqrt(3.0) * 1e-5 + 4e-7 * float(np.abs(crop_np).max()))
+    ref_tf = np.zeros((256, 4))
+    ref_vox = np.zeros((n, n, n))
+    kink = np.zeros((n, n, n))
+    mag = np.zeros((n, n, n))
+    for c, g, ns in zip(cams, grads, nss):
+        o = oracle.render(crop_np, c, tf_np, vmin, vmax, step, 2.0)
+        assert (o["n_used"] == ns.cpu().numpy()).all(), "sample counts differ from the oracle's"
+        rt, rv, kv, mv = oracle.render_backward(crop_np, c, tf_np, vmin, vmax, step,
+                                                g.cpu().numpy().astype(np.float64), ert=2.0, kink_eps=eps_u)
+        ref_tf += rt
+        ref_vox += rv
+        kink += kv
+        mag += mv
+    ok, err, bound = _grad_close(gtf.cpu().numpy(), ref_tf)
+    print("table gradient: worst err/bound %.3g" % float((err / bound).max()))
+    assert ok.all(), "table gradient: %d of %d entries outside the 1e-3 rule" % (int((~ok).sum()), ok.size)
+    gv = gvox.cpu().numpy().astype(np.float64)
+    _, err, bound = _grad_close(gv, ref_vox)
+    n_max = max(int(ns.max()) for ns in nss)
+    fp32 = 2.0 * n_max * 2.0 ** -24 * mag
+    allow = bound + kink + fp32
+    ok = err <= allow
+    print("voxel gradient: eps_u %.2g entries; %d of %d voxels touched by a sample at an interval end; "
+          "%d outside the plain rule (%d within their kink bound); worst err/allowance %.3g" % (
+              eps_u, int((kink > 0).sum()), kink.size, int((err > bound).sum()),
+              int(((err > bound) & (err <= bound + kink)).sum()), float((err / allow).max())))
+    for q in np.argwhere(~ok)[:20]:
+        q = tuple(q)
+        print("  voxel %s: got %.6g ref %.6g err %.3g bound %.3g kink %.3g fp32 %.3g" % (
+            q, gv[q], ref_vox[q], err[q], bound[q], kink[q], fp32[q]))
+    assert ok.all(), "voxel gradient: %d of %d entries outside the rule, worst at %s" % (
+        int((~ok).sum()), ok.size, np.unravel_index(int(np.argmax(err / allow)), ref_vox.shape))
+    assert (err <= bound).mean() > 0.99, "the plain 1e-3 rule should hold for almost every voxel"
+    assert (kink > 0).mean() < 0.5, "too many voxels at an interval end for the check to mean much"
+    vol.close()

@@ -145,7 +145,7 @@ def test_kink_bound_is_the_gap_between_one_sided_derivatives(oracle_lib, value, 
     bound.  u = 1 + 5e-4 is within the 1e-3 tolerance of the end u = 1: its
     bound is the gap of the one-sided derivatives at that end."""
     V, tf, cam, g = _kink_scene(value)
-    _, gvox, kink = oracle_lib.render_backward(V, cam, tf, 0.0, 4.0, 0.7, g, nthreads=1, kink_eps=1e-3)
+    _, gvox, kink, mag = oracle_lib.render_backward(V, cam, tf, 0.0, 4.0, 0.7, g, nthreads=1, kink_eps=1e-3)
     kinked = end is not None
     for voxel in ((4, 2, 2), (7, 3, 2), (1, 2, 3)):
         Vk = _kink_scene(end)[0] if kinked else V
@@ -163,9 +163,11 @@ def test_kink_bound_is_the_gap_between_one_sided_derivatives(oracle_lib, value, 
             assert kink[voxel] == 0.0
             np.testing.assert_allclose(gvox[voxel], d_plus, rtol=1e-4, atol=1e-9)
             np.testing.assert_allclose(d_plus, d_minus, rtol=1e-4, atol=1e-9)
+            # one sign everywhere and no colour: no cancellation, the magnitude is the gradient's
+            np.testing.assert_allclose(mag[voxel], abs(gvox[voxel]), rtol=1e-12)
     # a tolerance below the distance to the end finds no kink
     if value == 2.0 + 1e-3:
-        _, _, kink = oracle_lib.render_backward(V, cam, tf, 0.0, 4.0, 0.7, g, nthreads=1, kink_eps=1e-4)
+        _, _, kink, _ = oracle_lib.render_backward(V, cam, tf, 0.0, 4.0, 0.7, g, nthreads=1, kink_eps=1e-4)
         assert (kink == 0.0).all()
 
 
@@ -181,3 +183,7 @@ def test_kink_bound_leaves_gradients_unchanged(oracle_lib):
     np.testing.assert_array_equal(a[0], b[0])
     np.testing.assert_array_equal(a[1], b[1])
     assert (b[2] >= 0).all() and 0 < (b[2] > 0).sum() < (a[1] != 0).sum()
+    # the magnitudes bound the gradient (triangle inequality), and cancel somewhere
+    mag = b[3]
+    assert (mag >= np.abs(a[1]) * (1 - 1e-12)).all()
+    assert (mag > 2 * np.abs(a[1])).any()
