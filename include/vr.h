@@ -142,7 +142,8 @@ typedef struct {
                                  staged call) */
     int64_t copy_bytes;       /* device bytes of the brick copies (see vr_volume_create) */
     int copies;               /* which copies exist: bit 1 / 2 plain y- / z-fastest; bit 3 / 4 / 5
-                                 paired x- / y- / z-fastest (16-bit storage) */
+                                 paired x- / y- / z-fastest (16-bit storage); bit 6 / 7 / 8
+                                 blocked, deep along x / y / z (sparse views) */
     int64_t scratch_bytes;    /* device bytes of the backward scratch: the per-warp table-gradient
                                  rows and, once a dense view has used it, the voxel-gradient quad
                                  scratch (16 bytes per voxel) */
@@ -170,7 +171,13 @@ typedef struct {
  * and rays closer than VR_PAIRED_MAX_PITCH voxels (environment, default 3)
  * at the volume centre, a paired copy for any axis instead, each element
  * holding its own value and the next one along that axis so that four loads
- * fetch a cell's eight corners (twice the bricks' bytes).  A copy is built
+ * fetch a cell's eight corners (twice the bricks' bytes).  For rays at least
+ * VR_SPARSE_MIN_PITCH voxels apart (default 3), which share no sectors, the
+ * forward (vr_render, vr_render_batched) of a 16-bit volume reads a blocked
+ * copy instead: blocks of 2 x 2 x 4 voxels, one 32-byte sector each, deep
+ * along the axis the view direction is closest to (about 1.2x the bricks'
+ * bytes); VR_SPARSE_LAYOUT=b asks for blocked copies (2 x 2 x 2 blocks) for
+ * float volumes too, =i never.  A copy is built
  * only outside stream capture, while the device keeps an eighth of its memory
  * free besides it (else the bricks themselves serve), synchronising
  * cuda_stream once; environment variable VR_BRICK_COPIES=0 turns copies off.
@@ -188,6 +195,13 @@ vr_status vr_volume_create(const void *dev_cube, vr_dtype src_dtype, vr_dtype st
  * on the voxels). */
 vr_status vr_volume_update(vr_volume_t vol, const void *dev_cube, vr_dtype src_dtype, void *cuda_stream);
 
+/* A new handle holding the same voxels as `src` in bricks of another size
+ * (16, 32 or 64; 0 = 16), built on the device from src's bricks (no dense
+ * copy needed), for the batched autotuner's choice of brick size (not in the
+ * paper).  Copies of src are not carried over; the new handle builds its own
+ * on first use.  Synchronises cuda_stream.  Errors: INVALID_ARG, OOM, CUDA. */
+vr_status vr_volume_rebrick(vr_volume_t src, int brick, void *cuda_stream, vr_volume_t *out);
+
 /* Frees the handle and its device memory (synchronises the device). NULL is a no-op. */
 vr_status vr_volume_destroy(vr_volume_t vol);
 
@@ -196,7 +210,8 @@ vr_status vr_volume_info(vr_volume_t vol, vr_volume_info_t *out);
 /* The brick layout a software-filter render of this view reads as things
  * stand: *layout = -1 for the x-fastest bricks, else the copy id (1, 2: plain
  * copies with y / z fastest; 3, 4, 5: paired 16-bit copies with x / y / z
- * fastest; bit `id` of vr_volume_info's copies).  Builds nothing: a preferred
+ * fastest; 6, 7, 8: blocked copies deep along x / y / z; bit `id` of
+ * vr_volume_info's copies).  Builds nothing: a preferred
  * copy that does not exist yet reports -1 until a render builds it.  A batched
  * call launches one kernel per distinct layout of its views.  Errors:
  * INVALID_ARG. */
@@ -308,6 +323,9 @@ typedef struct {
                                  parameters); 0: launch the layouts one after another */
     int tile_w, tile_h;       /* ray tile of one warp: tile_w * tile_h == 32; 0 = 8 x 4 */
     int ctas_per_sm;          /* persistent CTAs per SM; 0 = occupancy limit */
+    int warps_per_tile;       /* 1, 2 or 4 warps of a CTA take one tile of tile_w x (tile_h x
+                                 warps_per_tile) rays together, one part each, so that neighbouring
+                                 parts share an SM's L1; 0 = 1 */
 } vr_batch_opts;
 
 /* All volumes of one batch must share store dtype and brick size
@@ -322,9 +340,10 @@ typedef struct {
  * UNSUPPORTED, OOM, CUDA. */
 vr_status vr_render_batched(const vr_job *jobs, int n, const vr_batch_opts *opts, void *cuda_stream);
 
-/* Times candidate tile shapes and CTA counts for this job list (it renders
- * the jobs several times on cuda_stream and synchronises it) and writes the
- * fastest into *best.  best->use_graph is left unchanged. */
+/* Times candidate tile shapes, CTA counts and warps per tile for this job
+ * list (it renders the jobs several times on cuda_stream and synchronises
+ * it) and writes the fastest into *best.  best->use_graph is left
+ * unchanged.  The brick size is the volumes' (see vr_volume_rebrick). */
 vr_status vr_autotune_batched(const vr_job *jobs, int n, vr_batch_opts *best, void *cuda_stream);
 
 /* ------------------------------------------------------------------------

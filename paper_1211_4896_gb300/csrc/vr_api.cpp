@@ -293,7 +293,11 @@ VolDev vol_dev_copy(const vr_volume *vol, int copy)
     if (copy >= 1 && copy < kCopyIds && vol->copies[copy]) {
         v.data = vol->copies[copy];
         v.order = copy_order(copy);
-        v.paired = copy_paired(copy);
+        v.paired = copy_blocked(copy) ? 2 : (copy_paired(copy) ? 1 : 0);
+        if (copy_blocked(copy)) {
+            v.stride = blocked_stride(vol->log2b, vol->store_dtype == VR_F32 ? 4 : 2);
+            v.nelem = vol->nb[0] * vol->nb[1] * vol->nb[2] * v.stride;
+        }
     }
     return v;
 }
@@ -326,12 +330,14 @@ static double ray_pitch_voxels(const vr_volume *vol, const vr_camera *cam, const
 // load) while neighbouring rays are closer than VR_PAIRED_MAX_PITCH voxels
 // (default 3) at the volume centre, where a warp's gathers share cache lines
 // and the number of loads bounds the march; sparser rays each touch their own
-// sectors in DRAM, so the plain copy (half the bytes of a paired one) serves.
+// sectors in DRAM, so the plain copy (half the bytes of a paired one) serves,
+// or, for the forward kernels of a 16-bit volume, a blocked copy (a cell's
+// 2 x 2 columns in 32-byte blocks deep along the view direction).
 // A copy is built on first use when `may_build`, the stream is not being
 // captured and the device keeps an eighth of its memory free besides it; it
 // is complete before the call returns, so any stream may read it.  Otherwise
 // (or with VR_BRICK_COPIES=0 in the environment) the bricks serve (-1).
-int preferred_copy(vr_volume *vol, const vr_camera *cam, bool may_build, cudaStream_t s)
+int preferred_copy(vr_volume *vol, const vr_camera *cam, bool may_build, cudaStream_t s, bool allow_blocked)
 {
     static const bool enabled = [] {
         const char *e = std::getenv("VR_BRICK_COPIES");
@@ -341,6 +347,21 @@ int preferred_copy(vr_volume *vol, const vr_camera *cam, bool may_build, cudaStr
         const char *e = std::getenv("VR_PAIRED_MAX_PITCH");
         return e ? std::atof(e) : 3.0;
     }();
+    static const double sparse_pitch = [] {
+        const char *e = std::getenv("VR_SPARSE_MIN_PITCH");
+        return e ? std::atof(e) : 3.0;
+    }();
+    // layout of sparse views (VR_SPARSE_LAYOUT): 'b' blocked copies (forward
+    // kernels only), 'i' as dense views (rows along the image's horizontal
+    // axis); default 'b' for 16-bit and 'i' for float storage, as measured on
+    // the 4096 x 4096 x 1024 cube (16-bit: blocked 4% faster; float: the two
+    // blocked copies its views want do not fit beside the cube, and the one
+    // row copy serves every view)
+    static const char sparse_env = [] {
+        const char *e = std::getenv("VR_SPARSE_LAYOUT");
+        return e && (e[0] == 'b' || e[0] == 'i') ? e[0] : 0;
+    }();
+    const char sparse_mode = sparse_env ? sparse_env : (vol->store_dtype == VR_F32 ? 'i' : 'b');
     if (!enabled) return -1;
     double f[3] = {cam->forward[0], cam->forward[1], cam->forward[2]}, r[3];
     cross3(f, cam->up, r);
@@ -355,13 +376,25 @@ int preferred_copy(vr_volume *vol, const vr_camera *cam, bool may_build, cudaStr
             axis = a;
         }
     }
-    const bool paired = vol->store_dtype != VR_F32 && ray_pitch_voxels(vol, cam, r) < max_pitch;
-    const int copy = paired ? 3 + axis : axis;
+    const double pitch = ray_pitch_voxels(vol, cam, r);
+    const bool paired = vol->store_dtype != VR_F32 && pitch < max_pitch;
+    int copy = paired ? 3 + axis : axis;
+    if (pitch >= sparse_pitch && sparse_mode == 'b' && allow_blocked) {
+        // rays too far apart to share sectors: each ray reads its own, so the
+        // blocks are deep along the axis w the rays advance along most
+        int w = 0;
+        double m = -1.0;
+        for (int a = 0; a < 3; ++a) {
+            const double c = std::fabs(cam->forward[a]) / vol->spacing[a];
+            if (c > m * (1.0 + 1e-9)) m = c, w = a;
+        }
+        copy = 6 + w;
+    }
     if (copy == 0) return -1;
     if (vol->copies[copy]) return copy;
     if (!may_build) return -1;
     log_line("view %dx%d prefers brick copy %d (%s); building it", cam->width, cam->height, copy,
-             copy_paired(copy) ? "paired" : "plain");
+             copy_paired(copy) ? "paired" : (copy_blocked(copy) ? "blocked" : "plain"));
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
         cudaGetLastError();
@@ -546,14 +579,11 @@ const char *vr_last_error(void) { return g_err.c_str(); }
 
 const char *vr_version(void) { return "vr-gb300 0.1 (sm_103a)"; }
 
-vr_status vr_volume_create(const void *dev_cube, vr_dtype src_dtype, vr_dtype store_dtype, const int64_t dims[3],
-                           const double origin[3], const double spacing[3], int brick, void *cuda_stream,
-                           vr_volume_t *out)
+// A volume handle with its bricks and counters allocated (not filled).
+static vr_status make_volume(vr_dtype src_dtype, vr_dtype store_dtype, const int64_t dims[3], const double origin[3],
+                             const double spacing[3], int brick, vr_volume **out)
 {
-    g_err.clear();
-    if (!out) return invalid("out is NULL");
     *out = nullptr;
-    if (!dev_cube) return invalid("dev_cube is NULL");
     if (!dims) return invalid("dims is NULL");
     if ((unsigned)src_dtype > VR_BF16 || (unsigned)store_dtype > VR_BF16)
         return invalid("dtype must be VR_F32, VR_F16 or VR_BF16");
@@ -604,12 +634,45 @@ vr_status vr_volume_create(const void *dev_cube, vr_dtype src_dtype, vr_dtype st
     vol->counter_slots = 64;
     e = dev_alloc(reinterpret_cast<void **>(&vol->counters), sizeof(unsigned) * vol->counter_slots);
     if (e != cudaSuccess) { vol->counters = nullptr; free_volume(vol); return cuda_fail(e, "cudaMalloc(counters)"); }
+    *out = vol;
+    return VR_OK;
+}
+
+vr_status vr_volume_create(const void *dev_cube, vr_dtype src_dtype, vr_dtype store_dtype, const int64_t dims[3],
+                           const double origin[3], const double spacing[3], int brick, void *cuda_stream,
+                           vr_volume_t *out)
+{
+    g_err.clear();
+    if (!out) return invalid("out is NULL");
+    *out = nullptr;
+    if (!dev_cube) return invalid("dev_cube is NULL");
+    vr_volume *vol = nullptr;
+    vr_status st = make_volume(src_dtype, store_dtype, dims, origin, spacing, brick, &vol);
+    if (st != VR_OK) return st;
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
-    e = cudaMemsetAsync(vol->counters, 0, sizeof(unsigned) * vol->counter_slots, s);
+    cudaError_t e = cudaMemsetAsync(vol->counters, 0, sizeof(unsigned) * vol->counter_slots, s);
     if (e == cudaSuccess) e = launch_brick(dev_cube, src_dtype, vol, s);
-    if (e == cudaSuccess && vol->dense) e = launch_densify(dev_cube, src_dtype, vol, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) { free_volume(vol); return cuda_fail(e, "vr_volume_create: bricking"); }
+    *out = vol;
+    return VR_OK;
+}
+
+vr_status vr_volume_rebrick(vr_volume_t src, int brick, void *cuda_stream, vr_volume_t *out)
+{
+    g_err.clear();
+    if (!out) return invalid("out is NULL");
+    *out = nullptr;
+    vr_status st = check_volume(src);
+    if (st != VR_OK) return st;
+    vr_volume *vol = nullptr;
+    st = make_volume(src->src_dtype, src->store_dtype, src->dims, src->origin, src->spacing, brick, &vol);
+    if (st != VR_OK) return st;
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    cudaError_t e = cudaMemsetAsync(vol->counters, 0, sizeof(unsigned) * vol->counter_slots, s);
+    if (e == cudaSuccess) e = launch_rebrick(src, vol, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) { free_volume(vol); return cuda_fail(e, "vr_volume_rebrick"); }
     *out = vol;
     return VR_OK;
 }
@@ -655,7 +718,7 @@ vr_status vr_view_layout(vr_volume_t vol, const vr_camera *cam, int *layout)
     if (st != VR_OK) return st;
     if (!vol) return invalid("volume handle is NULL");
     if (!layout) return invalid("layout is NULL");
-    *layout = preferred_copy(vol, cam, false, nullptr);
+    *layout = preferred_copy(vol, cam, false, nullptr, true);
     return VR_OK;
 }
 
@@ -748,9 +811,8 @@ vr_status vr_render(vr_volume_t vol, const vr_camera *cam, const vr_params *para
         e = launch_forward_staged(dense_dev(vol), vol->store_dtype, c, p, reinterpret_cast<float4 *>(dev_rgba_out),
                                   dev_nsamples_out, ctr, status_word(vol), s);
     } else {
-        e = launch_forward(vol_dev_copy(vol, preferred_copy(vol, cam, true, s)), vol->store_dtype, c, p,
-                           reinterpret_cast<float4 *>(dev_rgba_out),
-                           dev_nsamples_out, ctr, s);
+        e = launch_forward(vol_dev_copy(vol, preferred_copy(vol, cam, true, s, true)), vol->store_dtype, c, p,
+                           reinterpret_cast<float4 *>(dev_rgba_out), dev_nsamples_out, ctr, s);
     }
     if (e != cudaSuccess) return cuda_fail(e, "vr_render launch");
     return VR_OK;

@@ -61,6 +61,37 @@ template <> struct Pair<__nv_bfloat16> {
 template <typename T> struct is_pair { static constexpr bool value = false; };
 template <typename S> struct is_pair<Pair<S>> { static constexpr bool value = true; };
 
+// Element of a blocked brick copy (storage type S), for views whose rays are
+// far apart: inside each brick the voxels sit in blocks of 2 x 2 x BW that
+// fill one 32-byte sector (BW = 2 for float, 4 for 16-bit storage), deep
+// along the copy's axis w, the axis the view's rays advance along most.  A
+// ray that shares no sector with its neighbours then fetches a new sector
+// only every BW / 2 ... BW steps of a cell's 2 x 2 columns, where a
+// row-ordered brick costs two sectors per step whatever the voxel size; so
+// a 16-bit volume moves half the sectors of a float one.
+template <typename S> struct Blocked {
+    using storage = S;
+};
+template <typename T> struct is_blocked { static constexpr bool value = false; };
+template <typename S> struct is_blocked<Blocked<S>> { static constexpr bool value = true; };
+
+// Geometry of a blocked brick of B^3 cells (B + 1 voxels per axis with the
+// apron, padded to whole blocks).  Axes (u, v, w): w is the copy's axis, u
+// and v the other two in x, y, z order.  Element (lu, lv, lw) of a brick is
+//   (((lw / BW) NV + lv / 2) NU + lu / 2) BS + (lw % BW) 4 + (lv % 2) 2 + lu % 2.
+template <int ELEM_BYTES, int LOG2B> struct BlockGeom {
+    static constexpr int B = 1 << LOG2B;
+    static constexpr int BW = ELEM_BYTES == 4 ? 2 : 4;         // block depth along w
+    static constexpr int BS = 4 * BW;                          // elements per block (32 bytes)
+    static constexpr int NU = (B + 2) / 2, NV = (B + 2) / 2;   // blocks across u and v
+    static constexpr int NW = (B + BW) / BW;                   // blocks along w (B + 1 voxels, padded)
+    static constexpr long long stride = (long long)NU * NV * NW * BS;
+    static __host__ __device__ __forceinline__ int index(int lu, int lv, int lw)
+    {
+        return (((lw / BW) * NV + (lv >> 1)) * NU + (lu >> 1)) * BS + (lw % BW) * 4 + (lv & 1) * 2 + (lu & 1);
+    }
+};
+
 // ---------------------------------------------------------------------------
 // Brick layouts a kernel can read (host-side dispatch).  Every volume has its
 // x-fastest bricks (element type = storage type, order 0).  Copies for views
@@ -82,9 +113,9 @@ R visit_layout_b(const VolDev &v, F &&f, R none)
     if (!v.paired && v.order == 1) return f(Layout<S, LOG2B, 1>{});
     if (!v.paired && v.order == 2) return f(Layout<S, LOG2B, 2>{});
     if constexpr (!std::is_same<S, float>::value) {
-        if (v.paired && v.order == 0) return f(Layout<Pair<S>, LOG2B, 0>{});
-        if (v.paired && v.order == 1) return f(Layout<Pair<S>, LOG2B, 1>{});
-        if (v.paired && v.order == 2) return f(Layout<Pair<S>, LOG2B, 2>{});
+        if (v.paired == 1 && v.order == 0) return f(Layout<Pair<S>, LOG2B, 0>{});
+        if (v.paired == 1 && v.order == 1) return f(Layout<Pair<S>, LOG2B, 1>{});
+        if (v.paired == 1 && v.order == 2) return f(Layout<Pair<S>, LOG2B, 2>{});
     }
     return none;
 }
@@ -92,6 +123,7 @@ R visit_layout_b(const VolDev &v, F &&f, R none)
 template <typename S, typename F, typename R>
 R visit_layout_s(const VolDev &v, F &&f, R none)
 {
+    if (v.paired == 2) return none;                 // blocked copies: visit_layout_all
     switch (v.log2b) {
     case 4: return visit_layout_b<S, 4>(v, f, none);
     case 5: return visit_layout_b<S, 5>(v, f, none);
@@ -107,6 +139,40 @@ R visit_layout(const VolDev &v, vr_dtype dt, F &&f, R none)
     case VR_F32: return visit_layout_s<float>(v, f, none);
     case VR_F16: return visit_layout_s<__half>(v, f, none);
     case VR_BF16: return visit_layout_s<__nv_bfloat16>(v, f, none);
+    }
+    return none;
+}
+
+// visit_layout, blocked copies included (the kernels that read them: the
+// forward and the batched forward).
+template <typename S, int LOG2B, typename F, typename R>
+R visit_blocked_b(const VolDev &v, F &&f, R none)
+{
+    if (v.order == 0) return f(Layout<Blocked<S>, LOG2B, 0>{});
+    if (v.order == 1) return f(Layout<Blocked<S>, LOG2B, 1>{});
+    if (v.order == 2) return f(Layout<Blocked<S>, LOG2B, 2>{});
+    return none;
+}
+
+template <typename S, typename F, typename R>
+R visit_layout_all_s(const VolDev &v, F &&f, R none)
+{
+    if (v.paired != 2) return visit_layout_s<S>(v, f, none);
+    switch (v.log2b) {
+    case 4: return visit_blocked_b<S, 4>(v, f, none);
+    case 5: return visit_blocked_b<S, 5>(v, f, none);
+    case 6: return visit_blocked_b<S, 6>(v, f, none);
+    }
+    return none;
+}
+
+template <typename F, typename R>
+R visit_layout_all(const VolDev &v, vr_dtype dt, F &&f, R none)
+{
+    switch (dt) {
+    case VR_F32: return visit_layout_all_s<float>(v, f, none);
+    case VR_F16: return visit_layout_all_s<__half>(v, f, none);
+    case VR_BF16: return visit_layout_all_s<__nv_bfloat16>(v, f, none);
     }
     return none;
 }
@@ -236,6 +302,37 @@ __device__ __forceinline__ Cell locate(const VolDev &v, float3 p)
     return c;
 }
 
+// The cell of a sample in a blocked copy (storage S, copy axis W): base is
+// the element of corner (0, 0, 0); the corners' parities (the low bits of x0,
+// y0, z0, which B keeps inside the brick) give the other seven.
+template <typename S, int LOG2B, int W>
+__device__ __forceinline__ Cell locate_blocked(const VolDev &v, float3 p)
+{
+    Cell c;
+    c.x0 = min(max(__float2int_rd(p.x), 0), v.nx - 2);
+    c.y0 = min(max(__float2int_rd(p.y), 0), v.ny - 2);
+    c.z0 = min(max(__float2int_rd(p.z), 0), v.nz - 2);
+    c.fx = p.x - (float)c.x0;
+    c.fy = p.y - (float)c.y0;
+    c.fz = p.z - (float)c.z0;
+    using G = BlockGeom<(int)sizeof(S), LOG2B>;
+    constexpr int B = 1 << LOG2B;
+    const int bx = c.x0 >> LOG2B, by = c.y0 >> LOG2B, bz = c.z0 >> LOG2B;
+    const int lx = c.x0 & (B - 1), ly = c.y0 & (B - 1), lz = c.z0 & (B - 1);
+    const int lu = W == 0 ? ly : lx, lv = W == 2 ? ly : lz, lw = W == 0 ? lx : (W == 1 ? ly : lz);
+    const unsigned brick = ((unsigned)bz * (unsigned)v.nby + (unsigned)by) * (unsigned)v.nbx + (unsigned)bx;
+    c.base = (long long)((unsigned long long)brick * (unsigned)v.stride) + G::index(lu, lv, lw);
+    return c;
+}
+
+// The cell of a sample in the layout of element type T.
+template <typename T, int LOG2B, int L, bool NARROW>
+__device__ __forceinline__ Cell locate_t(const VolDev &v, float3 p)
+{
+    if constexpr (is_blocked<T>::value) return locate_blocked<typename T::storage, LOG2B, L>(v, p);
+    else return locate<LOG2B, L, NARROW>(v, p);
+}
+
 // The eight corners of a cell as floats (index bit 0: +x, bit 1: +y, bit 2: +z).
 struct Corners {
     float v[8];
@@ -263,6 +360,11 @@ template <typename S, int L> struct Gathered<Pair<S>, L> {
     }
 };
 
+template <typename S, int L> struct Gathered<Blocked<S>, L> {
+    S v[8];
+    __device__ __forceinline__ float at(int q) const { return to_f(v[q]); }
+};
+
 // T is the stored element: float / __half / __nv_bfloat16 (eight loads) or
 // Pair<...> (four paired loads; each returns a corner and its neighbour along
 // the fastest axis of order L).
@@ -270,7 +372,7 @@ template <typename T, int LOG2B, int L>
 __device__ __forceinline__ void fetch_corners(const VolDev &v, const Cell &c, Gathered<T, L> &f)
 {
     using O = BrickOrder<LOG2B, L>;
-    if constexpr (kBoundsCheck) {
+    if constexpr (kBoundsCheck && !is_blocked<T>::value) {
         constexpr long long span = is_pair<T>::value ? (L == 0 ? O::SY : O::SX) + (L == 2 ? O::SY : O::SZ)
                                                      : O::SX + O::SY + O::SZ;
         if (!index_ok(v.status, c.base, v.nelem) || !index_ok(v.status, c.base + span, v.nelem)) {
@@ -278,7 +380,32 @@ __device__ __forceinline__ void fetch_corners(const VolDev &v, const Cell &c, Ga
             return;
         }
     }
-    if constexpr (is_pair<T>::value) {
+    if constexpr (is_blocked<T>::value) {
+        using S = typename T::storage;
+        using G = BlockGeom<(int)sizeof(S), LOG2B>;
+        // steps to the +u, +v, +w neighbour of corner (0, 0, 0): inside its block,
+        // or into the next block across that axis
+        const int pu = L == 0 ? c.y0 : c.x0, pv = L == 2 ? c.y0 : c.z0, pw = L == 0 ? c.x0 : (L == 1 ? c.y0 : c.z0);
+        const int du = (pu & 1) ? G::BS - 1 : 1;
+        const int dv = (pv & 1) ? G::NU * G::BS - 2 : 2;
+        const int dw = (pw % G::BW == G::BW - 1) ? G::NV * G::NU * G::BS - (G::BW - 1) * 4 : 4;
+        const int dx = L == 0 ? dw : du, dy = L == 0 ? du : (L == 1 ? dw : dv), dz = L == 2 ? dw : dv;
+        if constexpr (kBoundsCheck) {
+            if (!index_ok(v.status, c.base, v.nelem) || !index_ok(v.status, c.base + dx + dy + dz, v.nelem)) {
+                f = Gathered<T, L>{};
+                return;
+            }
+        }
+        const S *b = static_cast<const S *>(v.data) + c.base;
+        f.v[0] = __ldg(b);
+        f.v[1] = __ldg(b + dx);
+        f.v[2] = __ldg(b + dy);
+        f.v[3] = __ldg(b + dx + dy);
+        f.v[4] = __ldg(b + dz);
+        f.v[5] = __ldg(b + dz + dx);
+        f.v[6] = __ldg(b + dz + dy);
+        f.v[7] = __ldg(b + dz + dx + dy);
+    } else if constexpr (is_pair<T>::value) {
         using V = typename T::V;
         const V *b = static_cast<const V *>(v.data) + c.base;
         // the three pair bases besides b: the two non-fastest axes and both
@@ -415,16 +542,15 @@ struct IdentityMap {
 
 // One sample: composites (cur, fc) and, while the ray goes on, issues the
 // gathers of sample k + depth into (nxt, fn).
-template <typename T, int LOG2B, int L, typename Map = IdentityMap>
+template <typename T, int LOG2B, int L, typename Map = IdentityMap, int D = Pipeline<T>::depth>
 __device__ __forceinline__ void march_step(const VolDev &v, const ParamDev &p, const Ray &ray, int &k, bool &active,
                                            Composite &acc, const Cell &cur, const Gathered<T, L> &fc, Cell &nxt,
                                            Gathered<T, L> &fn, const Map &map = Map())
 {
-    constexpr int D = Pipeline<T>::depth;
     constexpr bool N = !std::is_same<T, float>::value;
     const bool more = k + 1 < ray.n;
     if (D == 1 ? more : k + D < ray.n) {
-        nxt = locate<LOG2B, L, N>(v, sample_pos(ray, k + D, p.step));
+        nxt = locate_t<T, LOG2B, L, N>(v, sample_pos(ray, k + D, p.step));
         fetch_corners<T, LOG2B, L>(v, nxt, fn);
     }
     const float val = map(interp_corners(cur, fc), cur);
@@ -452,10 +578,10 @@ __device__ __forceinline__ int march_ray(const VolDev &v, const ParamDev &p, con
     Cell c0, c1, c2;
     Gathered<T, L> f0, f1, f2;
     if (active) {
-        c0 = locate<LOG2B, L, N>(v, sample_pos(ray, 0, p.step));
+        c0 = locate_t<T, LOG2B, L, N>(v, sample_pos(ray, 0, p.step));
         fetch_corners<T, LOG2B, L>(v, c0, f0);
         if (D == 2 && ray.n > 1) {
-            c1 = locate<LOG2B, L, N>(v, sample_pos(ray, 1, p.step));
+            c1 = locate_t<T, LOG2B, L, N>(v, sample_pos(ray, 1, p.step));
             fetch_corners<T, LOG2B, L>(v, c1, f1);
         }
     }

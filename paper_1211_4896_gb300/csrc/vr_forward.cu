@@ -130,7 +130,8 @@ static cudaError_t launch_fwd_t(const VolDev &v, const CamDev &c, const ParamDev
     cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(unsigned), s);
     if (e != cudaSuccess) return e;
     log_line("forward %dx%d: layout order %d%s, %u tiles of 8x4 rays, grid %u x %d threads (%d per SM)", c.W, c.H,
-             v.order, v.paired ? " paired" : "", ntiles, grid, kFwdThreads, per_sm);
+             v.order, v.paired == 1 ? " paired" : (v.paired == 2 ? " blocked" : ""), ntiles, grid, kFwdThreads,
+             per_sm);
     fn<<<grid, kFwdThreads, 0, s>>>(v, c, p, out, nsamples, counter, tiles_x, ntiles);
     return cudaGetLastError();
 }
@@ -138,7 +139,7 @@ static cudaError_t launch_fwd_t(const VolDev &v, const CamDev &c, const ParamDev
 cudaError_t launch_forward(const VolDev &v, vr_dtype dt, const CamDev &c, const ParamDev &p, float4 *out,
                            uint32_t *nsamples, unsigned *counter, cudaStream_t s)
 {
-    return visit_layout(
+    return visit_layout_all(
         v, dt,
         [&](auto lay) {
             using Y = decltype(lay);

@@ -51,7 +51,8 @@ struct VolDev {
     int log2b;             // B = 1 << log2b
     long long stride;      // elements per brick (>= (B+1)^3, padded)
     int order;             // element order inside a brick (0: x, 1: y, 2: z fastest)
-    int paired;            // 1: each element holds (own value, next value along the fastest axis)
+    int paired;            // 1: each element holds (own value, next value along the fastest axis);
+                           // 2: blocked, 2 x 2 x BW blocks of one 32-byte sector deep along axis `order`
     long long nelem;       // elements in the buffer (bricks x stride), for the bounds-check build
     unsigned *status;      // the volume's status word (timeouts, caught out-of-range indices)
 };
@@ -84,8 +85,9 @@ struct vr_volume {
     // copies of the bricks, built on the first software-filter call that
     // prefers them, indexed by copy id: 1, 2 plain copies with y / z fastest
     // (bytes each); 3, 4, 5 paired 16-bit copies with x / y / z fastest
-    // (2 * bytes each); [0] unused (the bricks themselves are copy -1)
-    void *copies[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    // (2 * bytes each); 6, 7, 8 blocked copies deep along x / y / z (sparse
+    // views, forward only); [0] unused (the bricks themselves are copy -1)
+    void *copies[9] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
     // backward scratch: one FP32 row of K RGBA gradient bins per warp
     float *wtab = nullptr;
     size_t wtab_cap = 0;         // floats
@@ -125,6 +127,7 @@ int sm_count();
 
 // Launchers (each .cu file).
 cudaError_t launch_brick(const void *src, vr_dtype src_dtype, vr_volume *vol, cudaStream_t s);
+cudaError_t launch_rebrick(const vr_volume *src, vr_volume *dst, cudaStream_t s);   // same dims and storage
 vr_status build_texture(vr_volume *vol, cudaStream_t s);
 cudaError_t launch_forward(const VolDev &v, vr_dtype dt, const CamDev &c, const ParamDev &p, float4 *out,
                            uint32_t *nsamples, unsigned *counter, cudaStream_t s);
@@ -136,11 +139,16 @@ cudaError_t launch_forward_texture(const vr_volume *vol, const CamDev &c, const 
 constexpr unsigned kStatusTimeout = 1u;        // a bounded wait gave up
 constexpr unsigned kStatusOutOfBounds = 2u;    // an index outside its buffer was caught and skipped
 
-constexpr int kCopyIds = 6;
-inline bool copy_paired(int copy) { return copy >= 3; }
-inline int copy_order(int copy) { return copy >= 3 ? copy - 3 : copy; }
+constexpr int kCopyIds = 9;
+inline bool copy_paired(int copy) { return copy >= 3 && copy < 6; }
+inline bool copy_blocked(int copy) { return copy >= 6; }
+inline int copy_order(int copy) { return copy >= 6 ? copy - 6 : (copy >= 3 ? copy - 3 : copy); }
+// Elements per brick of a blocked copy (B = 1 << log2b; elem_bytes 4 or 2).
+long long blocked_stride(int log2b, int elem_bytes);
 VolDev vol_dev_copy(const vr_volume *vol, int copy);
-int preferred_copy(vr_volume *vol, const vr_camera *cam, bool may_build, cudaStream_t s);
+// allow_blocked: the caller's kernels read blocked copies (the forward and
+// the batched forward); other callers get the plain or paired choice.
+int preferred_copy(vr_volume *vol, const vr_camera *cam, bool may_build, cudaStream_t s, bool allow_blocked = false);
 size_t copy_bytes(const vr_volume *vol, int copy);
 cudaError_t launch_copy(vr_volume *vol, int copy, cudaStream_t s);
 // One view of a backward call: the layout it reads (a brick copy or the

@@ -96,6 +96,61 @@ cudaError_t launch_brick(const void *src, vr_dtype src_dtype, vr_volume *vol, cu
     return cudaErrorInvalidValue;
 }
 
+// Re-bricking: the voxels of a volume's bricks (src) in bricks of another
+// size, without a dense copy.  One CTA per (destination brick, z-layer);
+// voxel (x, y, z) is read from the source brick that holds it.
+template <typename D>
+__global__ void __launch_bounds__(256) rebrick_kernel(VolDev src, D *__restrict__ dst, int log2b, int nbx, int nby,
+                                                      long long stride)
+{
+    const long long brick = blockIdx.x;
+    const int lz = blockIdx.y;
+    const int B = 1 << log2b, B1 = B + 1;
+    const int bx = (int)(brick % nbx);
+    const int by = (int)((brick / nbx) % nby);
+    const int bz = (int)(brick / ((long long)nbx * nby));
+    const int z = min(bz * B + lz, src.nz - 1);
+    const int SB1 = (1 << src.log2b) + 1;
+    const int sbz = min(z >> src.log2b, src.nbz - 1), slz = z - (sbz << src.log2b);
+    const D *sv = static_cast<const D *>(src.data);
+    D *out = dst + brick * stride + (long long)lz * B1 * B1;
+    for (int e = threadIdx.x; e < B1 * B1; e += blockDim.x) {
+        const int ly = e / B1, lx = e - ly * B1;
+        const int x = min(bx * B + lx, src.nx - 1), y = min(by * B + ly, src.ny - 1);
+        const int sbx = min(x >> src.log2b, src.nbx - 1), sby = min(y >> src.log2b, src.nby - 1);
+        const int slx = x - (sbx << src.log2b), sly = y - (sby << src.log2b);
+        const long long sb = ((long long)sbz * src.nby + sby) * src.nbx + sbx;
+        out[e] = sv[sb * src.stride + ((long long)slz * SB1 + sly) * SB1 + slx];
+    }
+    if (lz == B1 - 1) {
+        D *pad = dst + brick * stride + (long long)B1 * B1 * B1;
+        const long long npad = stride - (long long)B1 * B1 * B1;
+        for (long long e = threadIdx.x; e < npad; e += blockDim.x) pad[e] = convert_voxel<float, D>(0.0f);
+    }
+}
+
+cudaError_t launch_rebrick(const vr_volume *src, vr_volume *dst, cudaStream_t s)
+{
+    const long long nbricks = dst->nb[0] * dst->nb[1] * dst->nb[2];
+    dim3 grid((unsigned)nbricks, (unsigned)(dst->brick + 1));
+    const VolDev v = vol_dev(src);
+    switch (dst->store_dtype) {
+    case VR_F32:
+        rebrick_kernel<float><<<grid, 256, 0, s>>>(v, static_cast<float *>(dst->bricks), dst->log2b, (int)dst->nb[0],
+                                                   (int)dst->nb[1], dst->stride);
+        break;
+    case VR_F16:
+        rebrick_kernel<__half><<<grid, 256, 0, s>>>(v, static_cast<__half *>(dst->bricks), dst->log2b,
+                                                    (int)dst->nb[0], (int)dst->nb[1], dst->stride);
+        break;
+    case VR_BF16:
+        rebrick_kernel<__nv_bfloat16><<<grid, 256, 0, s>>>(v, static_cast<__nv_bfloat16 *>(dst->bricks), dst->log2b,
+                                                           (int)dst->nb[0], (int)dst->nb[1], dst->stride);
+        break;
+    }
+    return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------------------
 // Hardware-filter copy: a 3D CUDA array written from the bricks through a
 // surface, sampled with cudaFilterModeLinear (the measured alternative).
@@ -225,6 +280,36 @@ __global__ void __launch_bounds__(256) pair_kernel(const D *__restrict__ src, ty
     }
 }
 
+// Blocked copy (see Blocked in vr_device.cuh): one CTA per brick, writes in
+// the blocked order (coalesced), each element read from the x-fastest brick;
+// padding elements (past the apron) are zero.
+template <typename D, int LOG2B, int W>
+__global__ void __launch_bounds__(256) block_kernel(const D *__restrict__ src, D *__restrict__ dst,
+                                                    long long src_stride)
+{
+    using G = BlockGeom<(int)sizeof(D), LOG2B>;
+    constexpr int B1 = (1 << LOG2B) + 1;
+    const D *s = src + (long long)blockIdx.x * src_stride;
+    D *o = dst + (long long)blockIdx.x * G::stride;
+    for (int e = threadIdx.x; e < (int)G::stride; e += blockDim.x) {
+        const int blk = e / G::BS, in = e - blk * G::BS;
+        const int bu = blk % G::NU, bv = (blk / G::NU) % G::NV, bw = blk / (G::NU * G::NV);
+        const int lu = 2 * bu + (in & 1), lv = 2 * bv + ((in >> 1) & 1), lw = bw * G::BW + (in >> 2);
+        const int lx = W == 0 ? lw : lu, ly = W == 0 ? lu : (W == 1 ? lw : lv), lz = W == 2 ? lw : lv;
+        o[e] = (lx < B1 && ly < B1 && lz < B1) ? s[((long long)lz * B1 + ly) * B1 + lx]
+                                               : convert_voxel<float, D>(0.0f);
+    }
+}
+
+long long blocked_stride(int log2b, int elem_bytes)
+{
+    switch (log2b) {
+    case 4: return elem_bytes == 4 ? BlockGeom<4, 4>::stride : BlockGeom<2, 4>::stride;
+    case 5: return elem_bytes == 4 ? BlockGeom<4, 5>::stride : BlockGeom<2, 5>::stride;
+    default: return elem_bytes == 4 ? BlockGeom<4, 6>::stride : BlockGeom<2, 6>::stride;
+    }
+}
+
 template <typename D, int LOG2B, int L, bool PAIRED>
 static void copy_t(vr_volume *vol, void *dst, cudaStream_t s)
 {
@@ -243,12 +328,17 @@ template <typename D, int LOG2B>
 static void copy_b(vr_volume *vol, int copy, cudaStream_t s)
 {
     void *dst = vol->copies[copy];
+    const unsigned nbricks = (unsigned)(vol->nb[0] * vol->nb[1] * vol->nb[2]);
+    const D *src = static_cast<const D *>(vol->bricks);
     switch (copy) {
     case 1: copy_t<D, LOG2B, 1, false>(vol, dst, s); break;
     case 2: copy_t<D, LOG2B, 2, false>(vol, dst, s); break;
     case 3: copy_t<D, LOG2B, 0, true>(vol, dst, s); break;
     case 4: copy_t<D, LOG2B, 1, true>(vol, dst, s); break;
-    default: copy_t<D, LOG2B, 2, true>(vol, dst, s); break;
+    case 5: copy_t<D, LOG2B, 2, true>(vol, dst, s); break;
+    case 6: block_kernel<D, LOG2B, 0><<<nbricks, 256, 0, s>>>(src, static_cast<D *>(dst), vol->stride); break;
+    case 7: block_kernel<D, LOG2B, 1><<<nbricks, 256, 0, s>>>(src, static_cast<D *>(dst), vol->stride); break;
+    default: block_kernel<D, LOG2B, 2><<<nbricks, 256, 0, s>>>(src, static_cast<D *>(dst), vol->stride); break;
     }
 }
 
@@ -262,7 +352,14 @@ static void copy_d(vr_volume *vol, int copy, cudaStream_t s)
     }
 }
 
-size_t copy_bytes(const vr_volume *vol, int copy) { return copy_paired(copy) ? 2 * vol->bytes : vol->bytes; }
+size_t copy_bytes(const vr_volume *vol, int copy)
+{
+    if (copy_blocked(copy)) {
+        const int eb = vol->store_dtype == VR_F32 ? 4 : 2;
+        return (size_t)(vol->nb[0] * vol->nb[1] * vol->nb[2]) * (size_t)blocked_stride(vol->log2b, eb) * (size_t)eb;
+    }
+    return copy_paired(copy) ? 2 * vol->bytes : vol->bytes;
+}
 
 cudaError_t launch_copy(vr_volume *vol, int copy, cudaStream_t s)
 {

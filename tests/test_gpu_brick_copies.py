@@ -7,9 +7,11 @@ a sample does not depend on where its corners are stored, so a view and the
 same view rolled by 90 degrees about its forward axis (same rays, image
 transposed; square image, the eye on the axis) agree bit for bit although
 they read different layouts; so do a render from the bricks themselves and
-one from a copy.  Covered: single renders, one batch reading every layout,
-the allocation-free batch, the backward, and a voxel update that must
-refresh the copies.  Both views are also checked against the oracle."""
+one from a copy.  Views whose rays are far apart read blocked copies
+(2 x 2 x BW blocks of one sector, deep along the rays' main axis).  Covered:
+single renders, one batch reading every layout, the allocation-free batch,
+the backward, and a voxel update that must refresh the copies.  Both views
+are also checked against the oracle."""
 import numpy as np
 import pytest
 
@@ -190,40 +192,86 @@ def test_half_paired_copies_match_bricks(P, torch, scene, store):
         vol.close()
 
 
-@pytest.mark.parametrize("store", ["f16", "bf16"])
-def test_half_sparse_rays_read_plain_copies(P, torch, scene, store):
-    """16-bit storage with rays about 3-4 voxels apart (16x16 image of the
-    40x36x44 cube): the views read plain copies (half the bytes of paired
-    ones), bit for bit the bricks' result, and a rolled view matches."""
+def _sparse_blocked_case(P, torch, scene, store, brick):
+    """Rays about 3-4 voxels apart (16x16 images of the 40x36x44 cube): the
+    forward reads a blocked copy (2 x 2 x 2 float or 2 x 2 x 4 16-bit blocks
+    of one 32-byte sector, deep along the axis the rays advance along), bit
+    for bit the result of the bricks themselves (read by the allocation-free
+    batch, which builds no copy); a rolled view matches; a batch of these
+    views reads the same copies and equals the single renders."""
     cube, tf_np = scene
-    vol = _volume(P, torch, cube, store)
+    vol = P.Volume(torch.from_numpy(np.ascontiguousarray(cube)).cuda(), store, brick=brick)
     tf = torch.from_numpy(tf_np).cuda()
     n = 16
     i, j = np.arange(n)[None, :], np.arange(n)[:, None]
+    from paper_1211_4896_gb300 import _lib as L
     try:
-        cams = [_cam(*PAIRS[0][0], "persp", n), _cam(*PAIRS[0][1], "persp", n), _cam(*PAIRS[1][1], "ortho", n)]
+        cams = [_cam(*PAIRS[0][0], "persp", n), _cam(*PAIRS[0][1], "persp", n), _cam(*PAIRS[1][1], "ortho", n),
+                _cam((1, 0, 0), (0, 1, 0), "persp", n)]
         plain = []
         for c in cams:
             out = torch.full((n, n, 4), -1.0, device="cuda")
             ns = torch.full((n, n), -1, device="cuda", dtype=torch.int32)
-            from paper_1211_4896_gb300 import _lib as L
             job = L.vr_job(vol.handle, L.make_camera(c),
                            L.make_params(tf.data_ptr(), tf.shape[0], VMIN, VMAX, STEP, 2.0), out.data_ptr(),
                            ns.data_ptr())
             L.vr_render_batched_noalloc([job], 8, 4, int(torch.cuda.current_stream().cuda_stream))
             torch.cuda.synchronize()
             plain.append((out, ns))
+        assert _copies(P, vol) == 0
         for c, (img0, ns0) in zip(cams, plain):
             img, ns = P.render(vol, c, tf, VMIN, VMAX, STEP)
             torch.cuda.synchronize()
             assert torch.equal(img, img0) and torch.equal(ns, ns0)
-        assert _copies(P, vol) == 0b110                 # plain y and z copies, no paired ones
+        # blocked copies deep along z (views along z), y and x: ids 8, 7, 6
+        assert _copies(P, vol) == (1 << 8) | (1 << 7) | (1 << 6)
+        assert [L.vr_view_layout(vol.handle, L.make_camera(c)) for c in cams] == [8, 8, 7, 6]
+        info = L.vr_volume_info(vol.handle)
+        eb = 4 if store == "f32" else 2
+        bw = 2 if eb == 4 else 4
+        per = (brick + 2) ** 2 * ((brick + bw) // bw * bw) * eb * int(np.prod(info["bricks"]))
+        assert info["copy_bytes"] == 3 * per
         a = plain[0][0].cpu().numpy()
         b, _ = P.render(vol, cams[1], tf, VMIN, VMAX, STEP)
         assert np.array_equal(b.cpu().numpy(), a[n - 1 - i, j])
         assert a[..., 3].max() > 0.1
+        jobs = [dict(vol=vol, cam=c, tf=tf, vmin=VMIN, vmax=VMAX, step=STEP,
+                     out=torch.empty((n, n, 4), device="cuda"),
+                     nsamples=torch.empty((n, n), device="cuda", dtype=torch.int32)) for c in cams]
+        P.render_batched(jobs, use_graph=True)
+        torch.cuda.synchronize()
+        for jb, (img0, ns0) in zip(jobs, plain):
+            assert torch.equal(jb["out"], img0) and torch.equal(jb["nsamples"], ns0)
+        if store == "f32":
+            for c, (img, ns) in zip(cams, plain):
+                compare(img.cpu().numpy(), ns.cpu().numpy(), oracle.render(cube, c, tf_np, VMIN, VMAX, STEP), TOL_F32)
     finally:
         vol.close()
+
+
+@pytest.mark.parametrize("store,brick", [("f16", 16), ("bf16", 16), ("f16", 32)])
+def test_sparse_rays_read_blocked_copies(P, torch, scene, store, brick):
+    """16-bit storage: sparse views read blocked copies by default."""
+    _sparse_blocked_case(P, torch, scene, store, brick)
+
+
+@pytest.mark.parametrize("brick", [16, 32])
+def test_float_sparse_rays_read_blocked_copies_when_asked(brick):
+    """Float storage reads blocked copies for sparse views when
+    VR_SPARSE_LAYOUT=b (a separate process: the library reads the variable
+    once)."""
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = dict(os.environ, VR_SPARSE_LAYOUT="b",
+               PYTHONPATH=root + os.pathsep + os.environ.get("PYTHONPATH", ""))
+    code = ("import torch, tests.test_gpu_brick_copies as t, paper_1211_4896_gb300 as P, synth\n"
+            "cube = synth.hi_cube(t.DIMS, n_blobs=8, n_disks=1, seed=7).numpy()\n"
+            "tf = synth.tf_random_pwl(seed=3, alpha_max=0.3)\n"
+            "t._sparse_blocked_case(P, torch, (cube, tf), 'f32', %d)\nprint('ok')\n" % brick)
+    r = subprocess.run([sys.executable, "-c", code], cwd=root, env=env, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0 and "ok" in r.stdout, r.stdout[-2000:] + r.stderr[-4000:]
 
 
 @pytest.mark.parametrize("pair", range(len(PAIRS)))
