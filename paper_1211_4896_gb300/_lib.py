@@ -57,11 +57,13 @@ class vr_grad_view(C.Structure):
 
 
 class vr_batch_opts(C.Structure):
-    _fields_ = [("use_graph", C.c_int), ("tile_w", C.c_int), ("tile_h", C.c_int), ("ctas_per_sm", C.c_int)]
+    _fields_ = [("use_graph", C.c_int), ("tile_w", C.c_int), ("tile_h", C.c_int), ("ctas_per_sm", C.c_int),
+                ("warps_per_tile", C.c_int)]
 
 
 # every symbol include/vr.h declares
-EXPORTS = ("vr_volume_create", "vr_volume_update", "vr_volume_destroy", "vr_volume_info", "vr_view_layout",
+EXPORTS = ("vr_volume_create", "vr_volume_rebrick", "vr_volume_update", "vr_volume_destroy", "vr_volume_info",
+           "vr_view_layout",
            "vr_render",
            "vr_render_backward", "vr_render_backward_views", "vr_render_batched", "vr_autotune_batched", "vr_render_batched_noalloc",
            "vr_minimap", "vr_profile", "vr_render_subbox", "vr_render_subbox_of", "vr_composite", "vr_moments",
@@ -94,6 +96,7 @@ def load() -> C.CDLL:
         P, vp = C.POINTER, C.c_void_p
         L.vr_volume_create.argtypes = [vp, C.c_int, C.c_int, P(C.c_int64 * 3), P(C.c_double * 3),
                                        P(C.c_double * 3), C.c_int, vp, P(vp)]
+        L.vr_volume_rebrick.argtypes = [vp, C.c_int, vp, P(vp)]
         L.vr_volume_update.argtypes = [vp, vp, C.c_int, vp]
         L.vr_volume_destroy.argtypes = [vp]
         L.vr_volume_info.argtypes = [vp, P(vr_volume_info_t)]
@@ -121,7 +124,8 @@ def load() -> C.CDLL:
         L.vr_moments.argtypes = [vp, vp, vp]
         L.vr_histogram.argtypes = [vp, C.c_double, C.c_double, C.c_int, vp, vp]
         L.vr_median.argtypes = [vp, vp, vp]
-        for name in ("vr_volume_create", "vr_volume_update", "vr_volume_destroy", "vr_volume_info", "vr_view_layout",
+        for name in ("vr_volume_create", "vr_volume_rebrick", "vr_volume_update", "vr_volume_destroy",
+                     "vr_volume_info", "vr_view_layout",
                      "vr_render",
                      "vr_render_backward", "vr_render_backward_views", "vr_render_batched", "vr_autotune_batched",
                      "vr_render_batched_noalloc", "vr_minimap", "vr_profile", "vr_render_subbox", "vr_render_subbox_of",
@@ -178,6 +182,12 @@ def vr_volume_create(dev_cube: int, src_dtype: int, store_dtype: int, dims, orig
     _check("vr_volume_create", L.vr_volume_create(dev_cube, src_dtype, store_dtype, C.byref(d),
                                                   C.byref(o) if o else None, C.byref(s) if s else None,
                                                   int(brick), stream, C.byref(out)))
+    return out.value
+
+
+def vr_volume_rebrick(vol: int, brick: int, stream: int = 0) -> int:
+    out = C.c_void_p()
+    _check("vr_volume_rebrick", load().vr_volume_rebrick(vol, int(brick), stream, C.byref(out)))
     return out.value
 
 

@@ -57,6 +57,17 @@ class Volume:
                                              self.origin, self.spacing, brick, _stream(stream))
         self.info = L.vr_volume_info(self.handle)
 
+    def rebrick(self, brick: int, stream=None) -> "Volume":
+        """A new Volume with the same voxels in bricks of `brick` (16, 32 or
+        64), built on the device from this one's bricks."""
+        out = Volume.__new__(Volume)
+        for k in ("src_dtype", "store_dtype", "dims", "shape", "device", "origin", "spacing"):
+            setattr(out, k, getattr(self, k))
+        with torch.cuda.device(self.device):
+            out.handle = L.vr_volume_rebrick(self.handle, int(brick), _stream(stream))
+        out.info = L.vr_volume_info(out.handle)
+        return out
+
     def update(self, cube: torch.Tensor, stream=None):
         _need_cuda(cube, "cube")
         if tuple(cube.shape) != self.shape or _DTYPES.get(cube.dtype) != self.src_dtype:
@@ -326,15 +337,51 @@ def cached_tuning(key: str, tune, cache_path=None) -> dict:
 
 
 def autotune_batched(jobs, cache_path=None, stream=None) -> L.vr_batch_opts:
-    """Ray-tile shape and CTAs per SM for this job list (vr_autotune_batched
-    tries each and keeps the fastest), remembered across processes in the
-    autotune cache (cache_path or $VR_AUTOTUNE_CACHE) under autotune_key."""
+    """Ray-tile shape, CTAs per SM and warps per tile for this job list
+    (vr_autotune_batched tries each and keeps the fastest), remembered across
+    processes in the autotune cache (cache_path or $VR_AUTOTUNE_CACHE) under
+    autotune_key; the entry records the volumes' brick size too."""
     def tune():
         cj = render_batched(jobs, use_graph=False, stream=stream)
         best = L.vr_autotune_batched(cj, L.vr_batch_opts(0, 0, 0, 0), _stream(stream))
-        return {"tile_w": best.tile_w, "tile_h": best.tile_h, "ctas_per_sm": best.ctas_per_sm}
+        return {"tile_w": best.tile_w, "tile_h": best.tile_h, "ctas_per_sm": best.ctas_per_sm,
+                "warps_per_tile": best.warps_per_tile, "brick": int(jobs[0]["vol"].info["brick"])}
     b = cached_tuning(autotune_key(jobs), tune, cache_path)
-    return L.vr_batch_opts(1, b["tile_w"], b["tile_h"], b["ctas_per_sm"])
+    return L.vr_batch_opts(1, b["tile_w"], b["tile_h"], b["ctas_per_sm"], b.get("warps_per_tile", 1))
+
+
+def autotune_batched_bricks(jobs, brick_sizes=(16, 32, 64), cache_path=None, stream=None, reps: int = 3):
+    """The batched autotuner over brick sizes as well: for each size the job
+    list's volumes are re-bricked once (Volume.rebrick, kept on the source
+    Volume for later calls), autotune_batched picks tile shape, CTAs per SM and
+    warps per tile for it, and the size whose tuned graph call is fastest wins.
+    Returns (opts, brick, jobs) with `jobs` rewritten onto the volumes of that
+    brick size."""
+    best = None
+    s = _stream(stream)
+    for b in brick_sizes:
+        vj = []
+        for j in jobs:
+            v = j["vol"]
+            if int(v.info["brick"]) != b:
+                cache = v.__dict__.setdefault("_rebricked", {})
+                if b not in cache:
+                    cache[b] = v.rebrick(b, stream)
+                v = cache[b]
+            vj.append(dict(j, vol=v))
+        opts = autotune_batched(vj, cache_path, stream)
+        cj = render_batched(vj, opts=opts, stream=stream)              # plan + graph
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            L.vr_render_batched(cj, opts, s)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        if best is None or ms < best[0]:
+            best = (ms, opts, b, vj)
+    return best[1], best[2], best[3]
 
 
 def render_batched(jobs, use_graph: bool = True, tile=(8, 4), ctas_per_sm: int = 0, stream=None,

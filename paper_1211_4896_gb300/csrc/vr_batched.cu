@@ -34,22 +34,42 @@ struct JobDev {
 // single march; a batch reading several copies launches once per copy).
 // CTAs per SM the register budget is sized for: paired 16-bit copies fit
 // four (64 registers) without spills and gain from it; the other kernels keep
-// the compiler's choice (for float, three CTAs measured faster than four).
+// the compiler's choice (for float, three CTAs measured faster than four), so
+// do the kernels whose warps share tiles (their hand-over spills at 64).
 template <typename T> struct BatMinBlocks { static constexpr int value = 0; };   // 0: no minimum
 template <> struct BatMinBlocks<Pair<__half>> { static constexpr int value = 4; };
 template <> struct BatMinBlocks<Pair<__nv_bfloat16>> { static constexpr int value = 4; };
 
-template <typename T, int LOG2B, int L>
-__global__ void __launch_bounds__(kBatThreads, BatMinBlocks<T>::value) batched_kernel(const JobDev *__restrict__ jobs, int njobs,
+// Warps per tile: 2^log2_wpt warps of a CTA take one tile of tw x (th 2^log2_wpt)
+// rays together, each its own tw x th part, so that the neighbouring parts
+// run on one SM and share its L1; the group's first lane takes the tile from
+// the queue and hands it over through shared memory between two named
+// barriers of the group (the second keeps the slot until all have read it).
+__device__ __forceinline__ void group_barrier(int id, int threads)
+{
+    asm volatile("bar.sync %0, %1;\n" ::"r"(id), "r"(threads) : "memory");
+}
+
+template <typename T, int LOG2B, int L, int LOG2_WPT>
+__global__ void __launch_bounds__(kBatThreads, LOG2_WPT ? 0 : BatMinBlocks<T>::value) batched_kernel(const JobDev *__restrict__ jobs, int njobs,
                                                                unsigned total_tiles, unsigned *counter,
                                                                int log2_tw)
 {
+    __shared__ unsigned handed[kBatThreads / 32];
     const int lane = threadIdx.x & 31;
     const int tw = 1 << log2_tw;
     for (;;) {
         unsigned tile = 0;
-        if (lane == 0) tile = atomicAdd(counter, 1u);
-        tile = __shfl_sync(kFull, tile, 0);
+        if constexpr (LOG2_WPT == 0) {
+            if (lane == 0) tile = atomicAdd(counter, 1u);
+            tile = __shfl_sync(kFull, tile, 0);
+        } else {
+            const int group = (threadIdx.x >> 5) >> LOG2_WPT;
+            if ((threadIdx.x & ((32 << LOG2_WPT) - 1)) == 0) handed[group] = atomicAdd(counter, 1u);
+            group_barrier(1 + group, 32 << LOG2_WPT);
+            tile = handed[group];
+            group_barrier(1 + group, 32 << LOG2_WPT);
+        }
         if (tile >= total_tiles) break;
         // job = last j with tile_begin <= tile
         int lo = 0, hi = njobs - 1;
@@ -59,8 +79,10 @@ __global__ void __launch_bounds__(kBatThreads, BatMinBlocks<T>::value) batched_k
         }
         const JobDev &J = jobs[lo];
         const unsigned local = tile - J.tile_begin;
+        const int th = 32 >> log2_tw;
         const int i = (int)(local % J.tiles_x) * tw + (lane & (tw - 1));
-        const int j = (int)(local / J.tiles_x) * (32 >> log2_tw) + (lane >> log2_tw);
+        const int part = (threadIdx.x >> 5) & ((1 << LOG2_WPT) - 1);
+        const int j = (((int)(local / J.tiles_x) << LOG2_WPT) + part) * th + (lane >> log2_tw);
         const CamDev c = J.c;
         const ParamDev p = J.p;
         const VolDev v = J.v;
@@ -75,14 +97,19 @@ __global__ void __launch_bounds__(kBatThreads, BatMinBlocks<T>::value) batched_k
 
 using BatchFn = void (*)(const JobDev *, int, unsigned, unsigned *, int);
 
-// Kernel for the brick layout v reads (see Layout).
-static BatchFn pick_kernel(const VolDev &v, vr_dtype dt)
+// Kernel for the brick layout v reads (see Layout) and 2^log2_wpt warps per tile.
+static BatchFn pick_kernel(const VolDev &v, vr_dtype dt, int log2_wpt)
 {
-    return visit_layout(
+    return visit_layout_all(
         v, dt,
-        [](auto lay) -> BatchFn {
+        [&](auto lay) -> BatchFn {
             using Y = decltype(lay);
-            return batched_kernel<typename Y::type, Y::log2b, Y::order>;
+            switch (log2_wpt) {
+            case 0: return batched_kernel<typename Y::type, Y::log2b, Y::order, 0>;
+            case 1: return batched_kernel<typename Y::type, Y::log2b, Y::order, 1>;
+            case 2: return batched_kernel<typename Y::type, Y::log2b, Y::order, 2>;
+            }
+            return (BatchFn) nullptr;
         },
         (BatchFn) nullptr);
 }
@@ -108,6 +135,7 @@ struct BatchPlan {
     int njobs = 0;
     Segment seg[kGroups];
     int log2_tw = 3;
+    int log2_wpt = 0;
     cudaGraphExec_t exec = nullptr;
     int device = 0;
 };
@@ -127,7 +155,8 @@ template <typename V> static void key_put(std::vector<unsigned char> &k, const V
     k.insert(k.end(), b, b + sizeof(V));
 }
 
-static std::vector<unsigned char> plan_key(int dev, cudaStream_t s, int tile_w, int ctas, const vr_job *jobs, int n)
+static std::vector<unsigned char> plan_key(int dev, cudaStream_t s, int tile_w, int ctas, int wpt, const vr_job *jobs,
+                                           int n)
 {
     std::vector<unsigned char> k;
     k.reserve(64 + (size_t)n * 200);
@@ -135,6 +164,7 @@ static std::vector<unsigned char> plan_key(int dev, cudaStream_t s, int tile_w, 
     key_put(k, s);
     key_put(k, tile_w);
     key_put(k, ctas);
+    key_put(k, wpt);
     for (int q = 0; q < n; ++q) {
         const vr_job &J = jobs[q];
         key_put(k, J.vol);
@@ -173,10 +203,11 @@ static int log2_of(int x)
 // copies in order 0, 1, 2; call order within a group), and fills seg[] with
 // each group's offset, tile count and kernel.  group_of, order and cost are
 // host scratch of n entries.  may_build allows building a missing copy.
-static vr_status prepare_jobs(const vr_job *jobs, int n, int tile_w, bool may_build, cudaStream_t s, JobDev *hj,
-                              int *group_of, int *order, double *cost, Segment seg[kGroups], const char *who)
+static vr_status prepare_jobs(const vr_job *jobs, int n, int tile_w, int wpt, bool may_build, cudaStream_t s,
+                              JobDev *hj, int *group_of, int *order, double *cost, Segment seg[kGroups],
+                              const char *who)
 {
-    const int tile_h = 32 / tile_w;
+    const int tile_h = 32 / tile_w * wpt;           // rows of one group's tile
     vr_dtype dt = VR_F32;
     int log2b = 5;
     for (int g = 0; g < kGroups; ++g) seg[g] = Segment();
@@ -195,7 +226,7 @@ static vr_status prepare_jobs(const vr_job *jobs, int n, int tile_w, bool may_bu
             return (set_error(std::string(who) + ": all volumes of a batch must share store dtype and brick size"),
                     VR_ERR_UNSUPPORTED);
         }
-        group_of[q] = preferred_copy(J.vol, &J.cam, may_build, s) + 1;
+        group_of[q] = preferred_copy(J.vol, &J.cam, may_build, s, true) + 1;
         ++seg[group_of[q]].njobs;
     }
     int fill[kGroups];
@@ -237,22 +268,23 @@ static vr_status prepare_jobs(const vr_job *jobs, int n, int tile_w, bool may_bu
     }
     for (int g = 0; g < kGroups; ++g) {
         if (!seg[g].njobs) continue;
-        seg[g].fn = pick_kernel(hj[seg[g].first].v, dt);     // one layout per group
+        seg[g].fn = pick_kernel(hj[seg[g].first].v, dt, log2_of(wpt));     // one layout per group
         if (!seg[g].fn) return (set_error(std::string(who) + ": unsupported brick size"), VR_ERR_UNSUPPORTED);
     }
     return VR_OK;
 }
 
 // Persistent grid of each group: ctas_per_sm (0: the occupancy limit) x SMs,
-// capped at one warp per tile.
-static void size_grids(Segment seg[kGroups], int ctas)
+// capped at one warp per part of a tile.
+static void size_grids(Segment seg[kGroups], int ctas, int wpt)
 {
     for (int o = 0; o < kGroups; ++o) {
         Segment &g = seg[o];
         if (!g.njobs) continue;
         const int per_sm = ctas > 0 ? ctas : occupancy_blocks((const void *)g.fn, kBatThreads, 0);   // cached
         const unsigned grid = (unsigned)(per_sm * sm_count());
-        const unsigned useful = (g.total_tiles + kBatThreads / 32 - 1) / (kBatThreads / 32);
+        const unsigned per_cta = (unsigned)(kBatThreads / 32 / wpt);          // tiles a CTA works on at once
+        const unsigned useful = (g.total_tiles + per_cta - 1) / per_cta;
         g.grid = grid < useful ? grid : (useful ? useful : 1);
         log_line("batch, brick layout %d: %d job(s), %u tiles, grid %u x %d threads", o - 1, g.njobs, g.total_tiles,
                  g.grid, kBatThreads);
@@ -311,7 +343,8 @@ static cudaError_t launch_segments(const Segment seg[kGroups], const JobDev *djo
     return e;
 }
 
-static vr_status validate_batch(const vr_job *jobs, int n, const vr_batch_opts *opts, int &tile_w, int &ctas)
+static vr_status validate_batch(const vr_job *jobs, int n, const vr_batch_opts *opts, int &tile_w, int &ctas,
+                                int &wpt)
 {
     if (!jobs || n < 1) return (set_error("jobs must be non-NULL with n >= 1"), VR_ERR_INVALID_ARG);
     if (n > 65536) return (set_error("n must be <= 65536"), VR_ERR_INVALID_ARG);
@@ -321,6 +354,9 @@ static vr_status validate_batch(const vr_job *jobs, int n, const vr_batch_opts *
         return (set_error("tile_w * tile_h must be 32 with tile_w a power of two"), VR_ERR_INVALID_ARG);
     ctas = opts ? opts->ctas_per_sm : 0;
     if (ctas < 0 || ctas > 32) return (set_error("ctas_per_sm must be in [0, 32]"), VR_ERR_INVALID_ARG);
+    wpt = (opts && opts->warps_per_tile) ? opts->warps_per_tile : 1;
+    if (wpt != 1 && wpt != 2 && wpt != 4)
+        return (set_error("warps_per_tile must be 0, 1, 2 or 4"), VR_ERR_INVALID_ARG);
     return VR_OK;
 }
 
@@ -355,8 +391,8 @@ using namespace vr;
 extern "C" vr_status vr_render_batched(const vr_job *jobs, int n, const vr_batch_opts *opts, void *cuda_stream)
 {
     set_error("");
-    int tile_w = 8, ctas = 0;
-    vr_status st = validate_batch(jobs, n, opts, tile_w, ctas);
+    int tile_w = 8, ctas = 0, wpt = 1;
+    vr_status st = validate_batch(jobs, n, opts, tile_w, ctas, wpt);
     if (st != VR_OK) return st;
     for (int q = 0; q < n; ++q) {
         st = validate_job(&jobs[q], q);
@@ -367,7 +403,7 @@ extern "C" vr_status vr_render_batched(const vr_job *jobs, int n, const vr_batch
     int dev = 0;
     cudaGetDevice(&dev);
 
-    const std::vector<unsigned char> key = plan_key(dev, s, tile_w, ctas, jobs, n);
+    const std::vector<unsigned char> key = plan_key(dev, s, tile_w, ctas, wpt, jobs, n);
 
     std::lock_guard<std::mutex> g(g_plans_mu);
     BatchPlan *plan = nullptr;
@@ -378,10 +414,10 @@ extern "C" vr_status vr_render_batched(const vr_job *jobs, int n, const vr_batch
         std::vector<int> group_of((size_t)n), order((size_t)n);
         std::vector<double> cost((size_t)n);
         Segment seg[kGroups];
-        st = prepare_jobs(jobs, n, tile_w, true, s, hj.data(), group_of.data(), order.data(), cost.data(), seg,
+        st = prepare_jobs(jobs, n, tile_w, wpt, true, s, hj.data(), group_of.data(), order.data(), cost.data(), seg,
                           "vr_render_batched");
         if (st != VR_OK) return st;
-        size_grids(seg, ctas);
+        size_grids(seg, ctas, wpt);
         plan = new BatchPlan();
         plan->key = key;
         plan->njobs = n;
@@ -390,6 +426,7 @@ extern "C" vr_status vr_render_batched(const vr_job *jobs, int n, const vr_batch
                 plan->vols.push_back(jobs[q].vol);
         for (int g = 0; g < kGroups; ++g) plan->seg[g] = seg[g];
         plan->log2_tw = log2_of(tile_w);
+        plan->log2_wpt = log2_of(wpt);
         plan->device = dev;
         cudaError_t e = dev_alloc(reinterpret_cast<void **>(&plan->djobs), sizeof(JobDev) * (size_t)n);
         if (e == cudaSuccess) e = dev_alloc(reinterpret_cast<void **>(&plan->counter), kGroups * sizeof(unsigned));
@@ -432,6 +469,7 @@ extern "C" vr_status vr_autotune_batched(const vr_job *jobs, int n, vr_batch_opt
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
     const int shapes[4][2] = {{8, 4}, {4, 8}, {16, 2}, {32, 1}};
     const int ctas_list[5] = {0, 1, 2, 3, 4};
+    const int wpt_list[3] = {1, 2, 4};
     float best_ms = 1e30f;
     vr_batch_opts win = *best;
     cudaEvent_t e0, e1;
@@ -440,10 +478,12 @@ extern "C" vr_status vr_autotune_batched(const vr_job *jobs, int n, vr_batch_opt
     vr_status result = VR_OK;
     for (auto &sh : shapes) {
         for (int ct : ctas_list) {
+          for (int wpt : wpt_list) {
             vr_batch_opts o = *best;
             o.tile_w = sh[0];
             o.tile_h = sh[1];
             o.ctas_per_sm = ct;
+            o.warps_per_tile = wpt;
             o.use_graph = 0;
             vr_status st = vr_render_batched(jobs, n, &o, cuda_stream);      // warm-up (builds the plan)
             if (st != VR_OK) { result = st; goto done; }
@@ -457,6 +497,7 @@ extern "C" vr_status vr_autotune_batched(const vr_job *jobs, int n, vr_batch_opt
                 best_ms = ms;
                 win = o;
             }
+          }
         }
     }
     win.use_graph = best->use_graph;
@@ -548,10 +589,10 @@ extern "C" vr_status vr_render_batched_noalloc(const vr_job *jobs, int n, int ti
     Segment seg[kGroups];
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
     // only brick copies that exist already are used (building one allocates)
-    vr_status st = prepare_jobs(jobs, n, tile_w, false, s, hj, group_of, order, cost, seg,
+    vr_status st = prepare_jobs(jobs, n, tile_w, 1, false, s, hj, group_of, order, cost, seg,
                                   "vr_render_batched_noalloc");
     if (st != VR_OK) return st;
-    size_grids(seg, 0);
+    size_grids(seg, 0, 1);
     NoAllocScratch *scratch = noalloc_scratch_ptr(st);
     if (!scratch) return st;
     // The counters must start at zero; the descriptors overwrite the last call's.

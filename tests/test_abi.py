@@ -146,6 +146,14 @@ def test_batched_validation(L):
         L.vr_render_batched([job], L.vr_batch_opts(0, 5, 6, 0))
     with pytest.raises(L.VRError, match=r"jobs\[0\]"):
         L.vr_render_batched([job], L.vr_batch_opts(0, 8, 4, 0))
+    for wpt in (3, 8, -1):
+        with pytest.raises(L.VRError, match="warps_per_tile"):
+            L.vr_render_batched([job], L.vr_batch_opts(0, 8, 4, 0, wpt))
+
+
+def test_rebrick_validation(L):
+    with pytest.raises(L.VRError, match="volume handle is NULL"):
+        L.vr_volume_rebrick(None, 32)
 
 
 def test_product_path_has_no_cpu_fallback(L):

@@ -112,3 +112,77 @@ def test_autotune_cache_round_trip(P, torch, tmp_path):
         img, ns = P.render(j["vol"], j["cam"], j["tf"], j["vmin"], j["vmax"], j["step"], j["ert"])
         assert torch.equal(j["out"], img) and torch.equal(j["nsamples"], ns)
         j["vol"].close()
+
+
+@pytest.mark.parametrize("store", ["f32", "f16"])
+@pytest.mark.parametrize("wpt,tile", [(2, (8, 4)), (4, (8, 4)), (2, (16, 2)), (4, (32, 1))])
+def test_warps_sharing_a_tile_equal_single_renders(P, torch, store, wpt, tile):
+    """Two or four warps of a CTA take one tile together (each its own part,
+    handed over at a named barrier of the group): the images equal the single
+    renders bit for bit, with the graph replayed."""
+    from paper_1211_4896_gb300 import _lib as L
+    jobs, _ = _jobs(torch, P, n=5, store=store)
+    opts = L.vr_batch_opts(1, tile[0], tile[1], 0, wpt)
+    for _ in range(2):
+        for j in jobs:
+            j["out"].fill_(-1.0)
+            j["nsamples"].fill_(-1)
+        P.render_batched(jobs, opts=opts)
+        torch.cuda.synchronize()
+        for j in jobs:
+            img, ns = P.render(j["vol"], j["cam"], j["tf"], j["vmin"], j["vmax"], j["step"], j["ert"])
+            torch.cuda.synchronize()
+            assert torch.equal(j["out"], img) and torch.equal(j["nsamples"], ns)
+    with pytest.raises(P.VRError):
+        P.render_batched(jobs, opts=L.vr_batch_opts(0, 8, 4, 0, 3))
+    for j in jobs:
+        j["vol"].close()
+
+
+@pytest.mark.parametrize("store", ["f32", "f16"])
+def test_rebrick_renders_like_the_source(P, torch, store):
+    """vr_volume_rebrick builds bricks of another size from a volume's bricks:
+    renders from 32^3 and 64^3 bricks (and back to 16^3) equal the source's
+    and those of a volume created with that size from the dense cube."""
+    jobs, cubes = _jobs(torch, P, n=3, store=store)
+    for j, cube in zip(jobs, cubes):
+        ref, ref_ns = P.render(j["vol"], j["cam"], j["tf"], j["vmin"], j["vmax"], j["step"], j["ert"])
+        for b in (32, 64):
+            rb = j["vol"].rebrick(b)
+            direct = P.Volume(cube.cuda(), store, brick=b)
+            back = rb.rebrick(16)
+            assert rb.info["brick"] == b and rb.info["dims"] == j["vol"].info["dims"]
+            for v in (rb, direct, back):
+                img, ns = P.render(v, j["cam"], j["tf"], j["vmin"], j["vmax"], j["step"], j["ert"])
+                torch.cuda.synchronize()
+                assert torch.equal(img, ref) and torch.equal(ns, ref_ns)
+            for v in (rb, direct, back):
+                v.close()
+        with pytest.raises(P.VRError):
+            j["vol"].rebrick(8)
+        j["vol"].close()
+
+
+def test_autotune_over_brick_sizes(P, torch, tmp_path):
+    """The autotuner over brick sizes returns options, a brick size and the
+    job list on volumes of that size; rendering with them equals the single
+    renders; the cache entries record brick size and warps per tile."""
+    import json
+    jobs, _ = _jobs(torch, P, n=4, store="f16")
+    path = str(tmp_path / "tune.json")
+    opts, brick, tuned = P.autotune_batched_bricks(jobs, brick_sizes=(16, 32), cache_path=path)
+    assert brick in (16, 32) and opts.warps_per_tile in (1, 2, 4) and opts.tile_w * opts.tile_h == 32
+    assert all(int(j["vol"].info["brick"]) == brick for j in tuned)
+    table = json.load(open(path))
+    assert len(table) == 2 and {e["brick"] for e in table.values()} == {16, 32}
+    assert all("warps_per_tile" in e for e in table.values())
+    P.render_batched(tuned, opts=opts)
+    torch.cuda.synchronize()
+    for j in tuned:
+        img, ns = P.render(j["vol"], j["cam"], j["tf"], j["vmin"], j["vmax"], j["step"], j["ert"])
+        torch.cuda.synchronize()
+        assert torch.equal(j["out"], img) and torch.equal(j["nsamples"], ns)
+    for j in jobs:
+        for v in j["vol"].__dict__.get("_rebricked", {}).values():
+            v.close()
+        j["vol"].close()
