@@ -173,6 +173,145 @@ CLOCKS = ClockLog()
 
 
 # ---------------------------------------------------------------------------
+# Ceilings of a workload (measurement only; none of this is on the render path)
+# ---------------------------------------------------------------------------
+
+def footprint_voxels(torch, dims, cam, step, nsamples, max_bitmap_bytes=2 << 30):
+    """Distinct voxels touched by the trilinear footprints of one view's
+    composited samples (the view's compulsory voxel set).  Each pixel's ray
+    is re-derived in float64 with the renderer's camera conventions (basis
+    f, r = f x up, u = r x f; pixel centres; slab clip to the closed box
+    [0, n-1]; perspective rays from the eye), its first nsamples[j, i]
+    samples are placed at t_in + (k + 1/2) step, their cells (clamped corner
+    floor(p)) are marked in a bitmap and the bitmap is dilated by one voxel
+    towards +x, +y and +z (a cell's eight corners).  Unit spacing, origin 0.
+    Large grids are counted in slabs of cells along z."""
+    dev = nsamples.device
+    f64 = torch.float64
+    nx, ny, nz = (int(d) for d in dims)
+    H, W = int(cam["height"]), int(cam["width"])
+    f = torch.tensor(cam["forward"], dtype=f64, device=dev)
+    f = f / f.norm()
+    up = torch.tensor(cam["up"], dtype=f64, device=dev)
+    r = torch.linalg.cross(f, up)
+    r = r / r.norm()
+    u = torch.linalg.cross(r, f)
+    jj, ii = torch.meshgrid(torch.arange(H, device=dev, dtype=f64), torch.arange(W, device=dev, dtype=f64),
+                            indexing="ij")
+    sx = ((ii + 0.5) / W) * 2.0 - 1.0
+    sy = 1.0 - ((jj + 0.5) / H) * 2.0
+    aspect = W / H
+    eye = torch.tensor(cam["eye"], dtype=f64, device=dev)
+    if cam["kind"] == 0:
+        hh = 0.5 * cam["ortho_height"]
+        o = eye + (sx * hh * aspect)[..., None] * r + (sy * hh)[..., None] * u
+        d = f.expand(H, W, 3)
+        t0 = torch.full((H, W), -math.inf, dtype=f64, device=dev)
+    else:
+        th = math.tan(math.radians(cam["fov_y_deg"]) / 2.0)
+        d = f + (sx * th * aspect)[..., None] * r + (sy * th)[..., None] * u
+        d = d / d.norm(dim=-1, keepdim=True)
+        o = eye.expand(H, W, 3)
+        t0 = torch.zeros((H, W), dtype=f64, device=dev)
+    t1 = torch.full((H, W), math.inf, dtype=f64, device=dev)
+    hi = torch.tensor([nx - 1, ny - 1, nz - 1], dtype=f64, device=dev)
+    with torch.no_grad():
+        for a in range(3):
+            da = d[..., a]
+            inv = 1.0 / da
+            ta, tb = (0.0 - o[..., a]) * inv, (hi[a] - o[..., a]) * inv
+            t0 = torch.where(da != 0, torch.maximum(t0, torch.minimum(ta, tb)), t0)
+            t1 = torch.where(da != 0, torch.minimum(t1, torch.maximum(ta, tb)), t1)
+        n = nsamples.to(torch.int64).reshape(-1)
+        order = torch.argsort(n, descending=True)
+        n = n[order]
+        o = o.reshape(-1, 3)[order]
+        d = d.reshape(-1, 3)[order]
+        t0 = t0.reshape(-1)[order]
+        ncx, ncy, ncz = nx - 1, ny - 1, nz - 1
+        slab = max(1, min(ncz, max_bitmap_bytes // max(1, ncx * ncy)))
+        total = 0
+        carry = None
+        for z_lo in range(0, ncz, slab):
+            z_hi = min(ncz, z_lo + slab)
+            cells = torch.zeros((z_hi - z_lo) * ncy * ncx, dtype=torch.bool, device=dev)
+            live = int((n > 0).sum())
+            k = 0
+            while live > 0:
+                t = t0[:live] + (k + 0.5) * step
+                p = o[:live] + t[:, None] * d[:live]
+                c = torch.floor(p).to(torch.int64)
+                cx = c[:, 0].clamp(0, ncx - 1)
+                cy = c[:, 1].clamp(0, ncy - 1)
+                cz = c[:, 2].clamp(0, ncz - 1)
+                m = (cz >= z_lo) & (cz < z_hi)
+                cells[((cz[m] - z_lo) * ncy + cy[m]) * ncx + cx[m]] = True
+                k += 1
+                while live > 0 and int(n[live - 1]) <= k:
+                    live -= 1
+            cells = cells.view(z_hi - z_lo, ncy, ncx)
+            # voxel layers [z_lo, z_hi] touched by this slab's cells; layer z_lo
+            # also takes the previous slab's top layer, layer z_hi is carried
+            # to the next slab (the last slab counts it)
+            vox = torch.zeros((z_hi - z_lo + 1, ny, nx), dtype=torch.bool, device=dev)
+            for dz in (0, 1):
+                for dy in (0, 1):
+                    for dx in (0, 1):
+                        vox[dz:dz + z_hi - z_lo, dy:dy + ncy, dx:dx + ncx] |= cells
+            if carry is not None:
+                vox[0] |= carry
+            if z_hi < ncz:
+                total += int(vox[:-1].sum())
+                carry = vox[-1].clone()
+            else:
+                total += int(vox.sum())
+            del cells, vox
+        return total
+
+
+def issue_per_sample(kernel: str):
+    """Warp instructions issued per composited sample for `kernel`, measured
+    with ncu on the small profile cases (profiles/issue_per_sample.json; the
+    case of each figure is recorded there), or None."""
+    p = os.path.join(ROOT, "profiles", "issue_per_sample.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        rec = json.load(f)
+    if rec.get("sources_sha256") != kernel_sources_sha256():
+        return None
+    v = rec.get("warp_inst_per_sample", {}).get(kernel)
+    return None if v is None else float(v)
+
+
+def ceilings(samples, seconds, bytes_per_voxel, b_alg, kernel, sm_mhz):
+    """The three rates that bound a pass of the march (samples per second),
+    the one that binds, and where the achieved rate stands:
+      gather      BW / (8 s): every sample's eight corners from HBM, no reuse;
+      compulsory  samples BW / B_alg: each voxel any footprint touches read
+                  from HBM once (B_alg = s x touched voxels);
+      issue       SMs x 4 warp instructions per clock / instructions per
+                  sample (measured on the profile case of this kernel)."""
+    bw = measured_peaks()[0] * 1e9
+    import torch
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    out = {"gather_gs": bw / (8 * bytes_per_voxel) / 1e9}
+    if b_alg:
+        out["compulsory_gs"] = samples * bw / b_alg / 1e9
+        out["b_alg_bytes"] = b_alg
+        out["b_alg_per_sample"] = b_alg / samples
+    ips = issue_per_sample(kernel)
+    if ips and sm_mhz:
+        out["issue_gs"] = sms * 4 * sm_mhz * 1e6 / ips / 1e9
+        out["warp_inst_per_sample"] = ips
+    rates = {k[:-3]: v for k, v in out.items() if k.endswith("_gs")}
+    out["binding"] = min(rates, key=rates.get)
+    out["achieved_gs"] = samples / seconds / 1e9
+    out["achieved_frac_of_binding"] = out["achieved_gs"] / rates[out["binding"]]
+    return out
+
+
+# ---------------------------------------------------------------------------
 # Reference arm: the FP64 oracle on the host cores
 # ---------------------------------------------------------------------------
 
@@ -450,6 +589,14 @@ def run_ours(args, rank, world, local_rank):
     roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": achieved / peak, "traffic": traffic, "peak_source": peak_kind,
             "per_unit": "8 x 4 B trilinear gathers per composited sample"}
+    # the compulsory voxel set of every view (measurement only, after the timed region)
+    b_alg = 4 * sum(footprint_voxels(torch, vol.shape[::-1], c, step, n) for c, n in zip(cams, nss)) if rank == 0 \
+        else None
+    sm_mhz = clk["sm_mhz"] if clk else None
+    ceil = {"fwd_batched": ceilings(samples_per_step, fwd_only_ms * 1e-3, 4, b_alg, "batched_kernel<float>", sm_mhz),
+            "bwd": ceilings(samples_per_step, bwd_ms * nv * 1e-3, 4, b_alg, "bwd_kernel<float>", sm_mhz)}
+    if traffic and b_alg:
+        roof["waste_ratio"] = traffic * nv / b_alg      # DRAM bytes of the kernel / compulsory bytes
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
@@ -467,7 +614,7 @@ def run_ours(args, rank, world, local_rank):
                     "plain_fp32_single_view_gsamples_per_s": samples_per_step / (plain_ms * 1e-3) / 1e9,
                     "plain_fp32_view_ms_p75": p75, "fps_p75": 1e3 / p75},
             "bwd": {"ms_per_view": bwd_ms, "bwd_over_fwd": bwd_total / fwd_ms},
-            "px_err": px, "roofline": roof, "cpu_baseline": cpu,
+            "px_err": px, "roofline": roof, "ceilings": ceil, "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": args.steps * (groups + 2 * nv), "clocks": clk}
     if rank == 0:
@@ -570,9 +717,13 @@ def run_plain_128(args):
     ref = oracle.render(cube.numpy(), cam, tf_np, synth.TF_VMIN, synth.TF_VMAX, pre["step"], pre["ert"])
     t_cpu = time.perf_counter() - t0
     err = _px_err(out.cpu().numpy(), ns.cpu().numpy(), ref, range(256))
-    _emit({"workload": "plain_128", "gsamples_per_s": samples / ms / 1e6, "ms": ms, "samples": samples,
-                      "roofline_frac": gather_rate_frac(samples / ms / 1e6, 4),
-                      "px_err": err, "oracle_gsamples_per_s": samples / t_cpu / 1e9, "oracle_cores": os.cpu_count()})
+    line = {"workload": "plain_128", "gsamples_per_s": samples / ms / 1e6, "ms": ms, "samples": samples,
+            "roofline_frac": gather_rate_frac(samples / ms / 1e6, 4),
+            "px_err": err, "oracle_gsamples_per_s": samples / t_cpu / 1e9, "oracle_cores": os.cpu_count()}
+    b_alg = 4 * footprint_voxels(torch, pre["dims"], cam, pre["step"], ns)
+    clk = dict(CLOCKS.raw and ClockSampler.summarize(CLOCKS.raw) or {})
+    line["ceilings"] = ceilings(samples, ms * 1e-3, 4, b_alg, "fwd_kernel<float>@plain_128", clk.get("sm_mhz"))
+    _emit(line)
 
 
 def run_precision_4096(args):
@@ -604,6 +755,8 @@ def run_precision_4096(args):
                 r.setdefault(k, np.zeros_like(v))[row] = v[row]
         refs.append(r)
     base = None
+    b_alg_vox = None
+    from paper_1211_4896_gb300 import _lib as L
     for store in ("f32", "f16", "bf16"):
         vol = P.Volume(cube, store)
         outs = [torch.empty((1080, 1920, 4), device=dev) for _ in cams]
@@ -614,7 +767,13 @@ def run_precision_4096(args):
                 P.render(vol, c, tf, synth.TF_VMIN, synth.TF_VMAX, 1.0, 0.99, out=o, nsamples=n)
         ms = _time_ms(torch, f, 3)
         samples = sum(int(n.sum()) for n in nss)
+        layouts = [L.vr_view_layout(vol.handle, L.make_camera(c)) for c in cams]
         vol.close()
+        torch.cuda.empty_cache()
+        if b_alg_vox is None:       # the same samples for every storage type
+            b_alg_vox = sum(footprint_voxels(torch, dims, c, 1.0, n, max_bitmap_bytes=24 << 30)
+                            for c, n in zip(cams, nss))
+            torch.cuda.empty_cache()
         cvol = P.Volume(crop, store)
         errs = []
         for cam, ref in zip(crop_cams, refs):
@@ -624,8 +783,12 @@ def run_precision_4096(args):
         cvol.close()
         gs = samples / ms / 1e6
         base = base or gs
+        eb = 4 if store == "f32" else 2
+        kern = "fwd_kernel<float>@sparse" if store == "f32" else "fwd_kernel<Blocked<16-bit>>@sparse"
+        clk = ClockSampler.summarize(CLOCKS.raw) or {}
         res[store] = {"gsamples_per_s": gs, "ms_4_views": ms, "fps": 4e3 / ms, "vs_f32": gs / base,
-                      "roofline_frac": gather_rate_frac(gs, 4 if store == "f32" else 2),
+                      "roofline_frac": gather_rate_frac(gs, eb), "layouts": layouts,
+                      "ceilings": ceilings(samples, ms * 1e-3, eb, eb * b_alg_vox, kern, clk.get("sm_mhz")),
                       "bricked_gb": vol.info["bytes"] / 1e9,
                       "crop_px_err": _merge_px(errs, "FP64 oracle on the float32 256^3 crop, rows %s of its 4 "
                                                      "views" % rows)}
@@ -657,10 +820,10 @@ def run_batch_64(args):
                          nsamples=torch.empty((H, W), device=dev, dtype=torch.int32)))
     torch.cuda.empty_cache()
     s = int(torch.cuda.current_stream().cuda_stream)
-    cj = P.render_batched(jobs, use_graph=False)
-    best = L.vr_autotune_batched(cj, L.vr_batch_opts(1, 0, 0, 0), s)
-    opts = L.vr_batch_opts(1, best.tile_w, best.tile_h, best.ctas_per_sm)
-    L.vr_render_batched(cj, opts, s)
+    # the autotuner: brick size (volumes re-bricked on the device), tile shape,
+    # CTAs per SM and warps per tile
+    opts, brick, tuned = P.autotune_batched_bricks(jobs, brick_sizes=(16, 32, 64))
+    cj = P.render_batched(tuned, opts=opts)
     t_graph = _time_ms(torch, lambda: L.vr_render_batched(cj, opts, s), max(5, args.steps))
     ccams = [(j["vol"].handle, L.make_camera(j["cam"]),
               L.make_params(j["tf"].data_ptr(), 256, -3.0, 50.0, 1.0, 0.99), j["out"].data_ptr(),
@@ -675,8 +838,11 @@ def run_batch_64(args):
                       "graph_ms": t_graph, "separate_ms": t_sep, "speedup": t_sep / t_graph,
                       "graph_gsamples_per_s": samples / t_graph / 1e6, "separate_gsamples_per_s": samples / t_sep / 1e6,
                       "graph_roofline_frac": gather_rate_frac(samples / t_graph / 1e6, 2),
-                      "autotuned": {"tile": [best.tile_w, best.tile_h], "ctas_per_sm": best.ctas_per_sm}})
+                      "autotuned": {"brick": brick, "tile": [opts.tile_w, opts.tile_h], "ctas_per_sm": opts.ctas_per_sm,
+                                    "warps_per_tile": opts.warps_per_tile}})
     for j in jobs:
+        for v in j["vol"].__dict__.get("_rebricked", {}).values():
+            v.close()
         j["vol"].close()
 
 
