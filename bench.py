@@ -23,6 +23,7 @@ import argparse
 import json
 import math
 import os
+import platform
 import statistics
 import subprocess
 import sys
@@ -438,18 +439,19 @@ def run_ours(args, rank, world, local_rank):
     cjobs = P.render_batched(jobs, use_graph=True)          # builds the plan + graph
     opts = L.vr_batch_opts(1, 8, 4, 0)
     ccams = [L.make_camera(c) for c in cams]
-    # the batched call launches one kernel per brick layout its views read;
-    # each backward view launches the kernel and its FP64 row sum
+    # the batched call launches one kernel per brick layout its views read; the
+    # multi-view backward one kernel per view and one FP64 row sum
     groups = len({L.vr_view_layout(vol.handle, cc) for cc in ccams})
+    gviews = [L.vr_grad_view(cc, o.data_ptr(), n.data_ptr(), g.data_ptr())
+              for cc, o, n, g in zip(ccams, outs, nss, grads)]
     cpar = L.make_params(tf.data_ptr(), 256, vmin, vmax, step, ert)
     ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
 
     def fwd():
         L.vr_render_batched(cjobs, opts, s_ptr)
 
-    def bwd(v, acc):
-        L.vr_render_backward(vol.handle, ccams[v], cpar, outs[v].data_ptr(), nss[v].data_ptr(), grads[v].data_ptr(),
-                             grad_tf.data_ptr(), grad_vox.data_ptr(), L.VR_GRAD_ACCUMULATE if acc else 0, s_ptr)
+    def bwd():              # the loss summed over the 8 views: one multi-view call
+        L.vr_render_backward_views(vol.handle, gviews, cpar, grad_tf.data_ptr(), grad_vox.data_ptr(), 0, s_ptr)
 
     fwd_ev, bwd_ev = [], []
 
@@ -461,14 +463,13 @@ def run_ours(args, rank, world, local_rank):
         if record:
             e1.record(stream)
             fwd_ev.append((e0, e1))
-        for v in range(nv):
-            if record:
-                b0, b1 = ev(), ev()
-                b0.record(stream)
-            bwd(v, v > 0)
-            if record:
-                b1.record(stream)
-                bwd_ev.append((b0, b1))
+        if record:
+            b0, b1 = ev(), ev()
+            b0.record(stream)
+        bwd()
+        if record:
+            b1.record(stream)
+            bwd_ev.append((b0, b1))
 
     def barrier():
         torch.cuda.synchronize()
@@ -493,7 +494,7 @@ def run_ours(args, rank, world, local_rank):
     clk = clocks.stop()
     ms = t_start.elapsed_time(t_end) / args.steps
     fwd_ms = statistics.mean(a.elapsed_time(b) for a, b in fwd_ev)
-    bwd_ms = statistics.mean(a.elapsed_time(b) for a, b in bwd_ev)           # per view
+    bwd_ms = statistics.mean(a.elapsed_time(b) for a, b in bwd_ev)           # the 8 views
     ms_max, samples_all = reduce_over_ranks(ms, samples_per_step, dev)
     value = samples_all / (ms_max * 1e-3) / 1e9
 
@@ -533,8 +534,7 @@ def run_ours(args, rank, world, local_rank):
         for g, pg in zip(grads, pin_g):
             g.copy_(pg, non_blocking=True)
         fwd()
-        for v in range(nv):
-            bwd(v, v > 0)
+        bwd()
         for o, po in zip(outs, pin_out):
             po.copy_(o, non_blocking=True)
         pin_gtf.copy_(grad_tf, non_blocking=True)
@@ -578,10 +578,9 @@ def run_ours(args, rank, world, local_rank):
 
     # ---- roofline of the dominant kernel ---------------------------------------------
     peak, peak_kind = measured_peaks()
-    bwd_total = bwd_ms * nv
-    if bwd_total >= fwd_ms:
-        dom, dom_key, dom_ms, per = ("bwd_kernel (one view; timed with its scratch clear and FP64 row sum)",
-                                     "bwd_kernel", bwd_ms, samples_per_step / nv)
+    if bwd_ms >= fwd_ms:
+        dom, dom_key, dom_ms, per = ("bwd_kernel (one multi-view call: 8 launches over two streams; timed with "
+                                     "its scratch clear and FP64 row sum)", "bwd_kernel", bwd_ms, samples_per_step)
     else:
         dom, dom_key, dom_ms, per = "batched_kernel (8 views, one launch)", "batched_kernel", fwd_ms, samples_per_step
     achieved = per * GATHER_BYTES_F32 / (dom_ms * 1e-3) / 1e9
@@ -594,9 +593,9 @@ def run_ours(args, rank, world, local_rank):
         else None
     sm_mhz = clk["sm_mhz"] if clk else None
     ceil = {"fwd_batched": ceilings(samples_per_step, fwd_only_ms * 1e-3, 4, b_alg, "batched_kernel<float>", sm_mhz),
-            "bwd": ceilings(samples_per_step, bwd_ms * nv * 1e-3, 4, b_alg, "bwd_kernel<float>", sm_mhz)}
+            "bwd": ceilings(samples_per_step, bwd_ms * 1e-3, 4, b_alg, "bwd_kernel<float>", sm_mhz)}
     if traffic and b_alg:
-        roof["waste_ratio"] = traffic * nv / b_alg      # DRAM bytes of the kernel / compulsory bytes
+        roof["waste_ratio"] = traffic / b_alg      # DRAM bytes of the kernel's launches / compulsory bytes
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
@@ -604,7 +603,7 @@ def run_ours(args, rank, world, local_rank):
             "config": {"workload": "scale_1024: 1024^3 f32 HI-like cube (noise + 2000 blobs + 200 disks), "
                                    "8 perspective orbit views at 1920x1080, step 1 voxel, ERT 0.99; "
                                    "fwd = one batched graph launch of the 8 views, bwd = table + voxel "
-                                   "gradients per view (accumulated)",
+                                   "gradients of the loss summed over the 8 views (one multi-view call)",
                        "views": nv, "image": [W, H], "samples_per_step": samples_per_step,
                        "l2": "inputs larger than L2 (bricked cube %.2f GB)" % (vol.info["bytes"] / 1e9),
                        "parallelism": "views replicated per GPU" if world > 1 else "1 GPU"},
@@ -613,10 +612,10 @@ def run_ours(args, rank, world, local_rank):
                     "batched_ms_8_views": fwd_only_ms,
                     "plain_fp32_single_view_gsamples_per_s": samples_per_step / (plain_ms * 1e-3) / 1e9,
                     "plain_fp32_view_ms_p75": p75, "fps_p75": 1e3 / p75},
-            "bwd": {"ms_per_view": bwd_ms, "bwd_over_fwd": bwd_total / fwd_ms},
+            "bwd": {"ms_8_views": bwd_ms, "bwd_over_fwd": bwd_ms / fwd_ms},
             "px_err": px, "roofline": roof, "ceilings": ceil, "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-            "gpu_launches": args.steps * (groups + 2 * nv), "clocks": clk}
+            "gpu_launches": args.steps * (groups + nv + 1), "clocks": clk}
     if rank == 0:
         print(json.dumps(line))
     vol.close()
@@ -1164,10 +1163,109 @@ def run_tex_1024(args):
     vol.close()
 
 
+def _oracle_rate(fn, cores, min_s=1.0):
+    """Composited samples per second of fn(nthreads) -> samples, repeated
+    until min_s seconds have passed (one call at least)."""
+    t0 = time.perf_counter()
+    samples, calls = 0, 0
+    while True:
+        samples += fn(cores)
+        calls += 1
+        t = time.perf_counter() - t0
+        if t >= min_s:
+            break
+    return {"cores": cores, "calls": calls, "seconds": t, "samples": samples, "gsamples_per_s": samples / t / 1e9}
+
+
+def run_cpu_oracle(args):
+    """The FP64 oracle timed on the host cores, with every core and with one,
+    on the paper-scale workloads (CPU only; the cubes are generated on the GPU
+    when there is one, outside the timed calls):
+      plain_128   the whole 256^2 render of the 128^3 cube (forward);
+      scale_1024  one full 1080p view (view 0) of the 1024^3 cube, forward +
+                  backward (table gradient), as in the headline's cpu_baseline;
+      precision   one full 1080p view of the 256^3 crop of the 4096^2 x 1024
+                  cube that the precision workload checks pixels on (forward);
+      diff_crop   the 32^3 crop (around the brightest voxel) of the 512^3
+                  differentiation cube, its four 64^2 views: forward + backward
+                  with table and voxel gradients."""
+    import torch
+    import oracle
+    dev = torch.device("cuda") if torch.cuda.is_available() else torch.device("cpu")
+    ncores = os.cpu_count() or 1
+    tf_np = synth.tf_ramp(256)
+    vmin, vmax = synth.TF_VMIN, synth.TF_VMAX
+    out = {"workload": "cpu_oracle", "host_cores": ncores, "machine": platform.machine(), "rows": {}}
+
+    def both(name, fn, desc, min_s):
+        out["rows"][name] = {"what": desc, "all_cores": _oracle_rate(fn, ncores, min_s),
+                             "one_core": _oracle_rate(fn, 1, min_s)}
+        print("cpu_oracle: %s done" % name, file=sys.stderr)
+
+    # plain_128
+    pre = synth.preset_plain_128()
+    host = synth.hi_cube(pre["dims"], pre["n_blobs"], pre["n_disks"], pre["seed"]).numpy()
+    cam = pre["cameras"][0]
+    both("plain_128", lambda nt: int(oracle.render(host, cam, tf_np, vmin, vmax, pre["step"], pre["ert"],
+                                                   nthreads=nt)["n_used"].sum()),
+         "128^3 f32, orthographic 256^2 along +z, step 0.5, no ERT; whole image, forward", 2.0)
+    # scale_1024, one full view
+    pre = synth.preset_scale_1024()
+    host = make_cube(pre, dev).cpu().numpy()
+    torch.cuda.empty_cache() if dev.type == "cuda" else None
+    cam = pre["cameras"][0]
+    g = np.random.default_rng(0).normal(size=(cam["height"], cam["width"], 4))
+
+    def c2(nt):
+        o = oracle.render(host, cam, tf_np, vmin, vmax, pre["step"], pre["ert"], nthreads=nt)
+        oracle.render_backward(host, cam, tf_np, vmin, vmax, pre["step"], g, ert=pre["ert"], want_vox=False,
+                               nthreads=nt)
+        return int(o["n_used"].sum())
+    both("scale_1024", c2, "1024^3 f32, view 0 of the 8 orbit views (1920x1080), step 1, ERT 0.99; forward + "
+                           "backward (table gradient)", 0.0)
+    del host
+    # precision crop
+    dims = (4096, 4096, 1024)
+    nb = int(round(20 * (4096 * 4096 * 1024) / 128 ** 3))
+    nd = int(round(200 * (4096 * 4096 * 1024) / 1024 ** 3))
+    cube = synth.hi_cube(dims, nb, nd, seed=3, device=dev)
+    crop = cube[384:640, 1920:2176, 1920:2176].contiguous().cpu().numpy()
+    del cube
+    torch.cuda.empty_cache() if dev.type == "cuda" else None
+    cam = synth.orbit_cameras((256, 256, 256), 4, 40.0, 1920, 1080, start_deg=30.0)[0]
+    both("precision_crop", lambda nt: int(oracle.render(crop, cam, tf_np, vmin, vmax, 1.0, 0.99,
+                                                        nthreads=nt)["n_used"].sum()),
+         "the 256^3 f32 crop of the 4096^2 x 1024 cube, its first 1920x1080 orbit view, step 1, ERT 0.99; forward",
+         0.0)
+    # differentiation crop
+    pre = synth.preset_diff_512()
+    cube = synth.hi_cube(pre["dims"], pre["n_blobs"], pre["n_disks"], pre["seed"], device=dev)
+    n = 32
+    centre = np.unravel_index(int(torch.argmax(cube).item()), cube.shape)
+    lo = [int(min(max(c - n // 2, 0), d - n)) for c, d in zip(centre, cube.shape)]
+    crop = cube[lo[0]:lo[0] + n, lo[1]:lo[1] + n, lo[2]:lo[2] + n].contiguous().cpu().numpy()
+    del cube
+    cams = synth.orbit_cameras((n, n, n), 4, 40.0, 64, 64, start_deg=20.0)
+    gr = [np.random.default_rng(10 + q).normal(size=(64, 64, 4)) for q in range(4)]
+
+    def c5(nt):
+        s = 0
+        for c, gq in zip(cams, gr):
+            s += int(oracle.render(crop, c, tf_np, vmin, vmax, pre["step"], 2.0, nthreads=nt)["n_used"].sum())
+            oracle.render_backward(crop, c, tf_np, vmin, vmax, pre["step"], gq, nthreads=nt)
+        return s
+    both("diff_crop", c5, "32^3 f32 crop of the 512^3 differentiation cube, four 64^2 orbit views, step 0.5, "
+                          "no ERT; forward + backward (table and voxel gradients)", 2.0)
+    out["note"] = ("FP64 oracle (oracle/vr_oracle.c) as it stands, pixels dealt round-robin to pthreads; one_core = one "
+                   "thread; each figure repeats its call until at least the given time has passed")
+    print(json.dumps(out))
+
+
 WORKLOADS = {"plain_128": run_plain_128, "precision_4096": run_precision_4096, "batch_64": run_batch_64,
              "diff_512": run_diff_512, "mip_1024": lambda a: run_modes_1024(a, "mip"),
              "sigma_1024": lambda a: run_modes_1024(a, "sigma"), "stats_1024": run_stats_1024,
-             "sortlast_1024": run_sortlast_1024, "skip_1024": run_skip_1024, "tex_1024": run_tex_1024}
+             "sortlast_1024": run_sortlast_1024, "skip_1024": run_skip_1024, "tex_1024": run_tex_1024,
+             "cpu_oracle": run_cpu_oracle}
 
 
 def main():

@@ -281,8 +281,11 @@ vr_status vr_render_backward(vr_volume_t vol, const vr_camera *cam, const vr_par
  * renderings), equal to n vr_render_backward calls with VR_GRAD_ACCUMULATE
  * after the first.  One call clears the outputs (unless VR_GRAD_ACCUMULATE),
  * launches one backward kernel per view into the same per-warp table rows
- * and voxel gradient, then runs the FP64 row sum and, with the quad scratch,
- * its gather once for all views; the scratch is chosen where the views
+ * and voxel gradient, alternating between two streams of the volume's own
+ * (forked from and joined back to cuda_stream, created on first use) so that
+ * a view's kernel starts on the CTA slots the previous view's last tiles
+ * leave free; then it runs the FP64 row sum and, with the quad scratch, its
+ * gather once for all views; the scratch is chosen where the views
  * put at least one sample per voxel on average, with one quad orientation
  * (the carry axis most views share).  views is a host array of n (1..4096) entries; each view's
  * image, sample counts and dL/d(image) follow the rules of

@@ -566,6 +566,10 @@ static void free_volume(vr_volume *vol)
     for (void *o : vol->copies)
         if (o) cudaFree(o);
     if (vol->counters) cudaFree(vol->counters);
+    for (cudaStream_t a : vol->aux)
+        if (a) cudaStreamDestroy(a);
+    for (cudaEvent_t ev : vol->aux_ev)
+        if (ev) cudaEventDestroy(ev);
     delete vol;
 }
 

@@ -311,8 +311,9 @@ __global__ void __launch_bounds__(kBwdThreads) bwd_kernel(VolDev v, CamDev c, Pa
             if (bins_ok && (aT != 0.0f || da != 0.0f)) {
                 if (aT != 0.0f || !win.add(tp.i0, 1.0f - tp.w, tp.w, da))
                     bins.add(row, tp.i0, 1.0f - tp.w, tp.w, aT, da, g);
-                if (gd.vox && tp.interior) {
-                    // dr . de with dr = (aT g.rgb, da)
+                if (gd.vox && tp.interior && (aT != 0.0f || de.w != 0.0f)) {
+                    // dr . de with dr = (aT g.rgb, da); zero for a transparent sample
+                    // between two zero-opacity entries
                     const float dv = fmaf(aT, de.x * g.x + de.y * g.y + de.z * g.z, da * de.w) * vscale;
                     if (dv != 0.0f) {
                         const float fu = gd.axis == 0 ? cell.fy : cell.fx;
@@ -426,9 +427,58 @@ static cudaError_t view_kernel(const BwdView &bv, vr_dtype dt, const void **fn_o
         cudaErrorInvalidValue);
 }
 
+// The two streams and three events with which a backward of several views
+// overlaps each view's last tiles with the next view's first, created on
+// first use (on the volume's device) and kept with the volume.
+static cudaError_t ensure_aux_streams(vr_volume *vol)
+{
+    for (cudaStream_t &a : vol->aux)
+        if (!a) {
+            cudaError_t e = cudaStreamCreateWithFlags(&a, cudaStreamNonBlocking);
+            if (e != cudaSuccess) {
+                a = nullptr;
+                return e;
+            }
+        }
+    for (cudaEvent_t &ev : vol->aux_ev)
+        if (!ev) {
+            cudaError_t e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+            if (e != cudaSuccess) {
+                ev = nullptr;
+                return e;
+            }
+        }
+    return cudaSuccess;
+}
+
+// One view's backward kernel on stream s (its work counter cleared first).
+static cudaError_t launch_view(const BwdView &bv, vr_dtype dt, const ParamDev &p, float4 *wtab, const GradDev &gd,
+                               unsigned *counter, cudaStream_t s)
+{
+    const int tiles_x = (bv.c.W + 7) / 8;
+    const unsigned ntiles = (unsigned)tiles_x * (unsigned)((bv.c.H + 3) / 4);
+    cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(unsigned), s);
+    if (e != cudaSuccess) return e;
+    return visit_layout(
+        bv.v, dt,
+        [&](auto lay) {
+            using Y = decltype(lay);
+            auto fn = bwd_kernel<typename Y::type, Y::log2b, Y::order>;
+            fn<<<view_grid((const void *)fn, bv.c), kBwdThreads, 0, s>>>(bv.v, bv.c, p, bv.rgba, bv.nsamples,
+                                                                        bv.grad_rgba, wtab, gd, counter, tiles_x,
+                                                                        ntiles);
+            return cudaGetLastError();
+        },
+        cudaErrorInvalidValue);
+}
+
 // The backward of a loss summed over n views: every view's kernel adds into
-// the same per-warp table rows and voxel gradient, then one FP64 row sum and
-// (with the quad scratch) one gather finish all of them.
+// the same per-warp table rows and voxel gradient (all reductions), then one
+// FP64 row sum and (with the quad scratch) one gather finish all of them.
+// With several views the kernels alternate between two streams forked from
+// s, each with its own work counter: a view's grid holds every resident CTA
+// slot, so the next view's CTAs take the slots its first CTAs to run out of
+// tiles leave, instead of waiting for its last one.
 cudaError_t launch_backward(vr_volume *vol, const BwdView *views, int n, const ParamDev &p, double *grad_tf,
                             float *grad_vox, float4 *grad_quad, int quad_axis, long long nvox, bool accumulate,
                             unsigned *counter, cudaStream_t s)
@@ -460,28 +510,34 @@ cudaError_t launch_backward(vr_volume *vol, const BwdView *views, int n, const P
         if (e != cudaSuccess) return e;
     }
     float4 *wtab = reinterpret_cast<float4 *>(vol->wtab);
-    for (int q = 0; q < n; ++q) {
-        const BwdView &bv = views[q];
-        // direct reductions carry along each view's own axis; the quads have one
-        // orientation for the whole call
-        const GradDev gd = grad_dev(bv.v, grad_vox, grad_quad, grad_quad ? quad_axis : bv.carry_axis);
-        const int tiles_x = (bv.c.W + 7) / 8;
-        const unsigned ntiles = (unsigned)tiles_x * (unsigned)((bv.c.H + 3) / 4);
-        e = cudaMemsetAsync(counter, 0, sizeof(unsigned), s);
+    // direct reductions carry along each view's own axis; the quads have one
+    // orientation for the whole call
+    auto view_gd = [&](const BwdView &bv) {
+        return grad_dev(bv.v, grad_vox, grad_quad, grad_quad ? quad_axis : bv.carry_axis);
+    };
+    if (n == 1) {
+        e = launch_view(views[0], dt, p, wtab, view_gd(views[0]), counter, s);
+    } else {
+        unsigned *counter2 = nullptr;
+        next_counter(vol, &counter2);
+        e = ensure_aux_streams(vol);
         if (e != cudaSuccess) return e;
-        e = visit_layout(
-            bv.v, dt,
-            [&](auto lay) {
-                using Y = decltype(lay);
-                auto fn = bwd_kernel<typename Y::type, Y::log2b, Y::order>;
-                fn<<<view_grid((const void *)fn, bv.c), kBwdThreads, 0, s>>>(bv.v, bv.c, p, bv.rgba, bv.nsamples,
-                                                                            bv.grad_rgba, wtab, gd, counter,
-                                                                            tiles_x, ntiles);
-                return cudaGetLastError();
-            },
-            cudaErrorInvalidValue);
+        e = cudaEventRecord(vol->aux_ev[0], s);
         if (e != cudaSuccess) return e;
+        for (cudaStream_t a : vol->aux) {
+            e = cudaStreamWaitEvent(a, vol->aux_ev[0], 0);
+            if (e != cudaSuccess) return e;
+        }
+        for (int q = 0; q < n && e == cudaSuccess; ++q)
+            e = launch_view(views[q], dt, p, wtab, view_gd(views[q]), (q & 1) ? counter2 : counter, vol->aux[q & 1]);
+        // join both streams back into s, also after a failed launch
+        for (int k = 0; k < 2; ++k) {
+            cudaError_t j = cudaEventRecord(vol->aux_ev[1 + k], vol->aux[k]);
+            if (j == cudaSuccess) j = cudaStreamWaitEvent(s, vol->aux_ev[1 + k], 0);
+            if (e == cudaSuccess) e = j;
+        }
     }
+    if (e != cudaSuccess) return e;
     const int nb = 4 * p.K, chunk = 64;
     dim3 rgrid((unsigned)((nb + 255) / 256), (unsigned)((nrows + chunk - 1) / chunk));
     reduce_rows<<<rgrid, 256, 0, s>>>(vol->wtab, nrows, nb, grad_tf, chunk);

@@ -105,6 +105,11 @@ struct vr_volume {
     // hardware-filter copy (created on first texture-filter render)
     cudaArray_t tex_array = nullptr;
     cudaTextureObject_t tex = 0;
+    // backward of several views: two streams that overlap one view's last
+    // tiles with the next view's first, and the events that fork them from and
+    // join them to the caller's stream (created on first use)
+    cudaStream_t aux[2] = {nullptr, nullptr};
+    cudaEvent_t aux_ev[3] = {nullptr, nullptr, nullptr};
 };
 
 namespace vr {

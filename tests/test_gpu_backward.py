@@ -310,6 +310,60 @@ def test_multi_view_call_equals_accumulated_single_calls(P, torch, filt):
         vol.close()
 
 
+def test_multi_view_call_many_views_mixed_layouts_and_sizes(P, torch):
+    """One vr_render_backward_views call over 22 views (19 of them looking
+    along z, three along x or y, one of them away from the box), with images
+    of ragged sizes (widths and heights that are not multiples of the 8 x 4
+    ray tile), equals the per-view calls accumulated: the views' kernels
+    alternate between two streams and overlap, each with its own work
+    counter, all adding into the same rows and voxel gradient."""
+    from paper_1211_4896_gb300 import _lib as L
+    dev = torch.device("cuda")
+    dims = (34, 30, 28)
+    cube = synth.hi_cube(dims, n_blobs=6, n_disks=1, seed=77)
+    vol = P.Volume(cube.to(dev), "f32")
+    tf = torch.from_numpy(synth.tf_random_pwl(seed=8, alpha_max=0.3)).to(dev)
+    ext = [d - 1.0 for d in dims]
+    rng = np.random.default_rng(3)
+    cams = []
+    for q in range(22):
+        if q < 19:
+            f = np.array([rng.uniform(-0.2, 0.2), rng.uniform(-0.2, 0.2), 1.0])
+        else:
+            f = [np.array([1.0, 0.15, 0.1]), np.array([0.1, -1.0, 0.2]), np.array([0.0, 0.0, -1.0])][q - 19]
+        f = f / np.linalg.norm(f)
+        eye = tuple(e / 2.0 - 1.7 * max(ext) * c for e, c in zip(ext, f))
+        if q == 21:                     # looks away from the box
+            f = -f
+        up = (0.0, 1.0, 0.0) if abs(f[1]) < 0.9 else (0.0, 0.0, 1.0)
+        W, H = [(37, 29), (8, 4), (41, 13), (16, 9), (23, 31)][q % 5]
+        cams.append(synth.camera_persp(eye, tuple(f), up, 40.0, W, H))
+    imgs, nss, gs = [], [], []
+    for q, cam in enumerate(cams):
+        img, ns = P.render(vol, cam, tf, -3.0, 30.0, 0.5, 2.0)
+        imgs.append(img)
+        nss.append(ns)
+        gs.append(torch.randn(img.shape, device=dev, generator=torch.Generator(device=dev).manual_seed(300 + q)))
+    # the layouts the renders built and read
+    layouts = [L.vr_view_layout(vol.handle, L.make_camera(c)) for c in cams]
+    assert len(set(layouts)) >= 2, layouts
+    assert int(nss[21].sum()) == 0
+    try:
+        ref_tf, ref_vox = None, None
+        for q, cam in enumerate(cams):
+            ref_tf, ref_vox = P.render_backward(vol, cam, tf, -3.0, 30.0, 0.5, imgs[q], nss[q], gs[q], 2.0,
+                                                grad_tf=ref_tf, grad_vox=ref_vox, accumulate=q > 0,
+                                                vox_reduce="direct")
+        got_tf, got_vox = P.render_backward_views(vol, cams, tf, -3.0, 30.0, 0.5, imgs, nss, gs, 2.0,
+                                                  vox_reduce="direct")
+        torch.cuda.synchronize()
+        assert (got_tf - ref_tf).abs().max().item() <= 1e-5 * ref_tf.abs().max().item()
+        assert (got_vox - ref_vox).abs().max().item() <= 1e-4 * ref_vox.abs().max().item()
+        assert ref_vox.abs().max().item() > 0
+    finally:
+        vol.close()
+
+
 @pytest.mark.slow
 def test_differentiation_workload_crop_elementwise_against_fp64(P, torch):
     """The differentiation workload's kernel configuration checked element by
