@@ -143,7 +143,8 @@ typedef struct {
     int64_t copy_bytes;       /* device bytes of the brick copies (see vr_volume_create) */
     int copies;               /* which copies exist: bit 1 / 2 plain y- / z-fastest; bit 3 / 4 / 5
                                  paired x- / y- / z-fastest (16-bit storage); bit 6 / 7 / 8
-                                 blocked, deep along x / y / z (sparse views) */
+                                 blocked, deep along x / y / z (sparse views); bit 9 / 10 / 11
+                                 texture layers across x / y / z (float storage, dense views) */
     int64_t scratch_bytes;    /* device bytes of the backward scratch: the per-warp table-gradient
                                  rows and, once a dense view has used it, the voxel-gradient quad
                                  scratch (16 bytes per voxel) */
@@ -177,7 +178,16 @@ typedef struct {
  * copy instead: blocks of 2 x 2 x 4 voxels, one 32-byte sector each, deep
  * along the axis the view direction is closest to (about 1.2x the bricks'
  * bytes); VR_SPARSE_LAYOUT=b asks for blocked copies (2 x 2 x 2 blocks) for
- * float volumes too, =i never.  A copy is built
+ * float volumes too, =i never.  For float storage and rays closer than
+ * VR_SPARSE_MIN_PITCH, the forward, batched and backward calls read a
+ * texture-layer copy instead (the paper's texture memory, Section 4.3): a 2D
+ * layered texture (layers across the axis the view direction runs along
+ * most, 4 bytes per voxel), whose four-texel gather at a cell's exact
+ * integer corner fetches the cell's corners two per instruction (the values
+ * stored, interpolated in software: bit-identical results); a volume beyond
+ * the device's layered-texture limits (usually 32768 texels across a layer,
+ * 2048 layers) keeps the brick copies; VR_TEX_LAYERS=0 (read at each call)
+ * turns the layers off.  A copy is built
  * only outside stream capture, while the device keeps an eighth of its memory
  * free besides it (else the bricks themselves serve), synchronising
  * cuda_stream once; environment variable VR_BRICK_COPIES=0 turns copies off.
@@ -210,8 +220,8 @@ vr_status vr_volume_info(vr_volume_t vol, vr_volume_info_t *out);
 /* The brick layout a software-filter render of this view reads as things
  * stand: *layout = -1 for the x-fastest bricks, else the copy id (1, 2: plain
  * copies with y / z fastest; 3, 4, 5: paired 16-bit copies with x / y / z
- * fastest; 6, 7, 8: blocked copies deep along x / y / z; bit `id` of
- * vr_volume_info's copies).  Builds nothing: a preferred
+ * fastest; 6, 7, 8: blocked copies deep along x / y / z; 9, 10, 11:
+ * texture layers across x / y / z; bit `id` of vr_volume_info's copies).  Builds nothing: a preferred
  * copy that does not exist yet reports -1 until a render builds it.  A batched
  * call launches one kernel per distinct layout of its views.  Errors:
  * INVALID_ARG. */

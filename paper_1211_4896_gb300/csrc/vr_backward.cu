@@ -291,7 +291,7 @@ __global__ void __launch_bounds__(kBwdThreads) bwd_kernel(VolDev v, CamDev c, Pa
         auto step = [&](const Cell &cell, const Gathered<VT, L> &f, Cell &ncell, Gathered<VT, L> &nf) {
             const bool more = k + 1 < n;
             if (more) {
-                ncell = locate<LOG2B, L>(v, sample_pos(ray, k + 1, p.step));
+                ncell = locate_t<VT, LOG2B, L, false>(v, sample_pos(ray, k + 1, p.step));
                 fetch_corners<VT, LOG2B, L>(v, ncell, nf);
             }
             const float val = interp_corners(cell, f);
@@ -330,7 +330,7 @@ __global__ void __launch_bounds__(kBwdThreads) bwd_kernel(VolDev v, CamDev c, Pa
         Cell c0, c1;
         Gathered<VT, L> f0, f1;
         if (active) {
-            c0 = locate<LOG2B, L>(v, sample_pos(ray, 0, p.step));
+            c0 = locate_t<VT, LOG2B, L, false>(v, sample_pos(ray, 0, p.step));
             fetch_corners<VT, LOG2B, L>(v, c0, f0);
         }
         for (;;) {      // two register sets in turn (no copy of the prefetched sample)
@@ -417,7 +417,7 @@ static unsigned view_grid(const void *fn, const CamDev &c)
 
 static cudaError_t view_kernel(const BwdView &bv, vr_dtype dt, const void **fn_out)
 {
-    return visit_layout(
+    return visit_layout_tex(
         bv.v, dt,
         [&](auto lay) {
             using Y = decltype(lay);
@@ -459,7 +459,7 @@ static cudaError_t launch_view(const BwdView &bv, vr_dtype dt, const ParamDev &p
     const unsigned ntiles = (unsigned)tiles_x * (unsigned)((bv.c.H + 3) / 4);
     cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(unsigned), s);
     if (e != cudaSuccess) return e;
-    return visit_layout(
+    return visit_layout_tex(
         bv.v, dt,
         [&](auto lay) {
             using Y = decltype(lay);

@@ -226,7 +226,7 @@ static vr_status prepare_jobs(const vr_job *jobs, int n, int tile_w, int wpt, bo
             return (set_error(std::string(who) + ": all volumes of a batch must share store dtype and brick size"),
                     VR_ERR_UNSUPPORTED);
         }
-        group_of[q] = preferred_copy(J.vol, &J.cam, may_build, s, true) + 1;
+        group_of[q] = preferred_copy(J.vol, &J.cam, may_build, s, kReadsBlocked | kReadsLayers) + 1;
         ++seg[group_of[q]].njobs;
     }
     int fill[kGroups];

@@ -75,6 +75,29 @@ template <typename S> struct Blocked {
 template <typename T> struct is_blocked { static constexpr bool value = false; };
 template <typename S> struct is_blocked<Blocked<S>> { static constexpr bool value = true; };
 
+// Element of a texture-layer copy of a float volume (Section 4.3 keeps the
+// sub-cubes in texture memory): a 2D layered texture, one layer per voxel
+// plane across axis A (the copy's order), whose in-layer (u, v) axes are
+// given by LayerUV; read with tld4, the texture unit's four-texel
+// gather, two per sample (the cell's corners in layer a0 and a0 + 1) at the
+// cell's exact integer corner, so the values are the stored texels and the
+// interpolation stays the software one (bit-identical to the bricks).  The
+// texture's block-linear tiling keeps both in-layer axes local, and the
+// texture unit does the addressing that the bricks cost in instructions.
+// VolDev.data holds the cudaTextureObject_t.
+template <typename S> struct TexLayers {
+    using storage = S;
+};
+template <typename T> struct is_layers { static constexpr bool value = false; };
+template <typename S> struct is_layers<TexLayers<S>> { static constexpr bool value = true; };
+
+// In-layer texel axes (u, v) of a layer copy across axis A: layers across z
+// hold (x, y), across x hold (z, y), across y hold (x, z).
+template <int A> struct LayerUV {
+    static constexpr int u = A == 0 ? 2 : 0;
+    static constexpr int v = A == 1 ? 2 : 1;
+};
+
 // Geometry of a blocked brick of B^3 cells (B + 1 voxels per axis with the
 // apron, padded to whole blocks).  Axes (u, v, w): w is the copy's axis, u
 // and v the other two in x, y, z order.  Element (lu, lv, lw) of a brick is
@@ -123,7 +146,7 @@ R visit_layout_b(const VolDev &v, F &&f, R none)
 template <typename S, typename F, typename R>
 R visit_layout_s(const VolDev &v, F &&f, R none)
 {
-    if (v.paired == 2) return none;                 // blocked copies: visit_layout_all
+    if (v.paired >= 2) return none;                 // blocked and layer copies: see below
     switch (v.log2b) {
     case 4: return visit_layout_b<S, 4>(v, f, none);
     case 5: return visit_layout_b<S, 5>(v, f, none);
@@ -143,8 +166,28 @@ R visit_layout(const VolDev &v, vr_dtype dt, F &&f, R none)
     return none;
 }
 
-// visit_layout, blocked copies included (the kernels that read them: the
-// forward and the batched forward).
+// Texture-layer copies (float storage only): the brick size plays no part in
+// them, so one instance (LOG2B 4) serves every volume.
+template <typename F, typename R>
+R visit_layers(const VolDev &v, vr_dtype dt, F &&f, R none)
+{
+    if (dt != VR_F32) return none;
+    if (v.order == 0) return f(Layout<TexLayers<float>, 4, 0>{});
+    if (v.order == 1) return f(Layout<TexLayers<float>, 4, 1>{});
+    if (v.order == 2) return f(Layout<TexLayers<float>, 4, 2>{});
+    return none;
+}
+
+// visit_layout, texture-layer copies included (the backward).
+template <typename F, typename R>
+R visit_layout_tex(const VolDev &v, vr_dtype dt, F &&f, R none)
+{
+    if (v.paired == 3) return visit_layers(v, dt, f, none);
+    return visit_layout(v, dt, f, none);
+}
+
+// visit_layout, blocked and texture-layer copies included (the kernels that
+// read them: the forward and the batched forward).
 template <typename S, int LOG2B, typename F, typename R>
 R visit_blocked_b(const VolDev &v, F &&f, R none)
 {
@@ -169,6 +212,7 @@ R visit_layout_all_s(const VolDev &v, F &&f, R none)
 template <typename F, typename R>
 R visit_layout_all(const VolDev &v, vr_dtype dt, F &&f, R none)
 {
+    if (v.paired == 3) return visit_layers(v, dt, f, none);
     switch (dt) {
     case VR_F32: return visit_layout_all_s<float>(v, f, none);
     case VR_F16: return visit_layout_all_s<__half>(v, f, none);
@@ -325,11 +369,27 @@ __device__ __forceinline__ Cell locate_blocked(const VolDev &v, float3 p)
     return c;
 }
 
+// The cell of a sample in a texture-layer copy: the corner and fractions
+// only (the texture unit addresses the texels).
+__device__ __forceinline__ Cell locate_cell(const VolDev &v, float3 p)
+{
+    Cell c;
+    c.x0 = min(max(__float2int_rd(p.x), 0), v.nx - 2);
+    c.y0 = min(max(__float2int_rd(p.y), 0), v.ny - 2);
+    c.z0 = min(max(__float2int_rd(p.z), 0), v.nz - 2);
+    c.fx = p.x - (float)c.x0;
+    c.fy = p.y - (float)c.y0;
+    c.fz = p.z - (float)c.z0;
+    c.base = 0;
+    return c;
+}
+
 // The cell of a sample in the layout of element type T.
 template <typename T, int LOG2B, int L, bool NARROW>
 __device__ __forceinline__ Cell locate_t(const VolDev &v, float3 p)
 {
-    if constexpr (is_blocked<T>::value) return locate_blocked<typename T::storage, LOG2B, L>(v, p);
+    if constexpr (is_layers<T>::value) return locate_cell(v, p);
+    else if constexpr (is_blocked<T>::value) return locate_blocked<typename T::storage, LOG2B, L>(v, p);
     else return locate<LOG2B, L, NARROW>(v, p);
 }
 
@@ -364,12 +424,60 @@ template <typename S, int L> struct Gathered<Blocked<S>, L> {
     S v[8];
     __device__ __forceinline__ float at(int q) const { return to_f(v[q]); }
 };
+template <typename S, int L> struct Gathered<TexLayers<S>, L> {
+    float v[8];
+    __device__ __forceinline__ float at(int q) const { return v[q]; }
+};
+
+// tld4 on layer `layer` of a 2D layered texture at unnormalised (u, v): the
+// red channel of the 2 x 2 texels whose centres surround (u, v), in the
+// order (u0, v1), (u1, v1), (u1, v0), (u0, v0) with u0 = floor(u - 1/2).
+// At u = a + 1, v = b + 1 (integers a, b) that is texels a, a + 1 and b, b + 1
+// exactly, whatever the unit's fixed-point rounding.
+__device__ __forceinline__ float4 gather_layer(cudaTextureObject_t t, int layer, float u, float v)
+{
+    float4 r;
+    asm("tld4.r.a2d.v4.f32.f32 {%0, %1, %2, %3}, [%4, {%5, %6, %7, %7}];"
+        : "=f"(r.x), "=f"(r.y), "=f"(r.z), "=f"(r.w)
+        : "l"(t), "r"(layer), "f"(u), "f"(v));
+    return r;
+}
+
+template <typename T, int LOG2B, int L>
+__device__ __forceinline__ void fetch_corners_mem(const VolDev &v, const Cell &c, Gathered<T, L> &f);
 
 // T is the stored element: float / __half / __nv_bfloat16 (eight loads) or
 // Pair<...> (four paired loads; each returns a corner and its neighbour along
 // the fastest axis of order L).
 template <typename T, int LOG2B, int L>
 __device__ __forceinline__ void fetch_corners(const VolDev &v, const Cell &c, Gathered<T, L> &f)
+{
+    if constexpr (is_layers<T>::value) {
+        // corners q (bit 0 +x, bit 1 +y, bit 2 +z) of layers a0 and a0 + 1; a
+        // clamped cell keeps every texel inside the texture
+        const cudaTextureObject_t tex = static_cast<cudaTextureObject_t>(reinterpret_cast<uintptr_t>(v.data));
+        using UV = LayerUV<L>;
+        const int c3[3] = {c.x0, c.y0, c.z0};
+        const float u = (float)c3[UV::u] + 1.0f, w = (float)c3[UV::v] + 1.0f;
+        constexpr int bu = 1 << UV::u, bv = 1 << UV::v, ba = 1 << L;      // corner bits of u, v, layer
+        const float4 g0 = gather_layer(tex, c3[L], u, w);
+        const float4 g1 = gather_layer(tex, c3[L] + 1, u, w);
+        f.v[bv] = g0.x;
+        f.v[bu | bv] = g0.y;
+        f.v[bu] = g0.z;
+        f.v[0] = g0.w;
+        f.v[ba | bv] = g1.x;
+        f.v[ba | bu | bv] = g1.y;
+        f.v[ba | bu] = g1.z;
+        f.v[ba] = g1.w;
+    } else {
+        fetch_corners_mem<T, LOG2B, L>(v, c, f);
+    }
+}
+
+// The memory-copy layouts (bricks and their copies).
+template <typename T, int LOG2B, int L>
+__device__ __forceinline__ void fetch_corners_mem(const VolDev &v, const Cell &c, Gathered<T, L> &f)
 {
     using O = BrickOrder<LOG2B, L>;
     if constexpr (kBoundsCheck && !is_blocked<T>::value) {
@@ -532,6 +640,7 @@ struct Composite {
 // float loses from it (axis views 3% slower), so float keeps depth 1.
 template <typename T> struct Pipeline { static constexpr int depth = 2; };
 template <> struct Pipeline<float> { static constexpr int depth = 1; };
+template <> struct Pipeline<TexLayers<float>> { static constexpr int depth = 1; };
 
 // The value the transfer function sees for a sample: the interpolated value
 // itself (generic transfer function), or a transform of it at the sample's

@@ -130,7 +130,8 @@ static cudaError_t launch_fwd_t(const VolDev &v, const CamDev &c, const ParamDev
     cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(unsigned), s);
     if (e != cudaSuccess) return e;
     log_line("forward %dx%d: layout order %d%s, %u tiles of 8x4 rays, grid %u x %d threads (%d per SM)", c.W, c.H,
-             v.order, v.paired == 1 ? " paired" : (v.paired == 2 ? " blocked" : ""), ntiles, grid, kFwdThreads,
+             v.order, v.paired == 1 ? " paired" : (v.paired == 2 ? " blocked" : (v.paired == 3 ? " texture layers" : "")),
+             ntiles, grid, kFwdThreads,
              per_sm);
     fn<<<grid, kFwdThreads, 0, s>>>(v, c, p, out, nsamples, counter, tiles_x, ntiles);
     return cudaGetLastError();

@@ -52,7 +52,8 @@ struct VolDev {
     long long stride;      // elements per brick (>= (B+1)^3, padded)
     int order;             // element order inside a brick (0: x, 1: y, 2: z fastest)
     int paired;            // 1: each element holds (own value, next value along the fastest axis);
-                           // 2: blocked, 2 x 2 x BW blocks of one 32-byte sector deep along axis `order`
+                           // 2: blocked, 2 x 2 x BW blocks of one 32-byte sector deep along axis `order`;
+                           // 3: texture layers across axis `order`, `data` holds the cudaTextureObject_t
     long long nelem;       // elements in the buffer (bricks x stride), for the bounds-check build
     unsigned *status;      // the volume's status word (timeouts, caught out-of-range indices)
 };
@@ -86,8 +87,17 @@ struct vr_volume {
     // prefers them, indexed by copy id: 1, 2 plain copies with y / z fastest
     // (bytes each); 3, 4, 5 paired 16-bit copies with x / y / z fastest
     // (2 * bytes each); 6, 7, 8 blocked copies deep along x / y / z (sparse
-    // views, forward only); [0] unused (the bricks themselves are copy -1)
+    // views, forward only); [0] unused (the bricks themselves are copy -1).
+    // Copy ids 9, 10, 11 are the texture-layer copies below.
     void *copies[9] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    // texture-layer copies of a float volume (copy ids 9, 10, 11: layers
+    // across x / y / z), built on the first dense view that prefers them: the
+    // layered array, the surface that fills it and the texture that reads it
+    struct Layers {
+        cudaArray_t array = nullptr;
+        cudaSurfaceObject_t surf = 0;
+        cudaTextureObject_t tex = 0;
+    } layers[3];
     // backward scratch: one FP32 row of K RGBA gradient bins per warp
     float *wtab = nullptr;
     size_t wtab_cap = 0;         // floats
@@ -144,18 +154,29 @@ cudaError_t launch_forward_texture(const vr_volume *vol, const CamDev &c, const 
 constexpr unsigned kStatusTimeout = 1u;        // a bounded wait gave up
 constexpr unsigned kStatusOutOfBounds = 2u;    // an index outside its buffer was caught and skipped
 
-constexpr int kCopyIds = 9;
+constexpr int kCopyIds = 12;
 inline bool copy_paired(int copy) { return copy >= 3 && copy < 6; }
-inline bool copy_blocked(int copy) { return copy >= 6; }
-inline int copy_order(int copy) { return copy >= 6 ? copy - 6 : (copy >= 3 ? copy - 3 : copy); }
+inline bool copy_blocked(int copy) { return copy >= 6 && copy < 9; }
+inline bool copy_layers(int copy) { return copy >= 9 && copy < 12; }
+inline int copy_order(int copy) { return copy >= 9 ? copy - 9 : (copy >= 6 ? copy - 6 : (copy >= 3 ? copy - 3 : copy)); }
+// Whether copy id `copy` exists on vol.
+bool copy_built(const vr_volume *vol, int copy);
 // Elements per brick of a blocked copy (B = 1 << log2b; elem_bytes 4 or 2).
 long long blocked_stride(int log2b, int elem_bytes);
 VolDev vol_dev_copy(const vr_volume *vol, int copy);
-// allow_blocked: the caller's kernels read blocked copies (the forward and
-// the batched forward); other callers get the plain or paired choice.
-int preferred_copy(vr_volume *vol, const vr_camera *cam, bool may_build, cudaStream_t s, bool allow_blocked = false);
+// kinds: the copy kinds the caller's kernels read besides plain and paired
+// copies (kReadsBlocked: the forward and the batched forward; kReadsLayers:
+// those and the backward).
+constexpr unsigned kReadsBlocked = 1u, kReadsLayers = 2u;
+int preferred_copy(vr_volume *vol, const vr_camera *cam, bool may_build, cudaStream_t s, unsigned kinds = 0u);
 size_t copy_bytes(const vr_volume *vol, int copy);
 cudaError_t launch_copy(vr_volume *vol, int copy, cudaStream_t s);
+// Texture-layer copy across `axis` (float storage): allocates the layered
+// array (through the library's allocation hook), its surface and texture,
+// and fills it from the bricks; frees what it made on failure.
+cudaError_t build_layers(vr_volume *vol, int axis, cudaStream_t s);
+void free_layers(vr_volume *vol);
+cudaError_t dev_alloc_layers(cudaArray_t *a, int u, int v, int layers);   // hook of dev_alloc for arrays
 // One view of a backward call: the layout it reads (a brick copy or the
 // bricks), its camera, the forward's image and sample counts, dL/d(image),
 // and the axis along which its direct voxel-gradient sums are carried.

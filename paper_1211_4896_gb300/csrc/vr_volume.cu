@@ -352,8 +352,95 @@ static void copy_d(vr_volume *vol, int copy, cudaStream_t s)
     }
 }
 
+// ---------------------------------------------------------------------------
+// Texture-layer copies (float storage): voxel (x, y, z) is texel (u, v) of
+// layer a, with a the voxel's coordinate across the copy's axis A and (u, v)
+// its in-layer coordinates (LayerUV<A>).  One thread per voxel, reading the
+// bricks in x order and writing through the layered surface.
+// ---------------------------------------------------------------------------
+template <int A>
+__global__ void __launch_bounds__(256) unbrick_to_layers(VolDev v, cudaSurfaceObject_t surf)
+{
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y, z = blockIdx.z;
+    if (x >= v.nx) return;
+    const int B = 1 << v.log2b, B1 = B + 1;
+    const int bx = min(x >> v.log2b, v.nbx - 1), by = min(y >> v.log2b, v.nby - 1),
+              bz = min(z >> v.log2b, v.nbz - 1);
+    const int lx = x - bx * B, ly = y - by * B, lz = z - bz * B;
+    const long long brick = ((long long)bz * v.nby + by) * v.nbx + bx;
+    const float val = static_cast<const float *>(v.data)[brick * v.stride + ((long long)lz * B1 + ly) * B1 + lx];
+    const int c[3] = {x, y, z};
+    surf2DLayeredwrite(val, surf, c[LayerUV<A>::u] * (int)sizeof(float), c[LayerUV<A>::v], c[A]);
+}
+
+static cudaError_t fill_layers(vr_volume *vol, int axis, cudaStream_t s)
+{
+    const VolDev v = vol_dev(vol);
+    const dim3 grid((unsigned)((vol->dims[0] + 255) / 256), (unsigned)vol->dims[1], (unsigned)vol->dims[2]);
+    const cudaSurfaceObject_t surf = vol->layers[axis].surf;
+    switch (axis) {
+    case 0: unbrick_to_layers<0><<<grid, 256, 0, s>>>(v, surf); break;
+    case 1: unbrick_to_layers<1><<<grid, 256, 0, s>>>(v, surf); break;
+    default: unbrick_to_layers<2><<<grid, 256, 0, s>>>(v, surf); break;
+    }
+    return cudaGetLastError();
+}
+
+static void destroy_layers(vr_volume::Layers &l)
+{
+    if (l.tex) cudaDestroyTextureObject(l.tex);
+    if (l.surf) cudaDestroySurfaceObject(l.surf);
+    if (l.array) cudaFreeArray(l.array);
+    l = vr_volume::Layers();
+}
+
+void free_layers(vr_volume *vol)
+{
+    for (vr_volume::Layers &l : vol->layers) destroy_layers(l);
+}
+
+cudaError_t build_layers(vr_volume *vol, int axis, cudaStream_t s)
+{
+    if (vol->store_dtype != VR_F32 || axis < 0 || axis > 2) return cudaErrorInvalidValue;
+    if (vol->layers[axis].tex) return cudaSuccess;
+    const int64_t ext[3] = {vol->dims[0], vol->dims[1], vol->dims[2]};
+    const int u = (int)ext[axis == 0 ? 2 : 0], v = (int)ext[axis == 1 ? 2 : 1], n = (int)ext[axis];
+    int mw = 0, mh = 0, ml = 0;
+    cudaDeviceGetAttribute(&mw, cudaDevAttrMaxTexture2DLayeredWidth, vol->device);
+    cudaDeviceGetAttribute(&mh, cudaDevAttrMaxTexture2DLayeredHeight, vol->device);
+    cudaDeviceGetAttribute(&ml, cudaDevAttrMaxTexture2DLayeredLayers, vol->device);
+    if (u > mw || v > mh || n > ml) return cudaErrorInvalidValue;        // beyond the texture limits
+    vr_volume::Layers &l = vol->layers[axis];
+    cudaError_t e = dev_alloc_layers(&l.array, u, v, n);
+    if (e != cudaSuccess) {
+        l.array = nullptr;
+        return e;
+    }
+    cudaResourceDesc rd{};
+    rd.resType = cudaResourceTypeArray;
+    rd.res.array.array = l.array;
+    e = cudaCreateSurfaceObject(&l.surf, &rd);
+    if (e == cudaSuccess) e = fill_layers(vol, axis, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess) {
+        cudaTextureDesc td{};
+        td.addressMode[0] = td.addressMode[1] = td.addressMode[2] = cudaAddressModeClamp;
+        td.filterMode = cudaFilterModePoint;
+        td.readMode = cudaReadModeElementType;
+        td.normalizedCoords = 0;
+        e = cudaCreateTextureObject(&l.tex, &rd, &td, nullptr);
+    }
+    if (e != cudaSuccess) {
+        l.tex = 0;
+        destroy_layers(l);
+    }
+    return e;
+}
+
 size_t copy_bytes(const vr_volume *vol, int copy)
 {
+    if (copy_layers(copy)) return (size_t)(vol->dims[0] * vol->dims[1] * vol->dims[2]) * sizeof(float);
     if (copy_blocked(copy)) {
         const int eb = vol->store_dtype == VR_F32 ? 4 : 2;
         return (size_t)(vol->nb[0] * vol->nb[1] * vol->nb[2]) * (size_t)blocked_stride(vol->log2b, eb) * (size_t)eb;
@@ -363,7 +450,8 @@ size_t copy_bytes(const vr_volume *vol, int copy)
 
 cudaError_t launch_copy(vr_volume *vol, int copy, cudaStream_t s)
 {
-    if (copy < 1 || copy >= kCopyIds || !vol->copies[copy]) return cudaErrorInvalidValue;
+    if (copy_layers(copy)) return vol->layers[copy - 9].tex ? fill_layers(vol, copy - 9, s) : cudaErrorInvalidValue;
+    if (copy < 1 || copy >= 9 || !vol->copies[copy]) return cudaErrorInvalidValue;
     if (vol->store_dtype == VR_F32 && copy_paired(copy)) return cudaErrorInvalidValue;   // no float pairs
     switch (vol->store_dtype) {
     case VR_F32: copy_d<float>(vol, copy, s); break;

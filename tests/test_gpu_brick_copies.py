@@ -31,6 +31,13 @@ def torch():
     return cuda_or_skip()
 
 
+@pytest.fixture(autouse=True)
+def _brick_copies_only(monkeypatch):
+    """Dense float views would read texture-layer copies
+    (tests/test_gpu_tex_layers.py); these tests are about the brick copies."""
+    monkeypatch.setenv("VR_TEX_LAYERS", "0")
+
+
 @pytest.fixture(scope="module")
 def P(torch):
     import paper_1211_4896_gb300 as P

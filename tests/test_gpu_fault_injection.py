@@ -56,7 +56,8 @@ def test_volume_create_reports_oom_and_recovers(P, torch, L):
     vol.close()
 
 
-def test_brick_copy_that_cannot_be_allocated_is_not_used(P, torch, L):
+def test_brick_copy_that_cannot_be_allocated_is_not_used(P, torch, L, monkeypatch):
+    monkeypatch.setenv("VR_TEX_LAYERS", "0")          # the brick copies only
     vol = P.Volume(_cube(torch), "f32")
     tf = _tf(torch)
     cam = _cam((0, 0, 1), (1, 0, 0))         # image rows along +y: prefers the y-fastest copy
@@ -67,6 +68,26 @@ def test_brick_copy_that_cannot_be_allocated_is_not_used(P, torch, L):
         assert L.vr_view_layout(vol.handle, L.make_camera(cam)) == -1
         b, nb = P.render(vol, cam, tf, -3.0, 30.0, 0.5)   # now the copy is built and read
         assert L.vr_volume_info(vol.handle)["copies"] == 1 << 1
+        assert torch.equal(a, b) and torch.equal(na, nb)
+        assert a[..., 3].max().item() > 0.05
+    finally:
+        vol.close()
+
+
+def test_texture_layers_that_cannot_be_allocated_are_not_used(P, torch, L):
+    """The layered array's allocation fails: the view falls back to its brick
+    copy (built by the same call); the next call builds the layers and reads
+    them; the images agree bit for bit."""
+    vol = P.Volume(_cube(torch), "f32")
+    tf = _tf(torch)
+    cam = _cam((0, 0, 1), (1, 0, 0))         # along z, rows along +y: layers across z, else the y-fastest copy
+    try:
+        L.vr_debug_fail_alloc(0)
+        a, na = P.render(vol, cam, tf, -3.0, 30.0, 0.5)
+        assert L.vr_volume_info(vol.handle)["copies"] == 1 << 1
+        b, nb = P.render(vol, cam, tf, -3.0, 30.0, 0.5)
+        assert L.vr_volume_info(vol.handle)["copies"] == (1 << 1) | (1 << 11)
+        assert L.vr_view_layout(vol.handle, L.make_camera(cam)) == 11
         assert torch.equal(a, b) and torch.equal(na, nb)
         assert a[..., 3].max().item() > 0.05
     finally:

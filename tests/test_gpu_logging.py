@@ -1,5 +1,5 @@
 """VR_LOG=1: the library writes one line on stderr per launch decision (the
-brick layout a view reads and when a copy is built, the forward's grid, the
+layout a view reads and when a brick or texture-layer copy is built, the forward's grid, the
 batch's layout groups and grids, the backward's voxel-gradient form);
 without it, nothing."""
 import os
@@ -24,6 +24,9 @@ img, ns = P.render(vol, cams[1], tf, -3.0, 30.0, 0.5)
 P.render_backward(vol, cams[1], tf, -3.0, 30.0, 0.5, img, ns, torch.randn_like(img))
 P.render_batched([dict(vol=vol, cam=cam, tf=tf, vmin=-3.0, vmax=30.0, step=0.5, out=torch.empty_like(img))
                   for cam in cams], use_graph=False)
+import os
+os.environ["VR_TEX_LAYERS"] = "0"          # the brick copies
+P.render(vol, cams[1], tf, -3.0, 30.0, 0.5)
 torch.cuda.synchronize()
 vol.close()
 print("done")
@@ -33,6 +36,7 @@ print("done")
 def _run(log):
     env = dict(os.environ, PYTHONPATH=ROOT + os.pathsep + os.environ.get("PYTHONPATH", ""))
     env.pop("VR_LOG", None)
+    env.pop("VR_TEX_LAYERS", None)
     if log:
         env["VR_LOG"] = "1"
     r = subprocess.run([sys.executable, "-c", SCRIPT], cwd=ROOT, env=env, capture_output=True, text=True,
@@ -45,8 +49,10 @@ def test_log_lines_only_with_vr_log():
     cuda_or_skip()
     lines = _run(True)
     text = "\n".join(lines)
-    assert "prefers brick copy 1 (plain); building it" in text
-    assert "forward 64x64: layout order 1" in text
+    assert "prefers texture layers across axis 2; building them" in text
+    assert "forward 64x64: layout order 2 texture layers" in text
     assert "backward of 1 view(s): voxel gradient through the quad scratch" in text
-    assert "batch, brick layout -1: 1 job(s)" in text and "batch, brick layout 1: 1 job(s)" in text
+    assert "batch, brick layout 11: 2 job(s)" in text
+    assert "prefers brick copy 1 (plain); building it" in text
+    assert "forward 64x64: layout order 1," in text
     assert _run(False) == []
