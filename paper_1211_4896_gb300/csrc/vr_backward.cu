@@ -233,8 +233,16 @@ struct CellRun {
     }
 };
 
+// Resident CTAs the register budget is sized for: six for the texture layers
+// (80 registers, a few spilled, against 90 at five: the eight 1080p views of
+// the 1024^3 cube 2.82 against 3.10 ms per view; the layers' gathers need no
+// brick addressing, so they keep fewer values live); the compiler's choice
+// otherwise (six CTAs measured slower for the bricks).
+template <typename T> struct BwdMinBlocks { static constexpr int value = 0; };   // 0: no minimum
+template <> struct BwdMinBlocks<TexLayers<float>> { static constexpr int value = 6; };
+
 template <typename VT, int LOG2B, int L>
-__global__ void __launch_bounds__(kBwdThreads) bwd_kernel(VolDev v, CamDev c, ParamDev p,
+__global__ void __launch_bounds__(kBwdThreads, BwdMinBlocks<VT>::value) bwd_kernel(VolDev v, CamDev c, ParamDev p,
                                                            const float4 *__restrict__ rgba,
                                                            const uint32_t *__restrict__ nsamples,
                                                            const float4 *__restrict__ grad_rgba, float4 *wtab,

@@ -33,12 +33,17 @@ struct JobDev {
 // L; template parameters, so each instance keeps the register budget of a
 // single march; a batch reading several copies launches once per copy).
 // CTAs per SM the register budget is sized for: paired 16-bit copies fit
-// four (64 registers) without spills and gain from it; the other kernels keep
-// the compiler's choice (for float, three CTAs measured faster than four), so
-// do the kernels whose warps share tiles (their hand-over spills at 64).
+// four (64 registers) without spills and gain from it; the texture layers
+// gain from five (48 registers, some spilled to L1; the eight 1080p views of
+// the 1024^3 cube 13.0 ms, against 14.7 at four and 17.4 at the compiler's
+// three: their gathers wait on the texture unit, and more warps hide it); the other
+// kernels keep the compiler's choice (for float bricks, three CTAs measured
+// faster than four), so do the kernels whose warps share tiles (their
+// hand-over spills at 64).
 template <typename T> struct BatMinBlocks { static constexpr int value = 0; };   // 0: no minimum
 template <> struct BatMinBlocks<Pair<__half>> { static constexpr int value = 4; };
 template <> struct BatMinBlocks<Pair<__nv_bfloat16>> { static constexpr int value = 4; };
+template <> struct BatMinBlocks<TexLayers<float>> { static constexpr int value = 5; };
 
 // Warps per tile: 2^log2_wpt warps of a CTA take one tile of tw x (th 2^log2_wpt)
 // rays together, each its own tw x th part, so that the neighbouring parts

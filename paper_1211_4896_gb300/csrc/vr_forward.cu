@@ -21,8 +21,15 @@ namespace vr {
 
 constexpr int kFwdThreads = 256;
 
+// Resident CTAs the register budget is sized for: five for the texture layers
+// (48 registers, a few spilled to L1: the eight 1080p views of the 1024^3 cube
+// 14.9 against 16.7 ms at the compiler's four, whose gathers wait on the
+// texture unit); the compiler's choice for the brick layouts.
+template <typename T> struct FwdMinBlocks { static constexpr int value = 0; };   // 0: no minimum
+template <> struct FwdMinBlocks<TexLayers<float>> { static constexpr int value = 5; };
+
 template <typename T, int LOG2B, int L>
-__global__ void __launch_bounds__(kFwdThreads) fwd_kernel(VolDev v, CamDev c, ParamDev p, float4 *out,
+__global__ void __launch_bounds__(kFwdThreads, FwdMinBlocks<T>::value) fwd_kernel(VolDev v, CamDev c, ParamDev p, float4 *out,
                                                            uint32_t *nsamples, unsigned *counter, int tiles_x,
                                                            unsigned ntiles)
 {
