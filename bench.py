@@ -80,9 +80,10 @@ def kernel_sources_sha256() -> str:
 
 
 def recorded_traffic(kernel: str):
-    """DRAM bytes (read + write) per launch of `kernel` on this workload, from
-    the ncu capture summarised in profiles/traffic_scale_1024.json; None when
-    the kernels have changed since that capture."""
+    """DRAM bytes (read + write) of one call of `kernel` on this workload (the
+    multi-view backward: its eight launches), from the ncu capture summarised
+    in profiles/traffic_scale_1024.json; None when the CUDA sources have
+    changed since that capture."""
     p = os.path.join(ROOT, "profiles", "traffic_scale_1024.json")
     if not os.path.exists(p):
         return None
@@ -90,7 +91,7 @@ def recorded_traffic(kernel: str):
         rec = json.load(f)
     if rec.get("sources_sha256") != kernel_sources_sha256():
         return None
-    v = rec.get("dram_bytes_per_launch", {}).get(kernel)
+    v = rec.get("dram_bytes_per_call", {}).get(kernel)
     return None if v is None else float(v)
 
 
@@ -1077,9 +1078,10 @@ def run_sortlast_1024(args):
 def run_skip_1024(args):
     """Exact empty-space skipping on the 1024^3 float32 cube and eight 1080p
     views with a source-finding table (opacity 0 below v = 6, i.e. six noise
-    sigmas; most 16^3 bricks hold only noise): the plain march and the
-    skipping march, which must give identical images; rates on nominal
-    samples (those marched or skipped up to early termination)."""
+    sigmas; most 16^3 bricks hold only noise): the plain march (texture
+    layers, and the bricks with them off) and the skipping march (texture
+    layers), which must give identical images; rates on nominal samples (those
+    marched or skipped up to early termination)."""
     import torch
     import paper_1211_4896_gb300 as P
     dev = torch.device("cuda")
@@ -1107,9 +1109,17 @@ def run_skip_1024(args):
     reps = max(3, args.steps)
     t_plain = _time_ms(torch, run(plain, nsp, False), reps)
     t_skip = _time_ms(torch, run(skip, nss, True), reps)
+    # both marches read texture layers by default; the plain one again on the
+    # bricks (layers off) for the rate of the brick layout
+    os.environ["VR_TEX_LAYERS"] = "0"
+    try:
+        t_plain_bricks = _time_ms(torch, run(plain, nsp, False), reps)
+    finally:
+        del os.environ["VR_TEX_LAYERS"]
     samples = sum(int(n.sum()) for n in nsp)
     same = all(torch.equal(x, y) for x, y in zip(plain, skip)) and all(torch.equal(x, y) for x, y in zip(nsp, nss))
     _emit({"workload": "skip_1024", "views": len(cams), "plain_ms_8_views": t_plain,
+                      "plain_bricks_ms_8_views": t_plain_bricks,
                       "skip_ms_8_views": t_skip, "speedup": t_plain / t_skip, "nominal_samples": samples,
                       "plain_gsamples_per_s": samples / t_plain / 1e6, "skip_gsamples_per_s": samples / t_skip / 1e6,
                       "skip_roofline_frac_nominal": gather_rate_frac(samples / t_skip / 1e6, 4),
@@ -1161,6 +1171,62 @@ def run_tex_1024(args):
     res["texture_over_software_rate"] = res["texture"]["gsamples_per_s"] / res["software"]["gsamples_per_s"]
     _emit(res)
     vol.close()
+
+
+def run_half_1024(args):
+    """The 1024^3 cube and eight 1080p views of the default workload stored
+    f32, f16 and bf16: the batched forward of the eight views (one graph call)
+    and the eight single-view renders; f32 through the texture layers (its
+    default for these dense views) and through the brick copies (layers off),
+    so that the 16-bit rates stand against both."""
+    import torch
+    import paper_1211_4896_gb300 as P
+    from paper_1211_4896_gb300 import _lib as L
+    dev = torch.device("cuda")
+    pre = synth.preset_scale_1024()
+    cube = make_cube(pre, dev)
+    tf = torch.from_numpy(synth.tf_ramp(256)).to(dev)
+    cams = pre["cameras"]
+    s_ptr = int(torch.cuda.current_stream().cuda_stream)
+    res = {"workload": "half_1024", "views": len(cams), "image": [1920, 1080]}
+    ref = None
+    for store, layers in (("f32", True), ("f32", False), ("f16", False), ("bf16", False)):
+        if not layers:
+            os.environ["VR_TEX_LAYERS"] = "0"
+        try:
+            vol = P.Volume(cube, store)
+            outs = [torch.empty((1080, 1920, 4), device=dev) for _ in cams]
+            nss = [torch.empty((1080, 1920), device=dev, dtype=torch.int32) for _ in cams]
+            jobs = [dict(vol=vol, cam=c, tf=tf, vmin=synth.TF_VMIN, vmax=synth.TF_VMAX, step=1.0, ert=0.99, out=o,
+                         nsamples=n) for c, o, n in zip(cams, outs, nss)]
+            cj = P.render_batched(jobs, use_graph=True)
+            opts = L.vr_batch_opts(1, 8, 4, 0)
+            t_bat = _time_ms(torch, lambda: L.vr_render_batched(cj, opts, s_ptr), max(5, args.steps))
+            ccams = [L.make_camera(c) for c in cams]
+            cpar = L.make_params(tf.data_ptr(), 256, synth.TF_VMIN, synth.TF_VMAX, 1.0, 0.99)
+
+            def single():
+                for cc, o, n in zip(ccams, outs, nss):
+                    L.vr_render(vol.handle, cc, cpar, o.data_ptr(), n.data_ptr(), s_ptr)
+            t_one = _time_ms(torch, single, max(5, args.steps))
+            samples = sum(int(n.sum()) for n in nss)
+            key = store + ("_layers" if layers else "_bricks")
+            r = {"batched_ms_8_views": t_bat, "batched_gsamples_per_s": samples / t_bat / 1e6,
+                 "single_ms_8_views": t_one, "single_gsamples_per_s": samples / t_one / 1e6,
+                 "layouts": sorted({L.vr_view_layout(vol.handle, cc) for cc in ccams})}
+            if ref is None:
+                ref = [o.clone() for o in outs]
+            else:
+                r["max_abs_diff_vs_f32"] = max(float((o - q).abs().max()) for o, q in zip(outs, ref))
+            res[key] = r
+            vol.close()
+            torch.cuda.empty_cache()
+        finally:
+            os.environ.pop("VR_TEX_LAYERS", None)
+    for st in ("f16", "bf16"):
+        for base in ("f32_layers", "f32_bricks"):
+            res["%s_over_%s_batched" % (st, base)] = res[base]["batched_ms_8_views"] / res[st + "_bricks"]["batched_ms_8_views"]
+    _emit(res)
 
 
 def _oracle_rate(fn, cores, min_s=1.0):
@@ -1265,7 +1331,7 @@ WORKLOADS = {"plain_128": run_plain_128, "precision_4096": run_precision_4096, "
              "diff_512": run_diff_512, "mip_1024": lambda a: run_modes_1024(a, "mip"),
              "sigma_1024": lambda a: run_modes_1024(a, "sigma"), "stats_1024": run_stats_1024,
              "sortlast_1024": run_sortlast_1024, "skip_1024": run_skip_1024, "tex_1024": run_tex_1024,
-             "cpu_oracle": run_cpu_oracle}
+             "cpu_oracle": run_cpu_oracle, "half_1024": run_half_1024}
 
 
 def main():

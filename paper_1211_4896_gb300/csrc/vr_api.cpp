@@ -850,14 +850,15 @@ vr_status vr_render(vr_volume_t vol, const vr_camera *cam, const vr_params *para
                 return cuda_fail(e, "vr_render: brick ranges");
             }
         }
-        e = launch_forward_skip(vol_dev_copy(vol, preferred_copy(vol, cam, true, s)), vol->store_dtype, c, p,
+        e = launch_forward_skip(vol_dev_copy(vol, preferred_copy(vol, cam, true, s, kReadsLayers)), vol->store_dtype,
+                                c, p,
                                 vol->brick_range, reinterpret_cast<uint32_t *>(vol->brick_range + nbr),
                                 reinterpret_cast<float4 *>(dev_rgba_out), dev_nsamples_out, ctr, s);
     } else if (params->mode == VR_MODE_MIP) {
-        e = launch_mip(vol_dev_copy(vol, preferred_copy(vol, cam, true, s)), vol->store_dtype, c, p,
+        e = launch_mip(vol_dev_copy(vol, preferred_copy(vol, cam, true, s, kReadsLayers)), vol->store_dtype, c, p,
                        reinterpret_cast<float4 *>(dev_rgba_out), dev_nsamples_out, ctr, s);
     } else if (params->mode == VR_MODE_SIGMA) {
-        e = launch_sigma(vol_dev_copy(vol, preferred_copy(vol, cam, true, s)), vol->store_dtype, c, p,
+        e = launch_sigma(vol_dev_copy(vol, preferred_copy(vol, cam, true, s, kReadsLayers)), vol->store_dtype, c, p,
                          params->minimap, params->minimap_region, reinterpret_cast<float4 *>(dev_rgba_out),
                          dev_nsamples_out, ctr, s);
     } else if (params->filter == VR_FILTER_TEXTURE) {
@@ -1068,7 +1069,8 @@ static vr_status subbox_of(vr_volume_t vol, const int64_t gdims[3], const int64_
     next_counter(vol, &ctr);
     const int gd[3] = {(int)gdims[0], (int)gdims[1], (int)gdims[2]};
     const int off[3] = {(int)offset[0], (int)offset[1], (int)offset[2]};
-    cudaError_t e = launch_subbox(vol_dev_copy(vol, preferred_copy(vol, cam, true, s)), vol->store_dtype, c, p,
+    cudaError_t e = launch_subbox(vol_dev_copy(vol, preferred_copy(vol, cam, true, s, kReadsLayers)), vol->store_dtype,
+                                  c, p,
                                   cell_lo, cell_hi, gd, off, reinterpret_cast<float4 *>(dev_partial), dev_depth,
                                   dev_count, ctr, s);
     if (e != cudaSuccess) return cuda_fail(e, who);

@@ -166,7 +166,8 @@ long long blocked_stride(int log2b, int elem_bytes);
 VolDev vol_dev_copy(const vr_volume *vol, int copy);
 // kinds: the copy kinds the caller's kernels read besides plain and paired
 // copies (kReadsBlocked: the forward and the batched forward; kReadsLayers:
-// those and the backward).
+// those, the backward, maximum intensity projection, sigma clipping, the
+// skipping march and the sort-last sub-box renders).
 constexpr unsigned kReadsBlocked = 1u, kReadsLayers = 2u;
 int preferred_copy(vr_volume *vol, const vr_camera *cam, bool may_build, cudaStream_t s, unsigned kinds = 0u);
 size_t copy_bytes(const vr_volume *vol, int copy);

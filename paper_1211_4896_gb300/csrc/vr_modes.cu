@@ -35,13 +35,13 @@ __device__ __forceinline__ float march_max(const VolDev &v, const ParamDev &p, c
     Cell c0, c1;
     Gathered<T, L> f0, f1;
     if (active) {
-        c0 = locate<LOG2B, L>(v, sample_pos(ray, 0, p.step));
+        c0 = locate_t<T, LOG2B, L, false>(v, sample_pos(ray, 0, p.step));
         fetch_corners<T, LOG2B, L>(v, c0, f0);
     }
     auto step = [&](const Cell &cur, const Gathered<T, L> &fc, Cell &nxt, Gathered<T, L> &fn) {
         const bool more = k + 1 < ray.n;
         if (more) {
-            nxt = locate<LOG2B, L>(v, sample_pos(ray, k + 1, p.step));
+            nxt = locate_t<T, LOG2B, L, false>(v, sample_pos(ray, k + 1, p.step));
             fetch_corners<T, LOG2B, L>(v, nxt, fn);
         }
         m = fmaxf(m, interp_corners(cur, fc));
@@ -59,8 +59,14 @@ __device__ __forceinline__ float march_max(const VolDev &v, const ParamDev &p, c
 
 // The pixel is the table entry of the largest value composited once over
 // the background; a ray that misses the box shows the background.
+// Resident CTAs the maximum intensity projection's register budget is sized
+// for: five for the texture layers (as the forward), the compiler's choice
+// for the brick layouts.
+template <typename T> struct ModeMinBlocks { static constexpr int value = 0; };   // 0: no minimum
+template <> struct ModeMinBlocks<TexLayers<float>> { static constexpr int value = 5; };
+
 template <typename T, int LOG2B, int L>
-__global__ void __launch_bounds__(kModeThreads) mip_kernel(VolDev v, CamDev c, ParamDev p, float4 *out,
+__global__ void __launch_bounds__(kModeThreads, ModeMinBlocks<T>::value) mip_kernel(VolDev v, CamDev c, ParamDev p, float4 *out,
                                                             uint32_t *nsamples, unsigned *counter, int tiles_x,
                                                             unsigned ntiles)
 {
@@ -189,7 +195,7 @@ cudaError_t launch_mip(const VolDev &v, vr_dtype dt, const CamDev &c, const Para
     const unsigned ntiles = (unsigned)tiles_x * (unsigned)tiles_y;
     cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(unsigned), s);
     if (e != cudaSuccess) return e;
-    return visit_layout(
+    return visit_layout_tex(
         v, dt,
         [&](auto lay) {
             using Y = decltype(lay);
@@ -217,7 +223,7 @@ cudaError_t launch_sigma(const VolDev &v, vr_dtype dt, const CamDev &c, const Pa
     const unsigned ntiles = (unsigned)tiles_x * (unsigned)tiles_y;
     cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(unsigned), s);
     if (e != cudaSuccess) return e;
-    return visit_layout(
+    return visit_layout_tex(
         v, dt,
         [&](auto lay) {
             using Y = decltype(lay);
@@ -310,13 +316,13 @@ __global__ void __launch_bounds__(kModeThreads) subbox_kernel(VolDev v, CamDev c
             return make_float3(g.x - off.x, g.y - off.y, g.z - off.z);     // exact for 0 <= off <= g
         };
         if (active) {
-            c0 = locate<LOG2B, L>(v, local(k));
+            c0 = locate_t<T, LOG2B, L, false>(v, local(k));
             fetch_corners<T, LOG2B, L>(v, c0, f0);
         }
         auto step = [&](const Cell &cur, const Gathered<T, L> &fc, Cell &nxt, Gathered<T, L> &fn) {
             const bool more = k + 1 < k_end;
             if (more) {
-                nxt = locate<LOG2B, L>(v, local(k + 1));
+                nxt = locate_t<T, LOG2B, L, false>(v, local(k + 1));
                 fetch_corners<T, LOG2B, L>(v, nxt, fn);
             }
             // the sample's cell in the whole grid, clamped as the whole render clamps it
@@ -363,7 +369,7 @@ cudaError_t launch_subbox(const VolDev &v, vr_dtype dt, const CamDev &c, const P
     const int3 l3 = make_int3(lo[0], lo[1], lo[2]), h3 = make_int3(hi[0], hi[1], hi[2]);
     const int3 g3 = make_int3(gdim[0], gdim[1], gdim[2]);
     const float3 o3 = make_float3((float)off[0], (float)off[1], (float)off[2]);
-    return visit_layout(
+    return visit_layout_tex(
         v, dt,
         [&](auto lay) {
             using Y = decltype(lay);

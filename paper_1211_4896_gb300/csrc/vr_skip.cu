@@ -168,7 +168,7 @@ __global__ void __launch_bounds__(kSkipThreads) skip_kernel(VolDev v, CamDev c, 
         // (ray.n if none), with its cell
         auto next = [&](int k, Cell &cell) {
             while (k < ray.n) {
-                cell = locate<LOG2B, L>(v, sample_pos(ray, k, p.step));
+                cell = locate_t<T, LOG2B, L, false>(v, sample_pos(ray, k, p.step));
                 const int bx = cell.x0 >> LOG2B, by = cell.y0 >> LOG2B, bz = cell.z0 >> LOG2B;
                 const long long brick = ((long long)bz * v.nby + by) * v.nbx + bx;
                 if (brick != last) {
@@ -231,6 +231,31 @@ __global__ void __launch_bounds__(kSkipThreads) skip_kernel(VolDev v, CamDev c, 
     }
 }
 
+// The skipping march's layouts: those of visit_layout, and the texture
+// layers instantiated with the volume's own brick size (LOG2B sizes the
+// bricks whose transparency bits the march tests; the layers ignore it).
+template <int LOG2B, typename F, typename R>
+static R visit_skip_layers_b(const VolDev &v, F &&f, R none)
+{
+    if (v.order == 0) return f(Layout<TexLayers<float>, LOG2B, 0>{});
+    if (v.order == 1) return f(Layout<TexLayers<float>, LOG2B, 1>{});
+    if (v.order == 2) return f(Layout<TexLayers<float>, LOG2B, 2>{});
+    return none;
+}
+
+template <typename F, typename R>
+static R visit_skip_layout(const VolDev &v, vr_dtype dt, F &&f, R none)
+{
+    if (v.paired != 3) return visit_layout(v, dt, f, none);
+    if (dt != VR_F32) return none;
+    switch (v.log2b) {
+    case 4: return visit_skip_layers_b<4>(v, f, none);
+    case 5: return visit_skip_layers_b<5>(v, f, none);
+    case 6: return visit_skip_layers_b<6>(v, f, none);
+    }
+    return none;
+}
+
 cudaError_t launch_forward_skip(const VolDev &v, vr_dtype dt, const CamDev &c, const ParamDev &p,
                                 const float2 *range, uint32_t *mask, float4 *out, uint32_t *nsamples,
                                 unsigned *counter, cudaStream_t s)
@@ -247,7 +272,7 @@ cudaError_t launch_forward_skip(const VolDev &v, vr_dtype dt, const CamDev &c, c
     if (e != cudaSuccess) return e;
     const bool in_smem = mask_words <= kMaskSmemWords;
     const size_t smem = in_smem ? sizeof(uint32_t) * (size_t)mask_words : 0;
-    return visit_layout(
+    return visit_skip_layout(
         v, dt,
         [&](auto lay) {
             using Y = decltype(lay);

@@ -358,32 +358,60 @@ static void copy_d(vr_volume *vol, int copy, cudaStream_t s)
 // its in-layer coordinates (LayerUV<A>).  One thread per voxel, reading the
 // bricks in x order and writing through the layered surface.
 // ---------------------------------------------------------------------------
+// Voxel (x, y, z) of a float volume's bricks.
+__device__ __forceinline__ float brick_voxel(const VolDev &v, int x, int y, int z)
+{
+    const int B = 1 << v.log2b, B1 = B + 1;
+    const int bx = min(x >> v.log2b, v.nbx - 1), by = min(y >> v.log2b, v.nby - 1),
+              bz = min(z >> v.log2b, v.nbz - 1);
+    const int lx = x - bx * B, ly = y - by * B, lz = z - bz * B;
+    const long long brick = ((long long)bz * v.nby + by) * v.nbx + bx;
+    return static_cast<const float *>(v.data)[brick * v.stride + ((long long)lz * B1 + ly) * B1 + lx];
+}
+
+// Layers across z (u = x) or y (u = x): threads along x read and write
+// neighbouring voxels.
 template <int A>
 __global__ void __launch_bounds__(256) unbrick_to_layers(VolDev v, cudaSurfaceObject_t surf)
 {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y, z = blockIdx.z;
     if (x >= v.nx) return;
-    const int B = 1 << v.log2b, B1 = B + 1;
-    const int bx = min(x >> v.log2b, v.nbx - 1), by = min(y >> v.log2b, v.nby - 1),
-              bz = min(z >> v.log2b, v.nbz - 1);
-    const int lx = x - bx * B, ly = y - by * B, lz = z - bz * B;
-    const long long brick = ((long long)bz * v.nby + by) * v.nbx + bx;
-    const float val = static_cast<const float *>(v.data)[brick * v.stride + ((long long)lz * B1 + ly) * B1 + lx];
+    const float val = brick_voxel(v, x, y, z);
     const int c[3] = {x, y, z};
     surf2DLayeredwrite(val, surf, c[LayerUV<A>::u] * (int)sizeof(float), c[LayerUV<A>::v], c[A]);
+}
+
+// Layers across x (u = z): a 32 x 32 tile of (x, z) at one y goes through
+// shared memory, read along x and written along z.
+__global__ void __launch_bounds__(256) unbrick_to_x_layers(VolDev v, cudaSurfaceObject_t surf)
+{
+    __shared__ float tile[32][33];
+    const int x0 = blockIdx.x * 32, z0 = blockIdx.z * 32, y = blockIdx.y;
+    const int tx = threadIdx.x, ty = threadIdx.y;                 // 32 x 8 threads
+    for (int r = ty; r < 32; r += 8) {
+        const int x = x0 + tx, z = z0 + r;
+        if (x < v.nx && z < v.nz) tile[r][tx] = brick_voxel(v, x, y, z);
+    }
+    __syncthreads();
+    for (int r = ty; r < 32; r += 8) {
+        const int z = z0 + tx, x = x0 + r;
+        if (x < v.nx && z < v.nz) surf2DLayeredwrite(tile[tx][r], surf, z * (int)sizeof(float), y, x);
+    }
 }
 
 static cudaError_t fill_layers(vr_volume *vol, int axis, cudaStream_t s)
 {
     const VolDev v = vol_dev(vol);
-    const dim3 grid((unsigned)((vol->dims[0] + 255) / 256), (unsigned)vol->dims[1], (unsigned)vol->dims[2]);
     const cudaSurfaceObject_t surf = vol->layers[axis].surf;
-    switch (axis) {
-    case 0: unbrick_to_layers<0><<<grid, 256, 0, s>>>(v, surf); break;
-    case 1: unbrick_to_layers<1><<<grid, 256, 0, s>>>(v, surf); break;
-    default: unbrick_to_layers<2><<<grid, 256, 0, s>>>(v, surf); break;
+    if (axis == 0) {
+        const dim3 grid((unsigned)((vol->dims[0] + 31) / 32), (unsigned)vol->dims[1], (unsigned)((vol->dims[2] + 31) / 32));
+        unbrick_to_x_layers<<<grid, dim3(32, 8), 0, s>>>(v, surf);
+        return cudaGetLastError();
     }
+    const dim3 grid((unsigned)((vol->dims[0] + 255) / 256), (unsigned)vol->dims[1], (unsigned)vol->dims[2]);
+    if (axis == 1) unbrick_to_layers<1><<<grid, 256, 0, s>>>(v, surf);
+    else unbrick_to_layers<2><<<grid, 256, 0, s>>>(v, surf);
     return cudaGetLastError();
 }
 

@@ -90,9 +90,11 @@ def test_mip_half_storage_on_the_rounded_cube(P, torch, store):
         vol.close()
 
 
-def test_mip_rolled_view_reads_a_copy_bit_identically(P, torch):
+def test_mip_rolled_view_reads_a_copy_bit_identically(P, torch, monkeypatch):
     """A view and its 90-degree roll about the view axis (square image, eye on
-    the axis) read different brick layouts and give transposed images."""
+    the axis) read different brick layouts and give transposed images (the
+    brick copies: texture layers off)."""
+    monkeypatch.setenv("VR_TEX_LAYERS", "0")
     dims = (40, 36, 44)
     cube = synth.hi_cube(dims, n_blobs=8, n_disks=1, seed=7).numpy()
     vol = P.Volume(torch.from_numpy(cube).cuda(), "f32")
@@ -109,6 +111,19 @@ def test_mip_rolled_view_reads_a_copy_bit_identically(P, torch):
         i, j = np.arange(n)[None, :], np.arange(n)[:, None]
         assert np.array_equal(b.cpu().numpy(), a.cpu().numpy()[n - 1 - i, j])
         assert np.array_equal(nb.cpu().numpy(), na.cpu().numpy()[n - 1 - i, j])
+        # MIP and sigma clipping through the texture layers (across z for both
+        # views): the images of the bricks, bit for bit
+        mm = P.minimap(vol, (8, 8, 8))
+        for up in ((0, 1, 0), (1, 0, 0)):
+            cam = synth.camera_persp(eye, (0, 0, 1), up, 20.0, n, n)
+            for kw in (dict(mode=P.VR_MODE_MIP), dict(mode=P.VR_MODE_SIGMA, minimap=mm, region=(8, 8, 8))):
+                monkeypatch.setenv("VR_TEX_LAYERS", "0")
+                ref, rn = P.render(vol, cam, tf, -3, 30, 0.5, **kw)
+                monkeypatch.delenv("VR_TEX_LAYERS")
+                got, gn = P.render(vol, cam, tf, -3, 30, 0.5, **kw)
+                torch.cuda.synchronize()
+                assert torch.equal(got, ref) and torch.equal(gn, rn)
+        assert P._lib.vr_volume_info(vol.handle)["copies"] >> 9 == 0b100
     finally:
         vol.close()
 
