@@ -767,6 +767,11 @@ def run_precision_4096(args):
                 P.render(vol, c, tf, synth.TF_VMIN, synth.TF_VMAX, 1.0, 0.99, out=o, nsamples=n)
         ms = _time_ms(torch, f, 3)
         samples = sum(int(n.sum()) for n in nss)
+        per_view = []
+        for c, o, n in zip(cams, outs, nss):
+            ms_v = _time_ms(torch, lambda: P.render(vol, c, tf, synth.TF_VMIN, synth.TF_VMAX, 1.0, 0.99, out=o,
+                                                    nsamples=n), 3, min_s=0.2)
+            per_view.append({"ms": ms_v, "rays_hit": int((n > 0).sum()), "samples": int(n.sum())})
         layouts = [L.vr_view_layout(vol.handle, L.make_camera(c)) for c in cams]
         vol.close()
         torch.cuda.empty_cache()
@@ -787,7 +792,7 @@ def run_precision_4096(args):
         kern = "fwd_kernel<float>@sparse" if store == "f32" else "fwd_kernel<Blocked<16-bit>>@sparse"
         clk = ClockSampler.summarize(CLOCKS.raw) or {}
         res[store] = {"gsamples_per_s": gs, "ms_4_views": ms, "fps": 4e3 / ms, "vs_f32": gs / base,
-                      "roofline_frac": gather_rate_frac(gs, eb), "layouts": layouts,
+                      "roofline_frac": gather_rate_frac(gs, eb), "layouts": layouts, "per_view": per_view,
                       "ceilings": ceilings(samples, ms * 1e-3, eb, eb * b_alg_vox, kern, clk.get("sm_mhz")),
                       "bricked_gb": vol.info["bytes"] / 1e9,
                       "crop_px_err": _merge_px(errs, "FP64 oracle on the float32 256^3 crop, rows %s of its 4 "

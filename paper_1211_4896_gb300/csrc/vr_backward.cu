@@ -22,7 +22,9 @@
 // columns of 32 opacity bins in shared memory (plain loads and stores, no
 // conflicts), summed into the warp's row when it has no tiles left.  One
 // final kernel sums the warps' rows in FP64 (the only FP64 arithmetic: the
-// cross-block sum).
+// cross-block sum).  The table itself is copied into shared memory when the
+// kernel starts, so its two entries per sample do not wait behind the
+// volume gathers in the L1/texture pipeline.
 // The voxel gradient is scattered with reductions.  A ray's pending sums for
 // the eight corners of its current cell are kept as two planes of four
 // corners across the carry axis (the view's dominant axis); when the ray
@@ -260,7 +262,7 @@ __global__ void __launch_bounds__(kBwdThreads, BwdMinBlocks<VT>::value) bwd_kern
         const int lo = zero_opacity_window(p, lane);
         if (lane == 0) window_lo = lo;
     }
-    __syncthreads();
+    stage_tf(p);              // (its barrier also publishes the window)
     const OpacityWindow win{&window[warp][0][lane], window_lo};
 
     for (;;) {
@@ -305,7 +307,7 @@ __global__ void __launch_bounds__(kBwdThreads, BwdMinBlocks<VT>::value) bwd_kern
             const float val = interp_corners(cell, f);
             TfPos tp;
             float4 de;
-            const float4 e = tf_lookup_l1(p, val, tp, de);
+            const float4 e = tf_lookup_l1<true>(p, val, tp, de);
             const float a = e.w;
             const float cg = e.x * g.x + e.y * g.y + e.z * g.z;
             const float aT = a * T;
@@ -413,11 +415,11 @@ static GradDev grad_dev(const VolDev &v, float *grad_vox, float4 *grad_quad, int
 }
 
 // Persistent grid of one view's backward kernel: the resident CTAs, but no
-// more than its tiles need.
-static unsigned view_grid(const void *fn, const CamDev &c)
+// more than its tiles need (smem: the staged table).
+static unsigned view_grid(const void *fn, const CamDev &c, size_t smem)
 {
     const unsigned ntiles = (unsigned)((c.W + 7) / 8) * (unsigned)((c.H + 3) / 4);
-    unsigned grid = (unsigned)(occupancy_blocks(fn, kBwdThreads, 0) * sm_count());
+    unsigned grid = (unsigned)(occupancy_blocks(fn, kBwdThreads, smem) * sm_count());
     const unsigned max_useful = (ntiles + kBwdWarps - 1) / kBwdWarps;
     if (grid > max_useful) grid = max_useful;
     return grid < 1 ? 1 : grid;
@@ -472,7 +474,8 @@ static cudaError_t launch_view(const BwdView &bv, vr_dtype dt, const ParamDev &p
         [&](auto lay) {
             using Y = decltype(lay);
             auto fn = bwd_kernel<typename Y::type, Y::log2b, Y::order>;
-            fn<<<view_grid((const void *)fn, bv.c), kBwdThreads, 0, s>>>(bv.v, bv.c, p, bv.rgba, bv.nsamples,
+            const size_t smem = tf_shared_bytes(p);
+            fn<<<view_grid((const void *)fn, bv.c, smem), kBwdThreads, smem, s>>>(bv.v, bv.c, p, bv.rgba, bv.nsamples,
                                                                         bv.grad_rgba, wtab, gd, counter, tiles_x,
                                                                         ntiles);
             return cudaGetLastError();
@@ -497,7 +500,7 @@ cudaError_t launch_backward(vr_volume *vol, const BwdView *views, int n, const P
         const void *fn = nullptr;
         cudaError_t e = view_kernel(views[q], dt, &fn);
         if (e != cudaSuccess) return e;
-        const unsigned g = view_grid(fn, views[q].c);
+        const unsigned g = view_grid(fn, views[q].c, tf_shared_bytes(p));
         if (g > max_grid) max_grid = g;
     }
     const int nrows = (int)max_grid * kBwdWarps;
