@@ -159,8 +159,9 @@ typedef struct {
  * x fastest) into a bricked copy in store_dtype: bricks of B^3 cells, each
  * stored as (B+1)^3 voxels so that all 8 trilinear corners of any cell lie in
  * one brick, x fastest inside a brick.  F32 -> F16/BF16 rounds to nearest
- * even.  brick = 0 picks 16; otherwise 16, 32 or 64.  origin/spacing may be
- * NULL (0 and 1).
+ * even.  brick = 0 picks 16, or 64 for a volume whose 16^3 bricks would take
+ * more than 16 GiB; otherwise 16, 32 or 64.  origin/spacing may be NULL (0
+ * and 1).
  *
  * Copies made later, on first use: the first VR_FILTER_SOFTWARE_STAGED call
  * adds a dense copy with rows padded to 8 elements, streamed slab by slab
