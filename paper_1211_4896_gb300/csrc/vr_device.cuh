@@ -666,7 +666,8 @@ struct Composite {
 // Cell and a Gathered set of registers per stage, and so resident warps.
 // Measured on the 1024^3 eight-view workload: 16-bit layouts gain from depth
 // 2 (oblique views 10% faster; packed pairs keep the register cost low),
-// float loses from it (axis views 3% slower), so float keeps depth 1.
+// float loses from it (axis views 3% slower), so float keeps depth 1 (the
+// single-view kernel of the texture layers asks for 2, vr_forward.cu).
 template <typename T> struct Pipeline { static constexpr int depth = 2; };
 template <> struct Pipeline<float> { static constexpr int depth = 1; };
 template <> struct Pipeline<TexLayers<float>> { static constexpr int depth = 1; };
@@ -705,11 +706,10 @@ __device__ __forceinline__ void march_step(const VolDev &v, const ParamDev &p, c
 
 // The loop body is unrolled over depth + 1 register sets that take turns, so
 // a prefetched sample is never copied.
-template <typename T, int LOG2B, int L, typename Map = IdentityMap>
+template <typename T, int LOG2B, int L, typename Map = IdentityMap, int D = Pipeline<T>::depth>
 __device__ __forceinline__ int march_ray(const VolDev &v, const ParamDev &p, const Ray &ray, bool active,
                                          Composite &acc, const Map &map = Map())
 {
-    constexpr int D = Pipeline<T>::depth;
     static_assert(D == 1 || D == 2, "pipeline depth 1 or 2");
     constexpr bool N = !std::is_same<T, float>::value;
     int k = 0;
@@ -726,9 +726,9 @@ __device__ __forceinline__ int march_ray(const VolDev &v, const ParamDev &p, con
     if constexpr (D == 1) {
         for (;;) {
             if (!__any_sync(kFull, active)) break;
-            if (active) march_step<T, LOG2B, L, Map>(v, p, ray, k, active, acc, c0, f0, c1, f1, map);
+            if (active) march_step<T, LOG2B, L, Map, D>(v, p, ray, k, active, acc, c0, f0, c1, f1, map);
             if (!__any_sync(kFull, active)) break;
-            if (active) march_step<T, LOG2B, L, Map>(v, p, ray, k, active, acc, c1, f1, c0, f0, map);
+            if (active) march_step<T, LOG2B, L, Map, D>(v, p, ray, k, active, acc, c1, f1, c0, f0, map);
         }
     } else {
         // one warp vote per round of register sets (measured faster for the
@@ -736,9 +736,9 @@ __device__ __forceinline__ int march_ray(const VolDev &v, const ParamDev &p, con
         // the rest of it on its own `active`
         for (;;) {
             if (!__any_sync(kFull, active)) break;
-            if (active) march_step<T, LOG2B, L, Map>(v, p, ray, k, active, acc, c0, f0, c2, f2, map);
-            if (active) march_step<T, LOG2B, L, Map>(v, p, ray, k, active, acc, c1, f1, c0, f0, map);
-            if (active) march_step<T, LOG2B, L, Map>(v, p, ray, k, active, acc, c2, f2, c1, f1, map);
+            if (active) march_step<T, LOG2B, L, Map, D>(v, p, ray, k, active, acc, c0, f0, c2, f2, map);
+            if (active) march_step<T, LOG2B, L, Map, D>(v, p, ray, k, active, acc, c1, f1, c0, f0, map);
+            if (active) march_step<T, LOG2B, L, Map, D>(v, p, ray, k, active, acc, c2, f2, c1, f1, map);
         }
     }
     return k;
