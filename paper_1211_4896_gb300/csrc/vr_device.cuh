@@ -68,7 +68,12 @@ template <typename S> struct is_pair<Pair<S>> { static constexpr bool value = tr
 // ray that shares no sector with its neighbours then fetches a new sector
 // only every BW / 2 ... BW steps of a cell's 2 x 2 columns, where a
 // row-ordered brick costs two sectors per step whatever the voxel size; so
-// a 16-bit volume moves half the sectors of a float one.
+// a 16-bit volume moves half the sectors of a float one.  Blocks follow each
+// other across u first: a 128-byte line then holds a ray's neighbouring
+// columns, so each ray keeps fewer lines live in L1 and L2.  (Blocks of one
+// column made contiguous along w moved 10-20% fewer DRAM bytes per sample
+// but were 15% slower on the 4096 x 4096 x 1024 cube: every column a ray
+// reads then holds a line of its own for 16 steps.)
 template <typename S> struct Blocked {
     using storage = S;
 };

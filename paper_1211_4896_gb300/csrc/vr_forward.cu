@@ -114,17 +114,27 @@ int occupancy_blocks(const void *fn, int threads, size_t smem)
 }
 
 // Resident CTAs per SM for the persistent forward grid: the occupancy limit,
-// or VR_FWD_CTAS_PER_SM when set (a tuning knob: fewer resident warps thrash
-// the L1 less).
-static int fwd_ctas_per_sm(const void *fn)
+// at most `cap` (0: none), or VR_FWD_CTAS_PER_SM when set (a tuning knob:
+// fewer resident warps thrash the L1 and L2 less).
+static int fwd_ctas_per_sm(const void *fn, int cap)
 {
     const int occ = occupancy_blocks(fn, kFwdThreads, 0);
     static const int env = [] {
         const char *s = std::getenv("VR_FWD_CTAS_PER_SM");
         return s ? std::atoi(s) : 0;
     }();
-    return (env > 0 && env < occ) ? env : occ;
+    const int want = env > 0 ? env : cap;
+    return (want > 0 && want < occ) ? want : occ;
 }
+
+// CTAs per SM for the float brick layouts, which serve the views whose rays
+// are too far apart for texture layers: three, where each resident ray keeps
+// its own cache lines live and more of them thrash L1 and L2 (four 1080p
+// views of the 4096 x 4096 x 1024 cube: along z 6.20 -> 5.45 ms, along x
+// 7.19 -> 7.01 ms; two were slower again).  The other layouts: the occupancy
+// limit (16-bit blocked copies measured the same at two, three and four).
+template <typename T> struct FwdCtaCap { static constexpr int value = 0; };
+template <> struct FwdCtaCap<float> { static constexpr int value = 3; };
 
 template <typename T, int LOG2B, int L>
 static cudaError_t launch_fwd_t(const VolDev &v, const CamDev &c, const ParamDev &p, float4 *out,
@@ -133,7 +143,7 @@ static cudaError_t launch_fwd_t(const VolDev &v, const CamDev &c, const ParamDev
     const int tiles_x = (c.W + 7) / 8, tiles_y = (c.H + 3) / 4;
     const unsigned ntiles = (unsigned)tiles_x * (unsigned)tiles_y;
     auto fn = fwd_kernel<T, LOG2B, L>;
-    const int per_sm = fwd_ctas_per_sm((const void *)fn);
+    const int per_sm = fwd_ctas_per_sm((const void *)fn, FwdCtaCap<T>::value);
     unsigned grid = (unsigned)(per_sm * sm_count());
     const unsigned max_useful = (ntiles + kFwdThreads / 32 - 1) / (kFwdThreads / 32);
     if (grid > max_useful) grid = max_useful;

@@ -330,3 +330,18 @@ def test_update_refreshes_reordered_copies(P, torch, scene):
         compare(b, nb.cpu().numpy(), oracle.render(cube2, camB, tf_np, VMIN, VMAX, STEP), TOL_F32)
     finally:
         vol.close()
+
+
+def test_auto_brick_size_follows_volume_bytes(P, torch):
+    """brick = 0 picks 16^3 bricks, and 64^3 once 16^3 bricks (with their
+    +1 apron) would take more than 16 GiB: a 2048 x 2048 x 1024 16-bit cube
+    needs about 10 GB of 16^3 bricks, a 4096 x 2048 x 1024 one about 21 GB."""
+    for (nz, ny, nx), want in (((1024, 2048, 2048), 16), ((1024, 2048, 4096), 64)):
+        cube = torch.zeros((nz, ny, nx), device="cuda", dtype=torch.float16)
+        vol = P.Volume(cube, "f16")
+        try:
+            assert vol.info["brick"] == want, (nx, ny, nz, vol.info["brick"])
+        finally:
+            vol.close()
+            del cube
+            torch.cuda.empty_cache()
