@@ -530,14 +530,34 @@ def run_ours(args, rank, world, local_rank):
     h2d = pin_tf.numel() * 4 + sum(g.numel() * 4 for g in pin_g)
     d2h = sum(o.numel() * 4 for o in pin_out) + pin_gtf.numel() * 8
 
+    # The step's host copies run on a copy stream beside the kernels: the
+    # gradient images go up while the forward runs (the backward waits for
+    # them), the rendered images come down while the backward runs (the next
+    # forward waits for them), the table gradient after the backward.
+    copy_stream = torch.cuda.Stream(device=dev)
+    ev_bwd, ev_d2h = torch.cuda.Event(), torch.cuda.Event()
+    ev_bwd.record(stream)
+    ev_d2h.record(stream)
+
     def e2e_step():
+        ev_h2d, ev_fwd = torch.cuda.Event(), torch.cuda.Event()
+        with torch.cuda.stream(copy_stream):
+            copy_stream.wait_event(ev_bwd)             # the last backward has read the gradients
+            for g, pg in zip(grads, pin_g):
+                g.copy_(pg, non_blocking=True)
+            ev_h2d.record(copy_stream)
+        stream.wait_event(ev_d2h)                      # the last images have been read out
         tf.copy_(pin_tf, non_blocking=True)
-        for g, pg in zip(grads, pin_g):
-            g.copy_(pg, non_blocking=True)
         fwd()
+        ev_fwd.record(stream)
+        with torch.cuda.stream(copy_stream):
+            copy_stream.wait_event(ev_fwd)
+            for o, po in zip(outs, pin_out):
+                po.copy_(o, non_blocking=True)
+            ev_d2h.record(copy_stream)
+        stream.wait_event(ev_h2d)
         bwd()
-        for o, po in zip(outs, pin_out):
-            po.copy_(o, non_blocking=True)
+        ev_bwd.record(stream)
         pin_gtf.copy_(grad_tf, non_blocking=True)
 
     e2e_step()
@@ -546,6 +566,7 @@ def run_ours(args, rank, world, local_rank):
     a.record(stream)
     for _ in range(args.steps):
         e2e_step()
+    stream.wait_event(ev_d2h)                          # the last step's images are on the host
     b.record(stream)
     barrier()
     e2e_ms, _ = reduce_over_ranks(a.elapsed_time(b) / args.steps, samples_per_step, dev)
@@ -615,7 +636,10 @@ def run_ours(args, rank, world, local_rank):
                     "plain_fp32_view_ms_p75": p75, "fps_p75": 1e3 / p75},
             "bwd": {"ms_8_views": bwd_ms, "bwd_over_fwd": bwd_ms / fwd_ms},
             "px_err": px, "roofline": roof, "ceilings": ceil, "cpu_baseline": cpu,
-            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                    "copies": "pinned host buffers through a copy stream: each step's gradient images go up "
+                              "during its forward, its images come down during its backward, its table "
+                              "gradient after it; all inside the timed region"},
             "gpu_launches": args.steps * (groups + nv + 1), "clocks": clk}
     if rank == 0:
         print(json.dumps(line))
