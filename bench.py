@@ -813,7 +813,8 @@ def run_precision_4096(args):
         gs = samples / ms / 1e6
         base = base or gs
         eb = 4 if store == "f32" else 2
-        kern = "fwd_kernel<float>@sparse" if store == "f32" else "fwd_kernel<Blocked<16-bit>>@sparse"
+        kern = "fwd_kernel<float>@sparse" if store == "f32" else (
+            "fwd_kernel<Blocked<16-bit>>@sparse" if min(layouts) >= 6 else "fwd_kernel<16-bit>@sparse")
         clk = ClockSampler.summarize(CLOCKS.raw) or {}
         res[store] = {"gsamples_per_s": gs, "ms_4_views": ms, "fps": 4e3 / ms, "vs_f32": gs / base,
                       "roofline_frac": gather_rate_frac(gs, eb), "layouts": layouts, "per_view": per_view,

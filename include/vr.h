@@ -175,8 +175,9 @@ typedef struct {
  * holding its own value and the next one along that axis so that four loads
  * fetch a cell's eight corners (twice the bricks' bytes).  For rays at least
  * VR_SPARSE_MIN_PITCH voxels apart (default 3), which share no sectors, the
- * forward (vr_render, vr_render_batched) of a 16-bit volume reads a blocked
- * copy instead: blocks of 2 x 2 x 4 voxels, one 32-byte sector each, deep
+ * forward (vr_render, vr_render_batched) of a 16-bit volume in bricks smaller
+ * than 64^3 reads a blocked copy instead (in 64^3 bricks the plain copies
+ * measured faster and serve): blocks of 2 x 2 x 4 voxels, one 32-byte sector each, deep
  * along the axis the view direction is closest to (about 1.2x the bricks'
  * bytes); VR_SPARSE_LAYOUT=b asks for blocked copies (2 x 2 x 2 blocks) for
  * float volumes too, =i never.  For float storage and rays closer than

@@ -381,15 +381,17 @@ int preferred_copy(vr_volume *vol, const vr_camera *cam, bool may_build, cudaStr
     }();
     // layout of sparse views (VR_SPARSE_LAYOUT): 'b' blocked copies (forward
     // kernels only), 'i' as dense views (rows along the image's horizontal
-    // axis); default 'b' for 16-bit and 'i' for float storage, as measured on
-    // the 4096 x 4096 x 1024 cube (16-bit: blocked 4% faster; float: the two
-    // blocked copies its views want do not fit beside the cube, and the one
-    // row copy serves every view)
+    // axis); default 'b' for 16-bit storage in bricks smaller than 64^3 and
+    // 'i' otherwise, as measured on the four 1080p views of the 4096 x 4096 x
+    // 1024 cube (16-bit in 16^3 bricks: blocked 83.6 against 80.2 Gsamples/s
+    // for rows; in 64^3 bricks, this cube's default: rows 119 against 92.4;
+    // float: the two blocked copies its views want do not fit beside the
+    // cube, and the row copies serve every view)
     static const char sparse_env = [] {
         const char *e = std::getenv("VR_SPARSE_LAYOUT");
         return e && (e[0] == 'b' || e[0] == 'i') ? e[0] : 0;
     }();
-    const char sparse_mode = sparse_env ? sparse_env : (vol->store_dtype == VR_F32 ? 'i' : 'b');
+    const char sparse_mode = sparse_env ? sparse_env : (vol->store_dtype == VR_F32 || vol->log2b >= 6 ? 'i' : 'b');
     if (!enabled) return -1;
     double f[3] = {cam->forward[0], cam->forward[1], cam->forward[2]}, r[3];
     cross3(f, cam->up, r);

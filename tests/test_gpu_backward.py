@@ -71,6 +71,37 @@ def test_backward_matches_fp64_reverse_sweep(P, torch, ert, bg, filt):
     vol.close()
 
 
+@pytest.mark.parametrize("K", [2, 1600])
+def test_backward_smallest_and_largest_table(P, torch, K, monkeypatch):
+    """The backward copies its table into shared memory (K float4 entries, up
+    to 1600, the largest table it accepts): the two-entry table and the
+    largest one against the oracle's FP64 reverse sweep, through the texture
+    layers (the dense float view's copy) and through the brick copies."""
+    dims = (30, 26, 34)
+    cube, vol, cam = _setup(torch, P, dims, seed=33, W=40, H=36)
+    dev = torch.device("cuda")
+    tf_np = synth.tf_ramp(K, alpha_max=0.3)
+    tf = torch.from_numpy(tf_np).to(dev)
+    g, ref_tf, ref_vox = None, None, None
+    for layers in ("1", "0"):
+        monkeypatch.setenv("VR_TEX_LAYERS", layers)        # read at each call
+        img, ns = P.render(vol, cam, tf, -3.0, 30.0, 0.5, 2.0)
+        if g is None:
+            g = torch.randn(img.shape, device=dev, generator=torch.Generator(device=dev).manual_seed(K))
+            ref_tf, ref_vox = oracle.render_backward(cube.numpy(), cam, tf_np, -3.0, 30.0, 0.5,
+                                                     g.cpu().numpy().astype(np.float64))
+        gtf, gvox = P.render_backward(vol, cam, tf, -3.0, 30.0, 0.5, img, ns, g, 2.0)
+        torch.cuda.synchronize()
+        for got, ref in ((gtf.cpu().numpy(), ref_tf), (gvox.cpu().numpy().astype(np.float64), ref_vox)):
+            rel_norm = np.linalg.norm(got - ref) / np.linalg.norm(ref)
+            rel_max = np.abs(got - ref).max() / np.abs(ref).max()
+            assert rel_norm <= 1e-3 and rel_max <= 1e-3, (K, layers, rel_norm, rel_max)
+    with pytest.raises(P.VRError):                            # one entry more is refused
+        big = torch.from_numpy(synth.tf_ramp(1601, alpha_max=0.3)).to(dev)
+        P.render_backward(vol, cam, big, -3.0, 30.0, 0.5, img, ns, g, 2.0)
+    vol.close()
+
+
 @pytest.mark.parametrize("dims,brick,store,W,H,step", [((36, 30, 40), 16, "f32", 48, 40, 0.5),
                                                        ((41, 27, 33), 32, "f16", 64, 56, 0.35),
                                                        ((30, 34, 26), 16, "bf16", 40, 30, 1.0)])
